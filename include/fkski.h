@@ -1,0 +1,212 @@
+/*
+ * fkski -- faster kernel interpolation for Gaussian processes (GSGP / factorized SKI) on GB300.
+ *
+ * C ABI of libfkski.so.  Yadav, Sheldon & Musco, "Faster Kernel Interpolation for Gaussian
+ * Processes" (arXiv 2101.11751).  Notation follows the paper: n training points x_i with targets
+ * y_i, a regular grid G of m nodes, interpolation matrix W (n x m, cubic convolution, 4^d nonzeros
+ * per row), grid kernel matrix K_G (= K_UU), noise variance sigma^2.
+ *
+ * Conventions for every entry point
+ *  - Return value: FKSKI_OK (0) or a negative FKSKI_E_* code.  No call aborts or prints.
+ *  - Pointers documented "device" are CUDA device pointers owned by the caller; the library never
+ *    frees them.  Pointers documented "host" are ordinary host memory.
+ *  - Every call takes a CUDA stream (cudaStream_t passed as void*; NULL = legacy default stream)
+ *    and is ordered on it.  A call that synchronizes the stream says so.
+ *  - fkski_stats owns its device memory (sufficient statistics, spectra, solver workspace); it is
+ *    released only by fkski_destroy.  Calls on one fkski_stats must not run concurrently.
+ *  - Determinism: identical inputs on the same GPU give bit-identical outputs.
+ *  - Layouts: points X are d x n, structure of arrays (X[k*n + i] = coordinate k of point i).
+ *    Grid vectors of length m are in C order over (M_1, ..., M_d), last axis fastest; node
+ *    (j_1..j_d) sits at lo_k + j_k h_k.  Several right-hand sides are stored rhs-major.
+ */
+#ifndef FKSKI_H
+#define FKSKI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FKSKI_API __attribute__((visibility("default")))
+#else
+#define FKSKI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define FKSKI_OK 0
+#define FKSKI_E_INVALID_ARG (-1)   /* d not in {1,2,3}, M_k < 4, h <= 0, sigma^2 <= 0, n < 1, NULL */
+#define FKSKI_E_OUT_OF_GRID (-2)   /* some point has s_k = (x_k - lo_k)/h_k outside [1, M_k - 2]   */
+#define FKSKI_E_NONFINITE (-3)     /* NaN or Inf in X, y or the probes                             */
+#define FKSKI_E_NOT_CONVERGED (-4) /* maxiter reached; outputs are still written, info filled      */
+#define FKSKI_E_BREAKDOWN (-5)     /* CG breakdown: p^T A p <= 0 or a non-finite inner product      */
+#define FKSKI_E_TIMEOUT (-6)       /* a bounded device wait gave up (never a trap)                  */
+#define FKSKI_E_OOM (-7)           /* device allocation failed                                      */
+#define FKSKI_E_CUDA (-8)          /* another CUDA runtime error                                    */
+#define FKSKI_E_UNSUPPORTED (-9)   /* a size beyond what this build supports (see each call)        */
+#define FKSKI_E_IO (-10)           /* file error in save/load                                       */
+
+#define FKSKI_F32 0
+#define FKSKI_F64 1
+
+#define FKSKI_RBF 0      /* s * exp(-1/2 sum_k (r_k / l_k)^2), separable: K_G = s T_1 (x) ... (x) T_d */
+#define FKSKI_MATERN52 1 /* s (1 + sqrt5 r + 5/3 r^2) exp(-sqrt5 r), r = ||r / l||: multilevel Toeplitz */
+
+#define FKSKI_X0_ZERO 0      /* Alg. 3 (EFCG, x0 = 0, r0 = y)                                      */
+#define FKSKI_X0_Y_OVER_S2 1 /* Alg. 5 (simplified EFCG, x0 = y / sigma^2, r0 in span(W))            */
+
+#define FKSKI_MIXED 0  /* FP32 vectors, band, FFT; FP64 inner products and scalars */
+#define FKSKI_DOUBLE 1 /* FP64 throughout                                          */
+
+/* ------------------------------------------------------------------ configuration structs */
+
+/* Regular grid G (Sec. 2.2, "m points on a dense d-dimensional grid"): node j on axis k is at
+ * lo[k] + j*h[k], j = 0..M[k]-1.  Cubic interpolation needs nodes c-1..c+2 around a point, so a
+ * point must satisfy 1 <= (x_k - lo_k)/h_k <= M_k - 2 on every axis. */
+typedef struct {
+    int d;
+    int64_t M[3];
+    double lo[3];
+    double h[3];
+} fkski_grid;
+
+/* Stationary kernel k(x, x') with hyperparameters theta = (l_1..l_d, s) and noise sigma^2
+ * (App. C.1: squared exponential in a scale kernel; Matern-5/2 as a non-separable alternative). */
+typedef struct {
+    int type;
+    double lengthscale[3];
+    double outputscale;
+    double noise_var;
+} fkski_kernel;
+
+typedef struct {
+    double rtol;          /* stop when ||r_k||_2 <= rtol * ||b||_2, b = y or the probe z_p      */
+    int maxiter;          /* CG iteration cap                                                  */
+    int x0_mode;          /* FKSKI_X0_ZERO or FKSKI_X0_Y_OVER_S2 (fkski_solve only)             */
+    int precision;        /* FKSKI_MIXED or FKSKI_DOUBLE                                       */
+    int check_every;      /* iterations per captured CUDA graph between host convergence checks */
+    int n_probes;         /* Rademacher probes accumulated by fkski_precompute (<= 64)         */
+    uint64_t probe_seed;  /* probe z_p(i) = sign of SplitMix64(seed) output k = p*2^40 + i + 1 */
+    size_t iterate_budget_bytes; /* fkski_loglik_forward keeps its solutions if they fit     */
+    int keep_sort;        /* fkski_precompute keeps cell keys and the permutation for export   */
+    int reserved[7];
+} fkski_opts;
+
+typedef struct {
+    int iters;            /* CG iterations (max over right-hand sides)                          */
+    int status;           /* FKSKI_OK, FKSKI_E_NOT_CONVERGED or FKSKI_E_BREAKDOWN               */
+    double rel_residual;  /* final ||r||/||r_0|| (max over right-hand sides)                    */
+    double t_ms[8];       /* stage times when measured (0 otherwise)                            */
+    int iters_rhs[65];    /* per right-hand side iteration counts (grad: [y, z_1..z_T])         */
+} fkski_info;
+
+typedef struct fkski_stats fkski_stats;
+
+/* Fill opts with defaults: rtol 1e-6, maxiter 1000, x0 Alg. 5, mixed precision, check_every 16,
+ * no probes, seed 0, budget 1 GiB, keep_sort 0. */
+FKSKI_API void fkski_default_opts(fkski_opts *opts);
+
+/* Human-readable name of a status code (static string). */
+FKSKI_API const char *fkski_strerror(int status);
+
+/* ------------------------------------------------------------------ precompute (Sec. 3.1)
+ * One O(n) pass computing the sufficient statistics of the Bayesian linear regression of Def. 2:
+ *   W^T W  stored as its 7^d diagonals (Claim 2: at most (4r-1)^d = 7^d nonzeros per row, r = 2),
+ *   W^T y, y^T y, and for opts->n_probes Rademacher probes z_p (or the caller's probes Z) W^T z_p
+ *   and z_p^T z_p.
+ * Points are sorted by grid cell with a stable sort (ties by input index) and reduced per cell
+ * in that order, so the result is deterministic.
+ *   grid   host; X device d x n (dtype); y device n (dtype); Z device n_probes x n (dtype) or NULL
+ *   dtype  FKSKI_F32 or FKSKI_F64 (points and targets).  F32: per-cell sums in FP32 (runs of
+ *          32 points per lane, then a second FP32 level) and FP32 statistics; F64: FP64 throughout.
+ *   out    receives a new fkski_stats on success (NULL on failure).
+ * Errors: INVALID_ARG, OUT_OF_GRID, NONFINITE, OOM, CUDA, UNSUPPORTED (n >= 2^31, cells >= 2^31,
+ * n_probes > 64).  Synchronizes the stream once, at the end, to report point errors. */
+FKSKI_API int fkski_precompute(const fkski_grid *grid, const void *X, const void *y, const void *Z, int64_t n,
+                     int dtype, const fkski_opts *opts, fkski_stats **out, void *stream);
+
+/* Sizes of a stats object (host outputs; any pointer may be NULL). */
+FKSKI_API int fkski_stats_info(const fkski_stats *st, fkski_grid *grid, int64_t *n, int64_t *m,
+                     int64_t *ncells, int *n_probes, double *yty, int *dtype);
+
+/* Copy statistics to host memory in FP64 (any pointer may be NULL):
+ * band 7^d x m with band[o*m + j] = (W^T W)[j, j + delta(o)], o = sum_k (delta_k + 3) 7^(d-1-k);
+ * wty m; wtz n_probes x m; ztz n_probes.  Synchronizes the stream. */
+FKSKI_API int fkski_stats_export(const fkski_stats *st, double *band, double *wty, double *wtz, double *ztz,
+                       void *stream);
+
+/* Copy the cell sort to host memory: keys[i] = linear cell index of point i (C order over
+ * cells c_k - 1 in [0, M_k - 4]); perm = stable sort of points by key; offsets[c]..offsets[c+1]
+ * is cell c's segment (ncells + 1 entries).  Needs opts.keep_sort at precompute time
+ * (else UNSUPPORTED).  Synchronizes the stream. */
+FKSKI_API int fkski_stats_export_sort(const fkski_stats *st, uint32_t *keys, int64_t *perm, int64_t *offsets,
+                            void *stream);
+
+/* Save / load the statistics (the paper's "computed once and saved to disk", Sec. 5). */
+FKSKI_API int fkski_stats_save(const fkski_stats *st, const char *path, void *stream);
+FKSKI_API int fkski_stats_load(const char *path, fkski_stats **out, void *stream);
+
+/* Release a stats object and all its device memory (NULL is a no-op). */
+FKSKI_API void fkski_destroy(fkski_stats *st);
+
+/* ------------------------------------------------------------------ operators (Sec. 2.2, 3.2)
+ * K_G V for nrhs grid vectors (device, rhs-major, dtype), or its derivative w.r.t. one
+ * hyperparameter: param = -1 for K_G, k in [0, d) for dK_G/dl_k, d for dK_G/ds.
+ * RBF: Kronecker product of symmetric Toeplitz factors, one batched circulant-embedding FFT pass
+ * per axis (Sec. 2.2; Lee 1986).  Matern-5/2: d-level circulant embedding (multilevel Toeplitz).
+ * The spectra are recomputed on every call; in and out must not alias.  UNSUPPORTED if the
+ * embedding of some axis exceeds 4096 points.  Synchronizes the stream (temporaries are freed). */
+FKSKI_API int fkski_kg_mvm(const fkski_grid *grid, const fkski_kernel *kern, int param, const void *v,
+                 void *out, int nrhs, int dtype, void *stream);
+
+/* u = (W^T W) x for nrhs grid vectors (device, rhs-major, dtype) from the stored band
+ * (Claim 2: O(m 7^d)). */
+FKSKI_API int fkski_band_mvm(const fkski_stats *st, const void *x, void *u, int nrhs, int dtype, void *stream);
+
+/* ------------------------------------------------------------------ posterior mean (Sec. 4, App. B)
+ * Solves the SKI system (W K_G W^T + sigma^2 I) z = y by factorized CG using only the sufficient
+ * statistics: Alg. 5 (x0 = y/sigma^2) or Alg. 3 (x0 = 0), one B(x) = [(K_G W^T W + sigma^2 I)x,
+ * W^T W x] per iteration.  Outputs (device, m entries, FP32 for MIXED / FP64 for DOUBLE):
+ *   a_out = W^T z   and   v_out = K_G W^T z  (= z_bar, the GSGP posterior mean of theta, Fact 2).
+ * Stops when ||r_k|| <= rtol ||y||.  info (host, may be NULL) receives iterations and residual.
+ * Returns OK, NOT_CONVERGED (outputs written), BREAKDOWN, INVALID_ARG, OOM, CUDA.
+ * Synchronizes the stream every opts->check_every iterations to test convergence. */
+FKSKI_API int fkski_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, void *a_out,
+                void *v_out, fkski_info *info, void *stream);
+
+/* Posterior mean at test points: mu(x*) = w_{x*}^T v (Def. 1 mean with v = K_G W^T z; Fact 2).
+ * v device m (vdtype); Xstar device d x nstar (xdtype); mu_out device nstar (vdtype).
+ * Errors: OUT_OF_GRID / NONFINITE for a test point (mu for other points still written). */
+FKSKI_API int fkski_predict(const fkski_stats *st, const void *v, int vdtype, const void *Xstar, int xdtype,
+                  int64_t nstar, void *mu_out, void *stream);
+
+/* ------------------------------------------------------------------ log-likelihood and gradient
+ * Log marginal likelihood of Def. 1, L = -1/2 [logdet(A) + y^T A^{-1} y + n log 2pi] with
+ * A = W K_G W^T + sigma^2 I, from sufficient statistics only:
+ *   - batched factorized CG (Alg. 3, x0 = 0) on [y, z_1..z_T] sharing each B(x) application;
+ *   - logdet(A) by stochastic Lanczos quadrature over the probes, with the Lanczos tridiagonal
+ *     formed from the CG coefficients (Sec. 2.1 "Inference via iterative methods");
+ *   - y^T A^{-1} y = (W^T y)^T x_hat + c^x y^T y from the compressed solution.
+ * Gradient w.r.t. theta = (l_1..l_d, s, sigma^2) (the paper's "further trace computation",
+ * Sec. 2.1):
+ *   dL/dtheta   = 1/2 a^T dK a - 1/2 mean_p (W^T x_p)^T dK (W^T z_p),   a = W^T A^{-1} y
+ *   dL/dsigma^2 = 1/2 ||A^{-1} y||^2 - 1/2 mean_p z_p^T x_p,              x_p = A^{-1} z_p
+ * with dK applied by derivative-Toeplitz circulant-embedding MVMs.  Requires n_probes >= 1 at
+ * precompute time.  loglik_out: host double; grad_out: host double[d + 2].
+ * fkski_loglik_forward keeps the solutions in the stats workspace when
+ * (T + 1) * m * sizeof(vector) * 2 <= opts->iterate_budget_bytes; fkski_loglik_backward reuses
+ * them, or reruns the (deterministic) forward solves when they were not kept.
+ * All three synchronize the stream.  info (host, may be NULL) gets per-rhs iteration counts. */
+FKSKI_API int fkski_loglik_forward(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts,
+                         double *loglik_out, fkski_info *info, void *stream);
+FKSKI_API int fkski_loglik_backward(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts,
+                          double *grad_out, fkski_info *info, void *stream);
+FKSKI_API int fkski_grad(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts,
+               double *loglik_out, double *grad_out, fkski_info *info, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FKSKI_H */

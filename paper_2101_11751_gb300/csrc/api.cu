@@ -1,0 +1,266 @@
+// C ABI of libfkski.so (declared in include/fkski.h): argument checks, stream plumbing, the stats
+// object's lifetime, export and save/load.  All compute lives in the other translation units.
+#include "fkski_internal.cuh"
+
+#include <cstdio>
+#include <vector>
+
+namespace fk {
+
+void destroy_stats(fkski_stats *st) {
+    if (!st) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (st->device != cur) cudaSetDevice(st->device);
+    free_solve_work(st->work);
+    void *ptrs[] = {st->band, st->wty, st->wtz, st->band_alt, st->wty_alt, st->wtz_alt, st->keys, st->perm, st->offsets};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (st->device != cur) cudaSetDevice(cur);
+    delete st;
+}
+
+static cudaStream_t S(void *stream) { return reinterpret_cast<cudaStream_t>(stream); }
+
+}  // namespace fk
+
+using namespace fk;
+
+extern "C" {
+
+void fkski_default_opts(fkski_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->rtol = 1e-6;
+    o->maxiter = 1000;
+    o->x0_mode = FKSKI_X0_Y_OVER_S2;
+    o->precision = FKSKI_MIXED;
+    o->check_every = 16;
+    o->n_probes = 0;
+    o->probe_seed = 0;
+    o->iterate_budget_bytes = (size_t)1 << 30;
+    o->keep_sort = 0;
+}
+
+const char *fkski_strerror(int st) {
+    switch (st) {
+        case FKSKI_OK: return "ok";
+        case FKSKI_E_INVALID_ARG: return "invalid argument";
+        case FKSKI_E_OUT_OF_GRID: return "point outside the grid interior [1, M-2]";
+        case FKSKI_E_NONFINITE: return "non-finite input";
+        case FKSKI_E_NOT_CONVERGED: return "CG did not converge within maxiter";
+        case FKSKI_E_BREAKDOWN: return "CG breakdown (non-positive curvature or non-finite inner product)";
+        case FKSKI_E_TIMEOUT: return "bounded device wait gave up";
+        case FKSKI_E_OOM: return "device out of memory";
+        case FKSKI_E_CUDA: return "CUDA runtime error";
+        case FKSKI_E_UNSUPPORTED: return "size not supported by this build";
+        case FKSKI_E_IO: return "file error";
+        default: return "unknown status";
+    }
+}
+
+int fkski_precompute(const fkski_grid *grid, const void *X, const void *y, const void *Z, int64_t n, int dtype,
+                     const fkski_opts *opts, fkski_stats **out, void *stream) {
+    return precompute_impl(grid, X, y, Z, n, dtype, opts, out, S(stream));
+}
+
+int fkski_stats_info(const fkski_stats *st, fkski_grid *grid, int64_t *n, int64_t *m, int64_t *ncells, int *n_probes,
+                     double *yty, int *dtype) {
+    if (!st) return FKSKI_E_INVALID_ARG;
+    if (grid) *grid = st->grid;
+    if (n) *n = st->n;
+    if (m) *m = st->m;
+    if (ncells) *ncells = st->ncells;
+    if (n_probes) *n_probes = st->nprobes;
+    if (yty) *yty = st->yty;
+    if (dtype) *dtype = st->dtype;
+    return FKSKI_OK;
+}
+
+static int copy_to_host_f64(const void *src, int dtype, int64_t count, double *dst, cudaStream_t s) {
+    if (!dst || count == 0) return FKSKI_OK;
+    if (dtype == FKSKI_F64) {
+        FK_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+        FK_CUDA(cudaStreamSynchronize(s));
+        return FKSKI_OK;
+    }
+    std::vector<float> tmp((size_t)count);
+    FK_CUDA(cudaMemcpyAsync(tmp.data(), src, sizeof(float) * count, cudaMemcpyDeviceToHost, s));
+    FK_CUDA(cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < count; ++i) dst[i] = (double)tmp[(size_t)i];
+    return FKSKI_OK;
+}
+
+int fkski_stats_export(const fkski_stats *st, double *band, double *wty, double *wtz, double *ztz, void *stream) {
+    if (!st) return FKSKI_E_INVALID_ARG;
+    const cudaStream_t s = S(stream);
+    FK_TRY(copy_to_host_f64(st->band, st->dtype, ipow(7, st->d) * st->m, band, s));
+    FK_TRY(copy_to_host_f64(st->wty, st->dtype, st->m, wty, s));
+    if (st->nprobes > 0) FK_TRY(copy_to_host_f64(st->wtz, st->dtype, st->nprobes * st->m, wtz, s));
+    if (ztz)
+        for (int p = 0; p < st->nprobes; ++p) ztz[p] = st->ztz[p];
+    return FKSKI_OK;
+}
+
+int fkski_stats_export_sort(const fkski_stats *st, uint32_t *keys, int64_t *perm, int64_t *offsets, void *stream) {
+    if (!st) return FKSKI_E_INVALID_ARG;
+    if (!st->keys || !st->perm || !st->offsets) return FKSKI_E_UNSUPPORTED;
+    const cudaStream_t s = S(stream);
+    if (keys) FK_CUDA(cudaMemcpyAsync(keys, st->keys, sizeof(uint32_t) * st->n, cudaMemcpyDeviceToHost, s));
+    std::vector<uint32_t> tmp;
+    if (perm) {
+        tmp.resize((size_t)st->n);
+        FK_CUDA(cudaMemcpyAsync(tmp.data(), st->perm, sizeof(uint32_t) * st->n, cudaMemcpyDeviceToHost, s));
+        FK_CUDA(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < st->n; ++i) perm[i] = tmp[(size_t)i];
+    }
+    if (offsets) {
+        tmp.resize((size_t)(st->ncells + 1));
+        FK_CUDA(cudaMemcpyAsync(tmp.data(), st->offsets, sizeof(uint32_t) * (st->ncells + 1), cudaMemcpyDeviceToHost, s));
+        FK_CUDA(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i <= st->ncells; ++i) offsets[i] = tmp[(size_t)i];
+    }
+    FK_CUDA(cudaStreamSynchronize(s));
+    return FKSKI_OK;
+}
+
+// File layout: magic "FKSKI01\0", then the fixed header, then band, wty, wtz in the stats dtype.
+struct SaveHeader {
+    char magic[8];
+    fkski_grid grid;
+    int32_t d, dtype, nprobes, pad;
+    int64_t n, m, ncells;
+    uint64_t seed;
+    double yty;
+    double ztz[kMaxProbes];
+};
+
+int fkski_stats_save(const fkski_stats *st, const char *path, void *stream) {
+    if (!st || !path) return FKSKI_E_INVALID_ARG;
+    const cudaStream_t s = S(stream);
+    SaveHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "FKSKI01", 8);
+    h.grid = st->grid;
+    h.d = st->d;
+    h.dtype = st->dtype;
+    h.nprobes = st->nprobes;
+    h.n = st->n;
+    h.m = st->m;
+    h.ncells = st->ncells;
+    h.seed = st->probe_seed;
+    h.yty = st->yty;
+    for (int p = 0; p < kMaxProbes; ++p) h.ztz[p] = st->ztz[p];
+    const size_t es = st->dtype == FKSKI_F32 ? 4 : 8;
+    const size_t nb = (size_t)ipow(7, st->d) * st->m;
+    std::vector<char> buf(es * (nb + st->m + (size_t)st->nprobes * st->m));
+    FK_CUDA(cudaMemcpyAsync(buf.data(), st->band, es * nb, cudaMemcpyDeviceToHost, s));
+    FK_CUDA(cudaMemcpyAsync(buf.data() + es * nb, st->wty, es * st->m, cudaMemcpyDeviceToHost, s));
+    if (st->nprobes)
+        FK_CUDA(cudaMemcpyAsync(buf.data() + es * (nb + st->m), st->wtz, es * st->nprobes * st->m, cudaMemcpyDeviceToHost, s));
+    FK_CUDA(cudaStreamSynchronize(s));
+    FILE *f = fopen(path, "wb");
+    if (!f) return FKSKI_E_IO;
+    bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? FKSKI_OK : FKSKI_E_IO;
+}
+
+int fkski_stats_load(const char *path, fkski_stats **out, void *stream) {
+    if (!path || !out) return FKSKI_E_INVALID_ARG;
+    *out = nullptr;
+    const cudaStream_t s = S(stream);
+    FILE *f = fopen(path, "rb");
+    if (!f) return FKSKI_E_IO;
+    SaveHeader h;
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, "FKSKI01", 8) != 0 || h.d < 1 || h.d > 3 ||
+        (h.dtype != FKSKI_F32 && h.dtype != FKSKI_F64) || h.nprobes < 0 || h.nprobes > kMaxProbes || h.m < 1) {
+        fclose(f);
+        return FKSKI_E_IO;
+    }
+    const size_t es = h.dtype == FKSKI_F32 ? 4 : 8;
+    const size_t nb = (size_t)ipow(7, h.d) * h.m;
+    std::vector<char> buf(es * (nb + h.m + (size_t)h.nprobes * h.m));
+    const bool ok = fread(buf.data(), 1, buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok) return FKSKI_E_IO;
+    fkski_stats *st = new fkski_stats;
+    memset(st, 0, sizeof(*st));
+    st->grid = h.grid;
+    st->d = h.d;
+    st->dtype = h.dtype;
+    st->n = h.n;
+    st->m = h.m;
+    st->ncells = h.ncells;
+    st->nprobes = h.nprobes;
+    st->probe_seed = h.seed;
+    st->yty = h.yty;
+    for (int p = 0; p < kMaxProbes; ++p) st->ztz[p] = h.ztz[p];
+    cudaGetDevice(&st->device);
+    int rc = FKSKI_OK;
+    if (cudaMalloc(&st->band, es * nb) != cudaSuccess || cudaMalloc(&st->wty, es * h.m) != cudaSuccess ||
+        (h.nprobes && cudaMalloc(&st->wtz, es * h.nprobes * h.m) != cudaSuccess)) {
+        cudaGetLastError();
+        rc = FKSKI_E_OOM;
+    }
+    if (rc == FKSKI_OK) {
+        if (cudaMemcpyAsync(st->band, buf.data(), es * nb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(st->wty, buf.data() + es * nb, es * h.m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            (h.nprobes && cudaMemcpyAsync(st->wtz, buf.data() + es * (nb + h.m), es * h.nprobes * h.m,
+                                          cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            rc = FKSKI_E_CUDA;
+    }
+    if (rc != FKSKI_OK) {
+        destroy_stats(st);
+        return rc;
+    }
+    *out = st;
+    return FKSKI_OK;
+}
+
+void fkski_destroy(fkski_stats *st) { destroy_stats(st); }
+
+int fkski_kg_mvm(const fkski_grid *grid, const fkski_kernel *kern, int param, const void *v, void *out, int nrhs,
+                 int dtype, void *stream) {
+    return kg_mvm_impl(grid, kern, param, v, out, nrhs, dtype, S(stream));
+}
+
+int fkski_band_mvm(const fkski_stats *st, const void *x, void *u, int nrhs, int dtype, void *stream) {
+    return band_mvm_impl(st, x, u, nrhs, dtype, S(stream));
+}
+
+int fkski_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, void *a_out, void *v_out,
+                fkski_info *info, void *stream) {
+    return solve_impl(st, kern, opts, a_out, v_out, info, S(stream));
+}
+
+int fkski_predict(const fkski_stats *st, const void *v, int vdtype, const void *Xstar, int xdtype, int64_t nstar,
+                  void *mu_out, void *stream) {
+    return predict_impl(st, v, vdtype, Xstar, xdtype, nstar, mu_out, S(stream));
+}
+
+int fkski_loglik_forward(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, double *loglik_out,
+                         fkski_info *info, void *stream) {
+    return loglik_forward_impl(st, kern, opts, loglik_out, info, S(stream));
+}
+
+int fkski_loglik_backward(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, double *grad_out,
+                          fkski_info *info, void *stream) {
+    return loglik_backward_impl(st, kern, opts, grad_out, info, S(stream));
+}
+
+int fkski_grad(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, double *loglik_out,
+               double *grad_out, fkski_info *info, void *stream) {
+    fkski_opts o;
+    if (opts) o = *opts; else fkski_default_opts(&o);
+    o.iterate_budget_bytes = (size_t)-1;
+    double L = 0.0;
+    int rc = loglik_forward_impl(st, kern, &o, &L, info, S(stream));
+    if (rc != FKSKI_OK && rc != FKSKI_E_NOT_CONVERGED) return rc;
+    if (loglik_out) *loglik_out = L;
+    const int rb = loglik_backward_impl(st, kern, &o, grad_out, nullptr, S(stream));
+    return rb != FKSKI_OK ? rb : rc;
+}
+
+}  // extern "C"

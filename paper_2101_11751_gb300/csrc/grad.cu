@@ -1,0 +1,372 @@
+// Log marginal likelihood (Def. 1) and its gradient w.r.t. (l_1..l_d, s, sigma^2) from the
+// sufficient statistics only.
+//
+//   L = -1/2 [ logdet A + y^T A^{-1} y + n log 2 pi ],   A = W K_G W^T + sigma^2 I.
+// Solves: batched factorized CG (Alg. 3, x0 = 0) on [y, z_1..z_T], z_p the Rademacher probes
+// whose W^T z_p the precompute accumulated.  From the compressed solution x = W x_hat + c^x b:
+//   W^T x = W^T W x_hat + c^x W^T b     (x_hat_d = W^T W x_hat is carried by the recurrence)
+//   b^T x = (W^T b)^T x_hat + c^x b^T b
+// logdet A by stochastic Lanczos quadrature: each probe's CG coefficients give the Lanczos
+// tridiagonal T_p (T[0,0] = 1/a_0, T[i,i] = 1/a_i + b_{i-1}/a_{i-1}, T[i,i+1] = sqrt(b_i)/a_i) and
+//   z_p^T log(A) z_p ~ ||z_p||^2 e_1^T log(T_p) e_1,
+// evaluated from the eigen-decomposition of T_p (implicit-shift QL, first eigenvector row only).
+// Gradient (Hutchinson traces with the same probes):
+//   dL/dtheta   = 1/2 a^T dK a - 1/2 mean_p (W^T x_p)^T dK (W^T z_p),  a = W^T A^{-1} y
+//   dL/dsigma^2 = 1/2 ||A^{-1} y||^2 - 1/2 mean_p z_p^T x_p,
+//   ||A^{-1} y||^2 = (y^T y - 2 (W^T y)^T K a + (K a)^T W^T W (K a)) / sigma^4
+// since A^{-1} y = (y - W K a) / sigma^2.
+#include "fkski_internal.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace fk {
+
+template <typename T>
+struct Alg3Vecs {
+    T *r, *p, *x, *xd, *u, *v, *s, *z, *g, *kg;
+};
+int alg3_for_grad_f32(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, Alg3Vecs<float> &V,
+                      int *iters, double *res, int *status, cudaStream_t s);
+int alg3_for_grad_f64(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, Alg3Vecs<double> &V,
+                      int *iters, double *res, int *status, cudaStream_t s);
+
+// The solve workspace layout is private to solve.cu; grad.cu reaches it through these.
+struct GradView {
+    double *S;        // per-rhs fields (solve.cu enum)
+    double *hist_a;   // alpha history [k * R + r]
+    double *hist_b;   // beta history
+    int *iters;       // device per-rhs counts
+    KgOp *kg;
+};
+int grad_view(fkski_stats *st, int dtype, GradView *gv);
+int grad_sol_buffer(fkski_stats *st, size_t bytes, void **p);
+void grad_sol_mark(fkski_stats *st, int valid, const fkski_kernel *kern, int dtype);
+int grad_sol_valid(fkski_stats *st, const fkski_kernel *kern, int dtype);
+constexpr int GF_CX = 6, GF_RHO0 = 7;  // must match solve.cu's field enum
+int spmv_for_grad(fkski_stats *st, const void *x, void *u, int R, int dtype, cudaStream_t s);
+
+// ------------------------------------------------------------------ SLQ
+// One block per probe; thread 0 runs the implicit QL iteration on the k x k tridiagonal (FP64)
+// while carrying the first row of the eigenvector matrix.  Output est[p] = rho0 sum_l z_l^2 log lam_l.
+constexpr int SLQ_MAXK = 4096;
+
+__global__ void k_slq(const double *__restrict__ ha, const double *__restrict__ hb, const int *__restrict__ iters,
+                      const double *__restrict__ S, int R, int nf, double *__restrict__ est, int *__restrict__ status) {
+    extern __shared__ double sm[];
+    const int r = 1 + blockIdx.x;  // probe rhs
+    const int k = iters[r];
+    double *dg = sm;           // diagonal
+    double *of = sm + k + 1;   // off-diagonal (of[i] couples i, i+1)
+    double *z = of + k + 1;    // first eigenvector row
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const double a = ha[(int64_t)i * R + r];
+        double di = 1.0 / a;
+        if (i > 0) di += hb[(int64_t)(i - 1) * R + r] / ha[(int64_t)(i - 1) * R + r];
+        dg[i] = di;
+        of[i] = (i + 1 < k) ? sqrt(hb[(int64_t)i * R + r]) / a : 0.0;
+        z[i] = (i == 0) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double rho0 = S[GF_RHO0 * R + r];
+    if (k == 0) {
+        est[blockIdx.x] = 0.0;
+        return;
+    }
+    const double eps = 2.220446049250313e-16;
+    int fail = 0;
+    for (int l = 0; l < k; ++l) {
+        for (int guard = 0; guard < 60; ++guard) {
+            // smallest m >= l with a negligible coupling below it
+            int mm = l;
+            while (mm < k - 1 && fabs(of[mm]) > eps * (fabs(dg[mm]) + fabs(dg[mm + 1]))) ++mm;
+            if (mm == l) break;
+            if (guard == 59) { fail = 1; break; }
+            // Wilkinson-type shift from the leading 2x2 block at l
+            double gq = (dg[l + 1] - dg[l]) / (2.0 * of[l]);
+            double rr = hypot(gq, 1.0);
+            gq = dg[mm] - dg[l] + of[l] / (gq + (gq >= 0.0 ? rr : -rr));
+            double sn = 1.0, cs = 1.0, pp = 0.0;
+            int i = mm - 1;
+            bool early = false;
+            for (; i >= l; --i) {
+                const double f = sn * of[i], b = cs * of[i];
+                rr = hypot(f, gq);
+                of[i + 1] = rr;
+                if (rr == 0.0) {
+                    dg[i + 1] -= pp;
+                    of[mm] = 0.0;
+                    early = true;
+                    break;
+                }
+                sn = f / rr;
+                cs = gq / rr;
+                gq = dg[i + 1] - pp;
+                rr = (dg[i] - gq) * sn + 2.0 * cs * b;
+                pp = sn * rr;
+                dg[i + 1] = gq + pp;
+                gq = cs * rr - b;
+                const double zf = z[i + 1];
+                z[i + 1] = sn * z[i] + cs * zf;
+                z[i] = cs * z[i] - sn * zf;
+            }
+            if (early) continue;
+            dg[l] -= pp;
+            of[l] = gq;
+            of[mm] = 0.0;
+        }
+    }
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) {
+        if (!(dg[i] > 0.0)) fail = 1;
+        else acc += z[i] * z[i] * log(dg[i]);
+    }
+    if (fail) atomicOr(status, ST_BREAKDOWN);
+    est[blockIdx.x] = rho0 * acc;
+}
+
+// dots of row pairs: out[r] = sum_i a[r][i] b[r][i]; per-block FP64 partials then a fixed-order sum
+template <typename T>
+__global__ void __launch_bounds__(256) k_rowdots(const T *__restrict__ a, const T *__restrict__ b, int64_t m, int R,
+                                                 double *__restrict__ part) {
+    __shared__ double sh[8];
+    for (int r = 0; r < R; ++r) {
+        T acc = T(0);
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+            acc = fma(a[(int64_t)r * m + j], b[(int64_t)r * m + j], acc);
+        double dv = (double)acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dv += __shfl_xor_sync(0xFFFFFFFFu, dv, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dv;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < 8; ++w) s += sh[w];
+            part[(int64_t)blockIdx.x * R + r] = s;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_sum_rows(const double *__restrict__ part, int nb, int R, double *__restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * R + r];
+    out[r] = s;
+}
+
+constexpr int RD_BLOCKS = 304;
+
+template <typename T>
+static int rowdots(const T *a, const T *b, int64_t m, int R, double *part, double *out, cudaStream_t s) {
+    k_rowdots<T><<<RD_BLOCKS, 256, 0, s>>>(a, b, m, R, part);
+    FK_LAUNCH();
+    k_sum_rows<<<(unsigned)cdiv(R, 64), 64, 0, s>>>(part, RD_BLOCKS, R, out);
+    FK_LAUNCH();
+    return FKSKI_OK;
+}
+
+template <typename T>
+__global__ void k_wtx(const T *__restrict__ xd, const T *__restrict__ g, const double *__restrict__ S, int R, int64_t m,
+                      T *__restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / m);
+        out[e] = fma((T)S[GF_CX * R + r], g[e], xd[e]);
+    }
+}
+
+// Forward scalars.  fs layout: [0] L, [1] logdet, [2] quad, [3..3+R) z_p^T x_p (index 0 unused)
+__global__ void k_loglik_assemble(const double *__restrict__ S, const double *__restrict__ gx,
+                                  const double *__restrict__ est, int R, double n, double *__restrict__ fs) {
+    if (threadIdx.x != 0) return;
+    const double quad = gx[0] + S[GF_CX * R + 0] * S[GF_RHO0 * R + 0];
+    double ld = 0.0;
+    for (int p = 1; p < R; ++p) ld += est[p - 1];
+    ld /= (double)(R - 1);
+    fs[0] = -0.5 * (ld + quad + n * log(2.0 * 3.14159265358979323846));
+    fs[1] = ld;
+    fs[2] = quad;
+    for (int p = 1; p < R; ++p) fs[3 + p] = gx[p] + S[GF_CX * R + p] * S[GF_RHO0 * R + p];
+}
+
+// grad[t] for kernel params from dots dd[t*R + r] = sol[r] . dK_t src[r]
+__global__ void k_grad_assemble(const double *__restrict__ dd, int nth, int R, const double *__restrict__ fs,
+                                const double *__restrict__ s2dots, double yty, double sig2, double *__restrict__ grad) {
+    if (threadIdx.x != 0) return;
+    const int T = R - 1;
+    for (int t = 0; t < nth; ++t) {
+        double tr = 0.0;
+        for (int p = 1; p < R; ++p) tr += dd[t * R + p];
+        grad[t] = 0.5 * dd[t * R + 0] - 0.5 * tr / (double)T;
+    }
+    // sigma^2: s2dots[0] = (W^T y).(K a), s2dots[1] = (K a).(W^T W K a)
+    const double zz = (yty - 2.0 * s2dots[0] + s2dots[1]) / (sig2 * sig2);
+    double tr = 0.0;
+    for (int p = 1; p < R; ++p) tr += fs[3 + p];
+    grad[nth] = 0.5 * zz - 0.5 * tr / (double)T;
+}
+
+template <typename T>
+__global__ void k_copy_rows(const T *__restrict__ a, const T *__restrict__ wtz, int64_t m, int R, T *__restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = e < m ? a[e] : wtz[e - m];
+}
+
+// ------------------------------------------------------------------ forward
+// Buffers kept between forward and backward (in the stats' solution slot):
+//   sol[0..R) : a = W^T A^{-1} y, then W^T x_p (R x m)
+//   fs        : forward scalars (see k_loglik_assemble), 3 + R doubles
+template <typename T>
+static int forward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, double *L, fkski_info *info,
+                         cudaStream_t s) {
+    const int R = 1 + st->nprobes;
+    const int64_t m = st->m;
+    const int dt = sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64;
+    Alg3Vecs<T> V;
+    std::vector<int> it(R, 0);
+    std::vector<double> res(R, 0.0);
+    int status = FKSKI_OK;
+    if (sizeof(T) == 4)
+        FK_TRY(alg3_for_grad_f32(st, kern, o, R, reinterpret_cast<Alg3Vecs<float> &>(V), it.data(), res.data(), &status, s));
+    else
+        FK_TRY(alg3_for_grad_f64(st, kern, o, R, reinterpret_cast<Alg3Vecs<double> &>(V), it.data(), res.data(), &status, s));
+    GradView gv;
+    FK_TRY(grad_view(st, dt, &gv));
+    // solution slot: sol (R x m) + fs (3 + R + 64) + scratch partials
+    const size_t sol_bytes = sizeof(T) * (size_t)R * m;
+    const size_t need = sol_bytes + sizeof(double) * (size_t)(3 + R + 64 + R + RD_BLOCKS * R + 16);
+    void *slot;
+    FK_TRY(grad_sol_buffer(st, need, &slot));
+    T *sol = (T *)slot;
+    double *fs = (double *)((char *)slot + sol_bytes);
+    double *gx = fs + 3 + R + 64;
+    double *part = gx + R;
+    double *est = (double *)V.u;  // free after the solve: reuse as scratch (R doubles)
+    int *dstat;
+    FK_CUDA(cudaMallocAsync((void **)&dstat, sizeof(int), s));
+    FK_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int), s));
+    const unsigned gb = (unsigned)std::min<int64_t>(cdiv((int64_t)R * m, 256), 152 * 8);
+    k_wtx<T><<<gb, 256, 0, s>>>(V.xd, V.g, gv.S, R, m, sol);
+    FK_LAUNCH();
+    FK_TRY(rowdots<T>(V.g, V.x, m, R, part, gx, s));
+    int kmax = 0;
+    for (int r = 1; r < R; ++r) kmax = std::max(kmax, it[r]);
+    if (kmax > SLQ_MAXK) return FKSKI_E_UNSUPPORTED;
+    const size_t slq_sm = sizeof(double) * 3 * (size_t)(kmax + 1);
+    if (slq_sm > 48 * 1024) FK_CUDA(cudaFuncSetAttribute(k_slq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slq_sm));
+    k_slq<<<R - 1, 128, slq_sm, s>>>(gv.hist_a, gv.hist_b, gv.iters, gv.S, R, 0, est, dstat);
+    FK_LAUNCH();
+    k_loglik_assemble<<<1, 32, 0, s>>>(gv.S, gx, est, R, (double)st->n, fs);
+    FK_LAUNCH();
+    int hst = 0;
+    FK_CUDA(cudaMemcpyAsync(L, fs, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FK_CUDA(cudaMemcpyAsync(&hst, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FK_CUDA(cudaFreeAsync(dstat, s));
+    FK_CUDA(cudaStreamSynchronize(s));
+    if (info) {
+        info->iters = 0;
+        info->rel_residual = 0.0;
+        for (int r = 0; r < R && r < 65; ++r) {
+            info->iters_rhs[r] = it[r];
+            info->iters = std::max(info->iters, it[r]);
+            info->rel_residual = std::max(info->rel_residual, res[r]);
+        }
+        info->status = status;
+    }
+    const bool keep = 2 * sol_bytes <= o->iterate_budget_bytes;
+    grad_sol_mark(st, keep ? 1 : 0, kern, dt);
+    if (hst & ST_BREAKDOWN) return FKSKI_E_BREAKDOWN;
+    return status;
+}
+
+// ------------------------------------------------------------------ backward
+template <typename T>
+static int backward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, double *grad,
+                          fkski_info *info, cudaStream_t s) {
+    const int dt = sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64;
+    if (!grad_sol_valid(st, kern, dt)) {
+        double Ltmp;
+        fkski_opts o2 = *o;
+        o2.iterate_budget_bytes = (size_t)-1;  // keep for this backward pass
+        const int rc = forward_typed<T>(st, kern, &o2, &Ltmp, info, s);
+        if (rc != FKSKI_OK && rc != FKSKI_E_NOT_CONVERGED) return rc;
+    }
+    const int R = 1 + st->nprobes;
+    const int64_t m = st->m;
+    const int d = st->d;
+    GradView gv;
+    FK_TRY(grad_view(st, dt, &gv));
+    void *slot;
+    const size_t sol_bytes = sizeof(T) * (size_t)R * m;
+    FK_TRY(grad_sol_buffer(st, 0, &slot));
+    T *sol = (T *)slot;
+    double *fs = (double *)((char *)slot + sol_bytes);
+    double *gx = fs + 3 + R + 64;
+    double *part = gx + R;
+    const void *bandv, *wtyv, *wtzv;
+    FK_TRY(stats_band_as(st, dt, &bandv, &wtyv, &wtzv, s));
+    const T *wty = (const T *)wtyv, *wtz = (const T *)wtzv;
+    T *src, *dK;
+    double *dd;
+    FK_CUDA(cudaMallocAsync((void **)&src, 2 * sol_bytes, s));
+    dK = src + (size_t)R * m;
+    FK_CUDA(cudaMallocAsync((void **)&dd, sizeof(double) * ((d + 1) * R + 8 + 8), s));
+    double *s2dots = dd + (d + 1) * R;
+    double *dgrad = s2dots + 4;
+    const unsigned gb = (unsigned)std::min<int64_t>(cdiv((int64_t)R * m, 256), 152 * 8);
+    // src = [a, W^T z_1, ..., W^T z_T]
+    k_copy_rows<T><<<gb, 256, 0, s>>>(sol, wtz, m, R, src);
+    FK_LAUNCH();
+    KgOp *kg = gv.kg;
+    for (int t = 0; t <= d; ++t) {
+        FK_TRY(kgop_set(kg, kern, t, s));
+        FK_TRY(kgop_apply(kg, src, dK, R, nullptr, 0.0, s));
+        FK_TRY(rowdots<T>(sol, dK, m, R, part, dd + t * R, s));
+    }
+    // sigma^2 terms: v = K a, u = W^T W v
+    FK_TRY(kgop_set(kg, kern, -1, s));
+    FK_TRY(kgop_apply(kg, sol, dK, 1, nullptr, 0.0, s));
+    FK_TRY(spmv_for_grad(st, dK, dK + m, 1, dt, s));
+    FK_TRY(rowdots<T>(wty, dK, m, 1, part, s2dots, s));
+    FK_TRY(rowdots<T>(dK, dK + m, m, 1, part, s2dots + 1, s));
+    k_grad_assemble<<<1, 32, 0, s>>>(dd, d + 1, R, fs, s2dots, st->yty, kern->noise_var, dgrad);
+    FK_LAUNCH();
+    FK_CUDA(cudaMemcpyAsync(grad, dgrad, sizeof(double) * (d + 2), cudaMemcpyDeviceToHost, s));
+    FK_CUDA(cudaFreeAsync(src, s));
+    FK_CUDA(cudaFreeAsync(dd, s));
+    FK_CUDA(cudaStreamSynchronize(s));
+    (void)o;
+    return FKSKI_OK;
+}
+
+static int check_grad_args(fkski_stats *st, const fkski_kernel *kern, fkski_opts *o, const fkski_opts *opts) {
+    if (!st || !kern) return FKSKI_E_INVALID_ARG;
+    if (opts) *o = *opts; else fkski_default_opts(o);
+    if (st->nprobes < 1) return FKSKI_E_INVALID_ARG;
+    if (!(kern->noise_var > 0.0)) return FKSKI_E_INVALID_ARG;
+    if (o->maxiter < 1 || o->maxiter > SLQ_MAXK) return FKSKI_E_INVALID_ARG;
+    return FKSKI_OK;
+}
+
+int loglik_forward_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, double *L, fkski_info *info,
+                        cudaStream_t s) {
+    fkski_opts o;
+    FK_TRY(check_grad_args(st, kern, &o, opts));
+    if (!L) return FKSKI_E_INVALID_ARG;
+    if (info) memset(info, 0, sizeof(*info));
+    return o.precision == FKSKI_DOUBLE ? forward_typed<double>(st, kern, &o, L, info, s)
+                                       : forward_typed<float>(st, kern, &o, L, info, s);
+}
+
+int loglik_backward_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, double *grad,
+                         fkski_info *info, cudaStream_t s) {
+    fkski_opts o;
+    FK_TRY(check_grad_args(st, kern, &o, opts));
+    if (!grad) return FKSKI_E_INVALID_ARG;
+    return o.precision == FKSKI_DOUBLE ? backward_typed<double>(st, kern, &o, grad, info, s)
+                                       : backward_typed<float>(st, kern, &o, grad, info, s);
+}
+
+}  // namespace fk

@@ -1,0 +1,636 @@
+// K_G = K_UU on the regular grid: multilevel Toeplitz (Sec. 2.2, "SKI running time"), applied
+// through circulant embedding and FFTs (Lee 1986) in shared memory.
+//
+// RBF ARD factorises over axes, K_G = s T_1 (x) ... (x) T_d with T_k the symmetric Toeplitz
+// matrix of exp(-1/2 (delta h_k / l_k)^2): one batched pass per axis, each line zero-padded to
+// L_k = 2^ceil(log2(2 M_k - 1)), transformed, scaled by the real spectrum of the embedded
+// circulant, transformed back and cropped.  Two real lines ride in one complex FFT (real and
+// imaginary parts): the spectrum of a symmetric real circulant is real, so the two never mix.
+//
+// Matern-5/2 is not separable: the d-level embedding of k(delta_1 h_1, ..., delta_d h_d) on the
+// L_1 x ... x L_d torus has a real spectrum; vectors are packed in pairs into complex tensors and
+// transformed axis by axis (only the M-extent lines are transformed along each axis).
+//
+// FFT scheme: radix-2 decimation in frequency (natural order in, bit-reversed out), the
+// pointwise spectrum multiply in bit-reversed order, radix-2 decimation in time back (bit-reversed
+// in, natural out) -- no permutation pass.  Twiddles come from sincospi on the device.
+#include "fkski_internal.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace fk {
+
+template <typename T>
+struct Cx;
+template <>
+struct Cx<float> { using t = float2; };
+template <>
+struct Cx<double> { using t = double2; };
+
+template <typename T>
+__device__ __forceinline__ void sincospi_t(T x, T *s, T *c);
+template <>
+__device__ __forceinline__ void sincospi_t<float>(float x, float *s, float *c) { sincospif(x, s, c); }
+template <>
+__device__ __forceinline__ void sincospi_t<double>(double x, double *s, double *c) { sincospi(x, s, c); }
+
+constexpr int FFT_T = 256;
+constexpr int FFT_SMEM_CPLX = 4096;  // complex values of line data per CTA
+
+template <typename T>
+__device__ __forceinline__ void make_twiddles(typename Cx<T>::t *tw, int L) {
+    // tw[k] = exp(-2 pi i k / L), k < L/2
+    for (int k = threadIdx.x; k < L / 2; k += blockDim.x) {
+        T s, c;
+        sincospi_t<T>(T(2) * (T)k / (T)L, &s, &c);
+        tw[k].x = c;
+        tw[k].y = -s;
+    }
+}
+
+// In-place radix-2 DIF over `nl` lines of length L stored contiguously (line stride L).
+template <typename T>
+__device__ __forceinline__ void fft_dif(typename Cx<T>::t *x, int nl, int L, const typename Cx<T>::t *tw) {
+    using C = typename Cx<T>::t;
+    const int nbf = nl * (L >> 1);
+    const int lhalf = __ffs(L) - 2;  // log2(L/2)
+    for (int h = L >> 1; h >= 1; h >>= 1) {
+        const int tstep = L / (2 * h);
+        const int lh = __ffs(h) - 1;
+        for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
+            const int line = b >> lhalf, k = b & ((L >> 1) - 1);
+            const int j = k & (h - 1), blk = k >> lh;
+            C *xl = x + line * L + blk * 2 * h;
+            const C u = xl[j], v = xl[j + h];
+            const C w = tw[j * tstep];
+            const T dx = u.x - v.x, dy = u.y - v.y;
+            xl[j].x = u.x + v.x;
+            xl[j].y = u.y + v.y;
+            xl[j + h].x = dx * w.x - dy * w.y;
+            xl[j + h].y = dx * w.y + dy * w.x;
+        }
+        __syncthreads();
+    }
+}
+
+// In-place radix-2 DIT inverse (conjugate twiddles, no 1/L: folded into the spectrum).
+template <typename T>
+__device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L, const typename Cx<T>::t *tw) {
+    using C = typename Cx<T>::t;
+    const int nbf = nl * (L >> 1);
+    const int lhalf = __ffs(L) - 2;  // log2(L/2)
+    for (int h = 1; h < L; h <<= 1) {
+        const int tstep = L / (2 * h);
+        const int lh = __ffs(h) - 1;
+        for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
+            const int line = b >> lhalf, k = b & ((L >> 1) - 1);
+            const int j = k & (h - 1), blk = k >> lh;
+            C *xl = x + line * L + blk * 2 * h;
+            const C u = xl[j], v = xl[j + h];
+            const C w = tw[j * tstep];
+            // v * conj(w)
+            const T tx = v.x * w.x + v.y * w.y, ty = v.y * w.x - v.x * w.y;
+            xl[j].x = u.x + tx;
+            xl[j].y = u.y + ty;
+            xl[j + h].x = u.x - tx;
+            xl[j + h].y = u.y - ty;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ Kronecker (real) axis pass
+// Vector layout per rhs: [O][M][S] (axis of length M, S = product of later axes).
+// Real lines l = (r*O + o)*S + s; two consecutive lines form one complex line.
+struct RealPass {
+    int64_t nlines;  // R * O * S
+    int64_t S;       // inner stride
+    int M, L;
+    int Q;           // real lines per CTA (even)
+};
+
+template <typename T, bool EPI>
+__global__ void __launch_bounds__(FFT_T) k_kron_pass(const T *__restrict__ in, T *__restrict__ out, RealPass p,
+                                                      const T *__restrict__ lam_br, const T *__restrict__ addv,
+                                                      const double *__restrict__ alpha_dev, double alpha_host) {
+    using C = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *tw = reinterpret_cast<C *>(smraw);
+    C *x = tw + p.L / 2;
+    const int L = p.L, M = p.M, Q = p.Q;
+    const int nc = Q / 2;
+    make_twiddles<T>(tw, L);
+    const int64_t l0 = (int64_t)blockIdx.x * Q;
+    const int nq = (int)min((int64_t)Q, p.nlines - l0);
+    // zero padding region and odd partner
+    for (int e = threadIdx.x; e < nc * L; e += blockDim.x) {
+        x[e].x = T(0);
+        x[e].y = T(0);
+    }
+    __syncthreads();
+    // load: element (q, i), address base(l0+q) + i*S
+    const int64_t S = p.S;
+    for (int e = threadIdx.x; e < nq * M; e += blockDim.x) {
+        int q, i;
+        if (S == 1) { q = e / M; i = e % M; } else { q = e % nq; i = e / nq; }
+        const int64_t l = l0 + q;
+        const int64_t base = (l / S) * (int64_t)M * S + (l % S);
+        const T v = in[base + (int64_t)i * S];
+        if (q & 1) x[(q >> 1) * L + i].y = v; else x[(q >> 1) * L + i].x = v;
+    }
+    __syncthreads();
+    fft_dif<T>(x, nc, L, tw);
+    for (int e = threadIdx.x; e < nc * L; e += blockDim.x) {
+        const T lm = lam_br[e % L];
+        x[e].x *= lm;
+        x[e].y *= lm;
+    }
+    __syncthreads();
+    fft_dit_inv<T>(x, nc, L, tw);
+    const T alpha = EPI ? (alpha_dev ? (T)(*alpha_dev) : (T)alpha_host) : T(0);
+    for (int e = threadIdx.x; e < nq * M; e += blockDim.x) {
+        int q, i;
+        if (S == 1) { q = e / M; i = e % M; } else { q = e % nq; i = e / nq; }
+        const int64_t l = l0 + q;
+        const int64_t a = (l / S) * (int64_t)M * S + (l % S) + (int64_t)i * S;
+        T v = (q & 1) ? x[(q >> 1) * L + i].y : x[(q >> 1) * L + i].x;
+        if (EPI) v = fma(alpha, addv[a], v);
+        out[a] = v;
+    }
+}
+
+// ------------------------------------------------------------------ complex axis pass (BTTB)
+// Complex tensor with lines along one axis: line l = o*S + s, input extent Min, output extent
+// Mout along the axis (zero-pad to L on input, crop on output).  MODE 0: DIF forward,
+// 1: DIT inverse, 2: DIF -> multiply by lam[(k)*S + s] (bit-reversed k) -> DIT.
+struct CplxPass {
+    int64_t nlines, S;
+    int Min, Mout, L, Q;
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(FFT_T) k_cplx_pass(const typename Cx<T>::t *__restrict__ in, typename Cx<T>::t *__restrict__ out,
+                                                      CplxPass p, const T *__restrict__ lam) {
+    using C = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *tw = reinterpret_cast<C *>(smraw);
+    C *x = tw + p.L / 2;
+    const int L = p.L, Q = p.Q;
+    make_twiddles<T>(tw, L);
+    const int64_t l0 = (int64_t)blockIdx.x * Q;
+    const int nq = (int)min((int64_t)Q, p.nlines - l0);
+    const int64_t S = p.S;
+    for (int e = threadIdx.x; e < Q * L; e += blockDim.x) {
+        x[e].x = T(0);
+        x[e].y = T(0);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nq * p.Min; e += blockDim.x) {
+        int q, i;
+        if (S == 1) { q = e / p.Min; i = e % p.Min; } else { q = e % nq; i = e / nq; }
+        const int64_t l = l0 + q;
+        x[q * L + i] = in[(l / S) * (int64_t)p.Min * S + (l % S) + (int64_t)i * S];
+    }
+    __syncthreads();
+    if (MODE == 0 || MODE == 2) fft_dif<T>(x, Q, L, tw);
+    if (MODE == 2) {
+        for (int e = threadIdx.x; e < nq * L; e += blockDim.x) {
+            const int q = e / L, k = e % L;
+            const int64_t s = (l0 + q) % S;
+            const T lm = lam[(int64_t)k * S + s];
+            x[e].x *= lm;
+            x[e].y *= lm;
+        }
+        __syncthreads();
+    }
+    if (MODE == 1 || MODE == 2) fft_dit_inv<T>(x, Q, L, tw);
+    for (int e = threadIdx.x; e < nq * p.Mout; e += blockDim.x) {
+        int q, i;
+        if (S == 1) { q = e / p.Mout; i = e % p.Mout; } else { q = e % nq; i = e / nq; }
+        const int64_t l = l0 + q;
+        out[(l / S) * (int64_t)p.Mout * S + (l % S) + (int64_t)i * S] = x[q * L + i];
+    }
+}
+
+// pack real rhs pairs into complex tensors of shape (M_1..M_d) and unpack (with epilogue)
+template <typename T>
+__global__ void k_pack_pairs(const T *__restrict__ v, typename Cx<T>::t *__restrict__ z, int64_t m, int nrhs) {
+    const int npair = (nrhs + 1) / 2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)npair * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int pr = (int)(e / m);
+        const int64_t i = e % m;
+        typename Cx<T>::t c;
+        c.x = v[(int64_t)(2 * pr) * m + i];
+        c.y = (2 * pr + 1 < nrhs) ? v[(int64_t)(2 * pr + 1) * m + i] : T(0);
+        z[e] = c;
+    }
+}
+
+template <typename T>
+__global__ void k_unpack_pairs(const typename Cx<T>::t *__restrict__ z, T *__restrict__ out, int64_t m, int nrhs,
+                               const T *__restrict__ addv, const double *__restrict__ alpha_dev, double alpha_host) {
+    const T alpha = addv ? (alpha_dev ? (T)(*alpha_dev) : (T)alpha_host) : T(0);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nrhs * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / m);
+        const int64_t i = e % m;
+        const typename Cx<T>::t c = z[(int64_t)(r / 2) * m + i];
+        T v = (r & 1) ? c.y : c.x;
+        if (addv) v = fma(alpha, addv[e], v);
+        out[e] = v;
+    }
+}
+
+// ------------------------------------------------------------------ spectra
+// First column of the embedded circulant along one axis of length L: c[i] = k(delta(i) h)
+// with delta(i) = i for i < M, L - i for i > L - M, 0-weight slots otherwise.
+__device__ __forceinline__ int circ_delta(int i, int M, int L, bool &valid) {
+    if (i < M) { valid = true; return i; }
+    if (i > L - M) { valid = true; return L - i; }
+    valid = false;
+    return 0;
+}
+
+// Kronecker factor spectrum (one CTA): lam_br[k] = scale / L * DFT(c)[bitrev(k)] for the RBF
+// factor exp(-1/2 (delta h / l)^2) (or its derivative in l when deriv).
+template <typename T>
+__global__ void __launch_bounds__(FFT_T) k_spectrum_1d(T *__restrict__ lam_br, int M, int L, double h, double ell,
+                                                        int deriv, double scale) {
+    using C = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *tw = reinterpret_cast<C *>(smraw);
+    C *x = tw + L / 2;
+    make_twiddles<T>(tw, L);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        bool ok;
+        const int dl = circ_delta(i, M, L, ok);
+        double v = 0.0;
+        if (ok) {
+            const double r = (double)dl * h / ell;
+            v = exp(-0.5 * r * r);
+            if (deriv) v *= r * r / ell;
+        }
+        x[i].x = (T)v;
+        x[i].y = T(0);
+    }
+    __syncthreads();
+    fft_dif<T>(x, 1, L, tw);
+    for (int k = threadIdx.x; k < L; k += blockDim.x) lam_br[k] = (T)(scale / L) * x[k].x;
+}
+
+// d-level embedding values for a (possibly derivative) stationary kernel, written as a complex
+// tensor over the L-box (axis 0 outermost).  kind: 0 Matern-5/2, 1 RBF; deriv: -1 value,
+// k in [0,d) d/dl_k, d -> d/ds.
+struct EmbedParams {
+    int d;
+    int M[3], L[3];
+    double h[3], ell[3];
+    double s;
+    int kind, deriv;
+};
+
+template <typename T>
+__global__ void k_embed_values(typename Cx<T>::t *__restrict__ z, EmbedParams ep, int64_t N) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e;
+        double q = 0.0;
+        bool ok = true;
+        double dk2[3] = {0, 0, 0};
+        for (int k = ep.d - 1; k >= 0; --k) {
+            const int i = (int)(r % ep.L[k]);
+            r /= ep.L[k];
+            bool v;
+            const int dl = circ_delta(i, ep.M[k], ep.L[k], v);
+            ok = ok && v;
+            const double u = (double)dl * ep.h[k] / ep.ell[k];
+            dk2[k] = u * u / ep.ell[k];
+            q += u * u;
+        }
+        double val = 0.0;
+        if (ok) {
+            if (ep.kind == 0) {
+                const double rr = sqrt(q), s5 = sqrt(5.0);
+                if (ep.deriv < 0 || ep.deriv == ep.d)
+                    val = (ep.deriv < 0 ? ep.s : 1.0) * (1.0 + s5 * rr + 5.0 / 3.0 * q) * exp(-s5 * rr);
+                else
+                    val = ep.s * (5.0 / 3.0) * (1.0 + s5 * rr) * exp(-s5 * rr) * dk2[ep.deriv];
+            } else {
+                val = (ep.deriv == ep.d ? 1.0 : ep.s) * exp(-0.5 * q);
+                if (ep.deriv >= 0 && ep.deriv < ep.d) val *= dk2[ep.deriv];
+            }
+        }
+        z[e].x = (T)val;
+        z[e].y = T(0);
+    }
+}
+
+template <typename T>
+__global__ void k_take_real_scaled(const typename Cx<T>::t *__restrict__ z, T *__restrict__ lam, int64_t N, double scale) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
+        lam[e] = (T)(scale * (double)z[e].x);
+}
+
+// ------------------------------------------------------------------ operator object
+struct KgOp {
+    fkski_grid g;
+    int d, dtype;
+    int64_t m;
+    int L[3];
+    int kind;           // FKSKI_RBF / FKSKI_MATERN52
+    int param;
+    void *lam[3];       // Kronecker spectra (bit-reversed), L_k each
+    void *lamN;         // BTTB spectrum over the L-box (bit-reversed per axis)
+    int64_t N;          // prod L_k
+    void *scratch;      // work buffer
+    size_t scratch_bytes;
+};
+
+static int next_pow2(int64_t v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+int kgop_create(const fkski_grid *grid, int dtype, KgOp **op) {
+    *op = nullptr;
+    KgOp *k = new KgOp;
+    memset(k, 0, sizeof(*k));
+    k->g = *grid;
+    k->d = grid->d;
+    k->dtype = dtype;
+    k->m = 1;
+    k->N = 1;
+    k->kind = -1;
+    for (int a = 0; a < k->d; ++a) {
+        k->m *= grid->M[a];
+        k->L[a] = next_pow2(2 * grid->M[a] - 1);
+        if (k->L[a] > FFT_SMEM_CPLX) {
+            delete k;
+            return FKSKI_E_UNSUPPORTED;
+        }
+        k->N *= k->L[a];
+    }
+    *op = k;
+    return FKSKI_OK;
+}
+
+void kgop_destroy(KgOp *op) {
+    if (!op) return;
+    for (int a = 0; a < 3; ++a)
+        if (op->lam[a]) cudaFree(op->lam[a]);
+    if (op->lamN) cudaFree(op->lamN);
+    if (op->scratch) cudaFree(op->scratch);
+    delete op;
+}
+
+static size_t esz(int dtype) { return dtype == FKSKI_F32 ? 4 : 8; }
+
+static int ensure(void **p, size_t &have, size_t want) {
+    if (have >= want && *p) return FKSKI_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    have = 0;
+    if (cudaMalloc(p, want) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return FKSKI_E_OOM;
+    }
+    have = want;
+    return FKSKI_OK;
+}
+
+// Lines along axis a of a complex tensor whose extents are ext[0..d-1].
+static CplxPass cplx_geom(const int64_t ext[3], int d, int a, int Min, int Mout, int L, int64_t nbatch) {
+    CplxPass p;
+    int64_t O = nbatch, S = 1;
+    for (int k = 0; k < a; ++k) O *= ext[k];
+    for (int k = a + 1; k < d; ++k) S *= ext[k];
+    p.nlines = O * S;
+    p.S = S;
+    p.Min = Min;
+    p.Mout = Mout;
+    p.L = L;
+    p.Q = std::max(1, FFT_SMEM_CPLX / L);
+    return p;
+}
+
+template <typename T>
+static int launch_cplx(const typename Cx<T>::t *in, typename Cx<T>::t *out, CplxPass p, int mode, const T *lam,
+                       cudaStream_t s) {
+    using C = typename Cx<T>::t;
+    const size_t sm = sizeof(C) * ((size_t)p.L / 2 + (size_t)p.Q * p.L);
+    const unsigned nb = (unsigned)cdiv(p.nlines, p.Q);
+    if (mode == 0) {
+        FK_CUDA(cudaFuncSetAttribute(k_cplx_pass<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_cplx_pass<T, 0><<<nb, FFT_T, sm, s>>>(in, out, p, lam);
+    } else if (mode == 1) {
+        FK_CUDA(cudaFuncSetAttribute(k_cplx_pass<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_cplx_pass<T, 1><<<nb, FFT_T, sm, s>>>(in, out, p, lam);
+    } else {
+        FK_CUDA(cudaFuncSetAttribute(k_cplx_pass<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_cplx_pass<T, 2><<<nb, FFT_T, sm, s>>>(in, out, p, lam);
+    }
+    FK_LAUNCH();
+    return FKSKI_OK;
+}
+
+// BTTB spectrum: embed kernel values on the L-box, forward DIF along every axis (bit-reversed
+// order per axis), keep the real part scaled by 1/N.
+template <typename T>
+static int bttb_spectrum(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s) {
+    using C = typename Cx<T>::t;
+    const int d = op->d;
+    const int64_t N = op->N;
+    size_t have = 0;
+    if (!op->lamN) FK_TRY(ensure(&op->lamN, have, sizeof(T) * N));
+    C *z0 = nullptr, *z1 = nullptr;
+    FK_CUDA(cudaMallocAsync((void **)&z0, sizeof(C) * N, s));
+    FK_CUDA(cudaMallocAsync((void **)&z1, sizeof(C) * N, s));
+    EmbedParams ep;
+    memset(&ep, 0, sizeof(ep));
+    ep.d = d;
+    for (int k = 0; k < d; ++k) {
+        ep.M[k] = (int)op->g.M[k];
+        ep.L[k] = op->L[k];
+        ep.h[k] = op->g.h[k];
+        ep.ell[k] = kern->lengthscale[k];
+    }
+    ep.s = kern->outputscale;
+    ep.kind = kern->type == FKSKI_MATERN52 ? 0 : 1;
+    ep.deriv = param;
+    const unsigned nb = (unsigned)std::min<int64_t>(cdiv(N, 256), 4096);
+    k_embed_values<T><<<nb, 256, 0, s>>>(z0, ep, N);
+    FK_LAUNCH();
+    int64_t ext[3] = {op->L[0], op->L[1], op->L[2]};
+    C *cur = z0, *nxt = z1;
+    for (int a = d - 1; a >= 0; --a) {
+        CplxPass p = cplx_geom(ext, d, a, op->L[a], op->L[a], op->L[a], 1);
+        FK_TRY(launch_cplx<T>(cur, nxt, p, 0, (const T *)nullptr, s));
+        std::swap(cur, nxt);
+    }
+    k_take_real_scaled<T><<<nb, 256, 0, s>>>(cur, (T *)op->lamN, N, 1.0 / (double)N);
+    FK_LAUNCH();
+    cudaFreeAsync(z0, s);
+    cudaFreeAsync(z1, s);
+    return FKSKI_OK;
+}
+
+int kgop_set(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s) {
+    if (!kern) return FKSKI_E_INVALID_ARG;
+    if (kern->type != FKSKI_RBF && kern->type != FKSKI_MATERN52) return FKSKI_E_INVALID_ARG;
+    if (param < -1 || param > op->d) return FKSKI_E_INVALID_ARG;
+    for (int k = 0; k < op->d; ++k)
+        if (!(kern->lengthscale[k] > 0.0) || !std::isfinite(kern->lengthscale[k])) return FKSKI_E_INVALID_ARG;
+    if (!(kern->outputscale > 0.0)) return FKSKI_E_INVALID_ARG;
+    op->kind = kern->type;
+    op->param = param;
+    const size_t es = esz(op->dtype);
+    if (kern->type == FKSKI_RBF) {
+        for (int a = 0; a < op->d; ++a) {
+            size_t have = 0;
+            if (!op->lam[a]) FK_TRY(ensure(&op->lam[a], have, es * op->L[a]));
+            const double scale = (a == 0) ? (param == op->d ? 1.0 : kern->outputscale) : 1.0;
+            const int deriv = (param == a) ? 1 : 0;
+            const size_t sm = es * 2 * ((size_t)op->L[a] / 2 + (size_t)op->L[a]);
+            if (op->dtype == FKSKI_F32) {
+                FK_CUDA(cudaFuncSetAttribute(k_spectrum_1d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                k_spectrum_1d<float><<<1, FFT_T, sm, s>>>((float *)op->lam[a], (int)op->g.M[a], op->L[a], op->g.h[a],
+                                                          kern->lengthscale[a], deriv, scale);
+            } else {
+                FK_CUDA(cudaFuncSetAttribute(k_spectrum_1d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                k_spectrum_1d<double><<<1, FFT_T, sm, s>>>((double *)op->lam[a], (int)op->g.M[a], op->L[a], op->g.h[a],
+                                                           kern->lengthscale[a], deriv, scale);
+            }
+            FK_LAUNCH();
+        }
+        return FKSKI_OK;
+    }
+    return op->dtype == FKSKI_F32 ? bttb_spectrum<float>(op, kern, param, s) : bttb_spectrum<double>(op, kern, param, s);
+}
+
+template <typename T>
+static int kron_apply(KgOp *op, const T *v, T *out, int nrhs, const T *addv, const double *alpha_dev, double alpha,
+                      cudaStream_t s) {
+    const int d = op->d;
+    const int64_t m = op->m;
+    if (d > 1) {
+        FK_TRY(ensure(&op->scratch, op->scratch_bytes, sizeof(T) * (size_t)nrhs * m));
+    }
+    T *scr = (T *)op->scratch;
+    // pass order: last axis first; buffers so that the final pass writes `out`
+    const T *src = v;
+    for (int step = 0; step < d; ++step) {
+        const int a = d - 1 - step;
+        T *dst;
+        if (step == d - 1) dst = out;
+        else dst = ((d - 1 - step) % 2 == 1) ? scr : out;
+        RealPass p;
+        int64_t S = 1;
+        for (int k = a + 1; k < d; ++k) S *= op->g.M[k];
+        p.S = S;
+        p.M = (int)op->g.M[a];
+        p.L = op->L[a];
+        p.nlines = (int64_t)nrhs * (m / p.M);
+        p.Q = std::max(2, 2 * (FFT_SMEM_CPLX / p.L));
+        const size_t sm = sizeof(typename Cx<T>::t) * ((size_t)p.L / 2 + (size_t)(p.Q / 2) * p.L);
+        const unsigned nb = (unsigned)cdiv(p.nlines, p.Q);
+        const bool last = step == d - 1;
+        if (last && addv) {
+            FK_CUDA(cudaFuncSetAttribute(k_kron_pass<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_kron_pass<T, true><<<nb, FFT_T, sm, s>>>(src, dst, p, (const T *)op->lam[a], addv, alpha_dev, alpha);
+        } else {
+            FK_CUDA(cudaFuncSetAttribute(k_kron_pass<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_kron_pass<T, false><<<nb, FFT_T, sm, s>>>(src, dst, p, (const T *)op->lam[a], nullptr, nullptr, 0.0);
+        }
+        FK_LAUNCH();
+        src = dst;
+    }
+    return FKSKI_OK;
+}
+
+template <typename T>
+static int bttb_apply(KgOp *op, const T *v, T *out, int nrhs, const T *addv, const double *alpha_dev, double alpha,
+                      cudaStream_t s) {
+    using C = typename Cx<T>::t;
+    const int d = op->d;
+    const int64_t m = op->m;
+    const int npair = (nrhs + 1) / 2;
+    // largest intermediate: M_0 x L_1 x ... x L_{d-1} complex per pair (or m complex)
+    int64_t big = op->g.M[0];
+    for (int k = 1; k < d; ++k) big *= op->L[k];
+    big = std::max(big, m);
+    FK_TRY(ensure(&op->scratch, op->scratch_bytes, 2 * sizeof(C) * (size_t)npair * big));
+    C *z0 = (C *)op->scratch;
+    C *z1 = z0 + (size_t)npair * big;
+    const unsigned nb = (unsigned)std::min<int64_t>(cdiv((int64_t)npair * m, 256), 4096);
+    k_pack_pairs<T><<<nb, 256, 0, s>>>(v, z0, m, nrhs);
+    FK_LAUNCH();
+    int64_t ext[3] = {op->g.M[0], op->g.M[1], op->g.M[2]};
+    C *cur = z0, *nxt = z1;
+    // forward along axes d-1..1 (extent M -> L)
+    for (int a = d - 1; a >= 1; --a) {
+        CplxPass p = cplx_geom(ext, d, a, (int)op->g.M[a], op->L[a], op->L[a], npair);
+        FK_TRY(launch_cplx<T>(cur, nxt, p, 0, (const T *)nullptr, s));
+        ext[a] = op->L[a];
+        std::swap(cur, nxt);
+    }
+    // axis 0: forward, spectrum, inverse (extent M_0 -> M_0); spectrum lines indexed (k, rest)
+    {
+        CplxPass p = cplx_geom(ext, d, 0, (int)op->g.M[0], (int)op->g.M[0], op->L[0], npair);
+        // lam is indexed [k * S + s] with S = prod_{k>0} L_k = p.S (the pair index folds into O)
+        FK_TRY(launch_cplx<T>(cur, nxt, p, 2, (const T *)op->lamN, s));
+        std::swap(cur, nxt);
+    }
+    for (int a = 1; a < d; ++a) {
+        CplxPass p = cplx_geom(ext, d, a, op->L[a], (int)op->g.M[a], op->L[a], npair);
+        FK_TRY(launch_cplx<T>(cur, nxt, p, 1, (const T *)nullptr, s));
+        ext[a] = op->g.M[a];
+        std::swap(cur, nxt);
+    }
+    const unsigned nb2 = (unsigned)std::min<int64_t>(cdiv((int64_t)nrhs * m, 256), 4096);
+    k_unpack_pairs<T><<<nb2, 256, 0, s>>>(cur, out, m, nrhs, addv, alpha_dev, alpha);
+    FK_LAUNCH();
+    return FKSKI_OK;
+}
+
+static int kgop_apply_any(KgOp *op, const void *v, void *out, int nrhs, const void *addv, const double *alpha_dev,
+                          double alpha, cudaStream_t s) {
+    if (op->kind < 0) return FKSKI_E_INVALID_ARG;
+    if (nrhs < 1) return FKSKI_E_INVALID_ARG;
+    if (op->kind == FKSKI_RBF) {
+        if (op->dtype == FKSKI_F32)
+            return kron_apply<float>(op, (const float *)v, (float *)out, nrhs, (const float *)addv, alpha_dev, alpha, s);
+        return kron_apply<double>(op, (const double *)v, (double *)out, nrhs, (const double *)addv, alpha_dev, alpha, s);
+    }
+    if (op->dtype == FKSKI_F32)
+        return bttb_apply<float>(op, (const float *)v, (float *)out, nrhs, (const float *)addv, alpha_dev, alpha, s);
+    return bttb_apply<double>(op, (const double *)v, (double *)out, nrhs, (const double *)addv, alpha_dev, alpha, s);
+}
+
+int kgop_apply(KgOp *op, const void *v, void *out, int nrhs, const void *addv, double alpha, cudaStream_t s) {
+    return kgop_apply_any(op, v, out, nrhs, addv, nullptr, alpha, s);
+}
+
+int kgop_apply_dev(KgOp *op, const void *v, void *out, int nrhs, const void *addv, const double *alpha_dev,
+                   cudaStream_t s) {
+    return kgop_apply_any(op, v, out, nrhs, addv, alpha_dev, 0.0, s);
+}
+
+int kg_mvm_impl(const fkski_grid *grid, const fkski_kernel *kern, int param, const void *v, void *out, int nrhs,
+                int dtype, cudaStream_t s) {
+    if (!grid || !kern || !v || !out || nrhs < 1) return FKSKI_E_INVALID_ARG;
+    if (grid->d < 1 || grid->d > 3) return FKSKI_E_INVALID_ARG;
+    if (dtype != FKSKI_F32 && dtype != FKSKI_F64) return FKSKI_E_INVALID_ARG;
+    for (int k = 0; k < grid->d; ++k)
+        if (grid->M[k] < 4 || !(grid->h[k] > 0.0)) return FKSKI_E_INVALID_ARG;
+    if (v == out) return FKSKI_E_INVALID_ARG;
+    KgOp *op = nullptr;
+    FK_TRY(kgop_create(grid, dtype, &op));
+    int rc = kgop_set(op, kern, param, s);
+    if (rc == FKSKI_OK) rc = kgop_apply(op, v, out, nrhs, nullptr, 0.0, s);
+    cudaStreamSynchronize(s);  // op buffers are freed below
+    kgop_destroy(op);
+    return rc;
+}
+
+}  // namespace fk

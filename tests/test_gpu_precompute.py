@@ -1,0 +1,141 @@
+"""GPU precompute (keys, stable cell sort, W^T W band, W^T y, probes) against the CPU oracle.
+
+Bars: keys, permutation and segment offsets bit-exact; band and W^T y within 1e-6 relative
+(Frobenius over the whole array, and max-abs relative to the largest entry); y^T y 1e-6."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import max_rel, problem, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # d, M, n, dtype, clustered
+    (1, (3000,), 30000, np.float32, False),     # > 1 tile along the only axis (D=1 cap 2048 cells)
+    (1, (1000,), 10000, np.float64, False),     # the sine workload's grid, FP64
+    (2, (40, 37), 50000, np.float32, True),
+    (2, (9, 600), 20000, np.float32, False),    # last axis longer than a D=2 tile
+    (2, (33, 21), 7777, np.float64, False),
+    (3, (12, 10, 11), 20001, np.float32, False),
+    (3, (6, 5, 130), 20000, np.float32, False), # last axis longer than a D=3 tile (halo recompute)
+    (3, (8, 9, 7), 5000, np.float64, True),
+]
+
+
+def _tt(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("d,M,n,dtype,clustered", CASES)
+def test_precompute_matches_oracle(fk, oracle_mod, d, M, n, dtype, clustered):
+    from oracle import core
+    grid, X, y = problem(d, M, n, seed=n % 97, dtype=dtype, clustered=clustered)
+    st = fk.precompute(_tt(X), _tt(y), grid, n_probes=3, probe_seed=7, keep_sort=True)
+    ex = fk.stats_export(st)
+    srt = fk.stats_export_sort(st)
+    ref = core.precompute(grid, X, y, nprobe=3, seed=7)
+    np.testing.assert_array_equal(srt["keys"], ref["keys"])
+    np.testing.assert_array_equal(srt["perm"], ref["perm"])
+    np.testing.assert_array_equal(srt["offsets"], ref["offsets"])
+    assert rel_fro(ex["band"], ref["band"]) <= 1e-6
+    assert max_rel(ex["band"], ref["band"]) <= 1e-6
+    assert rel_fro(ex["wty"], ref["wty"]) <= 1e-6
+    assert max_rel(ex["wty"], ref["wty"]) <= 1e-6
+    assert rel_fro(ex["wtz"], ref["wtz"]) <= 1e-6
+    assert ex["yty"] == pytest.approx(ref["yty"], rel=1e-6)
+    np.testing.assert_allclose(ex["ztz"], [n] * 3)
+
+
+def test_sort_three_radix_passes(fk, oracle_mod):
+    """More than 2^20 cells: three 7-bit digit passes; keys/permutation/offsets bit-exact."""
+    from oracle import core
+    grid, X, y = problem(3, (110, 105, 100), 200000, seed=3)
+    st = fk.precompute(_tt(X), _tt(y), grid, keep_sort=True)
+    srt = fk.stats_export_sort(st)
+    ref = core.precompute(grid, X, y, want_band=False)
+    assert grid.ncells > (1 << 20)
+    np.testing.assert_array_equal(srt["keys"], ref["keys"])
+    np.testing.assert_array_equal(srt["perm"], ref["perm"])
+    np.testing.assert_array_equal(srt["offsets"], ref["offsets"])
+
+
+def test_single_point_and_boundaries(fk, oracle_mod):
+    """n = 1, and points exactly on s = 1 and s = M-2 of an exactly representable grid."""
+    from oracle import core
+    from paper_2101_11751_gb300 import synth
+    grid = synth.Grid(d=2, M=(10, 12), lo=(0.0, 0.0), h=(0.25, 0.5))
+    X = np.array([[0.25, 2.0, 1.0, 0.6], [0.5, 5.0, 2.75, 3.3]], dtype=np.float32)
+    y = np.array([1.0, -2.0, 0.5, 3.0], dtype=np.float32)
+    for k in (1, 4):
+        st = fk.precompute(_tt(X[:, :k]), _tt(y[:k]), grid, keep_sort=True)
+        ex = fk.stats_export(st)
+        ref = core.precompute(grid, X[:, :k], y[:k])
+        np.testing.assert_allclose(ex["band"], ref["band"], atol=1e-6)
+        np.testing.assert_allclose(ex["wty"], ref["wty"], atol=1e-6)
+        srt = fk.stats_export_sort(st)
+        np.testing.assert_array_equal(srt["keys"], ref["keys"])
+
+
+def test_point_errors(fk):
+    from paper_2101_11751_gb300 import synth
+    grid = synth.Grid(d=1, M=(10,), lo=(0.0,), h=(0.25,))
+    y = _tt(np.ones(3, np.float32))
+    with pytest.raises(fk.FkskiError) as e:
+        fk.precompute(_tt(np.array([[0.3, 0.1, 1.0]], np.float32)), y, grid)
+    assert e.value.code == fk.E_OUT_OF_GRID
+    with pytest.raises(fk.FkskiError) as e:
+        fk.precompute(_tt(np.array([[0.3, float("nan"), 1.0]], np.float32)), y, grid)
+    assert e.value.code == fk.E_NONFINITE
+    with pytest.raises(fk.FkskiError) as e:
+        fk.precompute(_tt(np.array([[0.3, 0.5, 1.0]], np.float32)), _tt(np.array([1, np.inf, 0], np.float32)), grid)
+    assert e.value.code == fk.E_NONFINITE
+    bad = synth.Grid(d=1, M=(3,), lo=(0.0,), h=(0.25,))
+    with pytest.raises(fk.FkskiError) as e:
+        fk.precompute(_tt(np.array([[0.3]], np.float32)), _tt(np.ones(1, np.float32)), bad)
+    assert e.value.code == fk.E_INVALID_ARG
+
+
+def test_user_probes(fk, oracle_mod):
+    """Caller-supplied probes Z give W^T Z and Z Z^T diagonals."""
+    from oracle import core
+    grid, X, y = problem(2, (20, 18), 9000, seed=5)
+    Z = np.random.default_rng(1).normal(size=(5, 9000)).astype(np.float32)
+    st = fk.precompute(_tt(X), _tt(y), grid, Z=_tt(Z))
+    ex = fk.stats_export(st, want_band=False)
+    W = core.w_csr(grid, X)
+    ref = (W.T @ Z.astype(np.float64).T).T
+    assert rel_fro(ex["wtz"], ref) <= 1e-6
+    np.testing.assert_allclose(ex["ztz"], np.sum(Z.astype(np.float64) ** 2, axis=1), rtol=1e-6)
+
+
+def test_deterministic(fk):
+    grid, X, y = problem(3, (10, 11, 9), 30000, seed=9)
+    st1 = fk.precompute(_tt(X), _tt(y), grid, n_probes=2)
+    st2 = fk.precompute(_tt(X), _tt(y), grid, n_probes=2)
+    a, b = fk.stats_export(st1), fk.stats_export(st2)
+    for k in ("band", "wty", "wtz"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_save_load_roundtrip(fk, tmp_path):
+    grid, X, y = problem(2, (16, 15), 4000, seed=2)
+    st = fk.precompute(_tt(X), _tt(y), grid, n_probes=2)
+    p = str(tmp_path / "stats.bin")
+    fk.stats_save(st, p)
+    st2 = fk.stats_load(p, grid)
+    a, b = fk.stats_export(st), fk.stats_export(st2)
+    for k in ("band", "wty", "wtz"):
+        np.testing.assert_array_equal(a[k], b[k])
+    assert st2.info()["n"] == 4000
+
+
+def test_band_mvm_matches_oracle(fk, oracle_mod):
+    from oracle import core
+    grid, X, y = problem(3, (9, 8, 10), 6000, seed=4)
+    st = fk.precompute(_tt(X), _tt(y), grid)
+    ref = core.precompute(grid, X, y)
+    V = np.random.default_rng(0).normal(size=(3, grid.m)).astype(np.float32)
+    U = fk.band_mvm(st, _tt(V)).cpu().numpy()
+    Uref = core.band_matvec(grid, ref["band"], V.astype(np.float64).T).T
+    assert rel_fro(U, Uref) <= 2e-6

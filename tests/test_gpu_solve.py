@@ -1,0 +1,94 @@
+"""GPU factorized CG (Alg. 5 and Alg. 3) and prediction against the oracle's n-space CG (Alg. 1).
+
+Bar: posterior mean (v = K_G W^T z on the grid, and mu at test points) within 1e-4 relative L2 of
+the oracle at equal CG tolerance and start; iteration counts close (App. C.2: they differ only
+through finite precision)."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import problem, rel_fro
+from paper_2101_11751_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # d, M, n, kernel, rtol, precision
+    (1, (1000,), 10000, synth.Kernel(synth.RBF, (0.05,), 1.0, 0.01), 1e-10, 1),
+    (1, (300,), 20000, synth.Kernel(synth.RBF, (0.05,), 1.0, 0.01), 1e-5, 0),
+    (2, (48, 48), 30000, synth.Kernel(synth.RBF, (0.1, 0.15), 1.0, 0.01), 1e-6, 0),
+    (2, (40, 44), 25000, synth.Kernel(synth.MATERN52, (0.08, 0.12), 1.0, 0.0025), 1e-6, 0),
+    (3, (14, 13, 12), 40000, synth.Kernel(synth.RBF, (0.2, 0.2, 0.2), 1.0, 0.01), 1e-5, 0),
+    (3, (10, 11, 9), 15000, synth.Kernel(synth.RBF, (0.25, 0.2, 0.3), 1.5, 0.05), 1e-10, 1),
+]
+
+
+def _tt(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("d,M,n,kern,rtol,prec", CASES)
+@pytest.mark.parametrize("x0_mode", [0, 1])
+def test_mean_matches_nspace_cg(fk, oracle_mod, d, M, n, kern, rtol, prec, x0_mode):
+    from oracle import core
+    dtype = np.float64 if prec == 1 else np.float32
+    grid, X, y = problem(d, M, n, seed=11 + d, dtype=dtype)
+    st = fk.precompute(_tt(X), _tt(y), grid)
+    a, v, info = fk.solve(st, kern, rtol=rtol, maxiter=3000, x0_mode=x0_mode, precision=prec)
+    a_ref, v_ref, it_ref, _ = core.nspace_mean(grid, kern, X, y, rtol=rtol, x0_mode=x0_mode)
+    assert rel_fro(v.double().cpu().numpy(), v_ref) <= 1e-4
+    assert rel_fro(a.double().cpu().numpy(), a_ref) <= 1e-4
+    # iteration counts: FP64 runs track the n-space recurrence closely
+    if prec == 1:
+        assert abs(info["iters"] - it_ref) <= max(3, 0.05 * it_ref), (info["iters"], it_ref)
+    Xs = np.random.default_rng(3).uniform(0, 1, size=(d, 1000)).astype(dtype)
+    mu = fk.predict(st, v, _tt(Xs)).double().cpu().numpy()
+    mu_ref = core.predict(grid, v_ref, Xs)
+    assert rel_fro(mu, mu_ref) <= 1e-4
+
+
+def test_mean_against_tight_oracle(fk, oracle_mod):
+    """Both sides bounded by a tight (1e-12) FP64 reference of the same system."""
+    from oracle import core
+    grid, X, y = problem(2, (32, 30), 20000, seed=3)
+    kern = synth.Kernel(synth.RBF, (0.1, 0.12), 1.0, 0.02)
+    st = fk.precompute(_tt(X), _tt(y), grid)
+    a, v, info = fk.solve(st, kern, rtol=1e-6)
+    _, v_tight, _, _ = core.nspace_mean(grid, kern, X, y, rtol=1e-12)
+    assert rel_fro(v.double().cpu().numpy(), v_tight) <= 1e-4
+
+
+def test_not_converged_and_invalid(fk):
+    grid, X, y = problem(2, (20, 20), 5000, seed=1)
+    kern = synth.Kernel(synth.RBF, (0.1, 0.1), 1.0, 0.001)
+    st = fk.precompute(_tt(X), _tt(y), grid)
+    a, v, info = fk.solve(st, kern, rtol=1e-12, maxiter=2, allow_not_converged=True)
+    assert info["status"] == fk.E_NOT_CONVERGED and info["iters"] == 2
+    assert torch.isfinite(v).all()
+    with pytest.raises(fk.FkskiError) as e:
+        fk.solve(st, synth.Kernel(synth.RBF, (0.1, 0.1), 1.0, 0.0))
+    assert e.value.code == fk.E_INVALID_ARG
+    with pytest.raises(fk.FkskiError) as e:
+        fk.solve(st, synth.Kernel(synth.RBF, (0.1, -1.0), 1.0, 0.1))
+    assert e.value.code == fk.E_INVALID_ARG
+
+
+def test_predict_out_of_grid(fk):
+    grid, X, y = problem(1, (50,), 1000, seed=1)
+    st = fk.precompute(_tt(X), _tt(y), grid)
+    v = torch.ones(grid.m, device="cuda")
+    with pytest.raises(fk.FkskiError) as e:
+        fk.predict(st, v, _tt(np.array([[0.5, 2.0]], np.float32)))
+    assert e.value.code == fk.E_OUT_OF_GRID
+    # partition of unity: a constant field interpolates to itself
+    mu = fk.predict(st, v, _tt(np.array([[0.1, 0.5, 0.77]], np.float32)))
+    np.testing.assert_allclose(mu.cpu().numpy(), 1.0, rtol=1e-6)
+
+
+def test_solve_deterministic(fk):
+    grid, X, y = problem(3, (12, 12, 12), 20000, seed=5)
+    kern = synth.Kernel(synth.RBF, (0.2, 0.2, 0.2), 1.0, 0.01)
+    st = fk.precompute(_tt(X), _tt(y), grid)
+    a1, v1, _ = fk.solve(st, kern, rtol=1e-6)
+    a2, v2, _ = fk.solve(st, kern, rtol=1e-6)
+    assert torch.equal(v1, v2) and torch.equal(a1, a2)
