@@ -111,6 +111,10 @@ FKSKI_API void fkski_default_opts(fkski_opts *opts);
 /* Human-readable name of a status code (static string). */
 FKSKI_API const char *fkski_strerror(int status);
 
+/* The CUDA error behind the calling thread's last FKSKI_E_CUDA / FKSKI_E_OOM (runtime error
+ * string, code and source location; empty if none).  Valid until the thread's next failing call. */
+FKSKI_API const char *fkski_last_error_detail(void);
+
 /* ------------------------------------------------------------------ precompute (Sec. 3.1)
  * One O(n) pass computing the sufficient statistics of the Bayesian linear regression of Def. 2:
  *   W^T W  stored as its 7^d diagonals (Claim 2: at most (4r-1)^d = 7^d nonzeros per row, r = 2),

@@ -27,6 +27,8 @@ MIXED, DOUBLE = 0, 1
 class FkskiError(RuntimeError):
     def __init__(self, code: int, where: str):
         msg = _lib.fkski_strerror(code).decode() if _lib is not None else str(code)
+        if _lib is not None and code in (E_CUDA, E_OOM):
+            msg += " [" + _lib.fkski_last_error_detail().decode() + "]"
         super().__init__(f"{where}: {msg} ({code})")
         self.code = code
 
@@ -60,6 +62,7 @@ PD = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "fkski_default_opts": (None, [ctypes.POINTER(COpts)]),
     "fkski_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "fkski_last_error_detail": (ctypes.c_char_p, []),
     "fkski_precompute": (ctypes.c_int, [ctypes.POINTER(CGrid), P, P, P, ctypes.c_int64, ctypes.c_int,
                                         ctypes.POINTER(COpts), ctypes.POINTER(P), P]),
     "fkski_stats_info": (ctypes.c_int, [P, ctypes.POINTER(CGrid), PI64, PI64, PI64,

@@ -22,6 +22,16 @@ void destroy_stats(fkski_stats *st) {
 
 static cudaStream_t S(void *stream) { return reinterpret_cast<cudaStream_t>(stream); }
 
+static thread_local char g_detail[256] = "";
+
+int note_cuda_error(cudaError_t e, const char *file, int line) {
+    const char *base = strrchr(file, '/');
+    snprintf(g_detail, sizeof(g_detail), "%s (%d) at %s:%d", cudaGetErrorString(e), (int)e, base ? base + 1 : file,
+             line);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? FKSKI_E_OOM : FKSKI_E_CUDA;
+}
+
 }  // namespace fk
 
 using namespace fk;
@@ -58,6 +68,8 @@ const char *fkski_strerror(int st) {
         default: return "unknown status";
     }
 }
+
+const char *fkski_last_error_detail(void) { return g_detail; }
 
 int fkski_precompute(const fkski_grid *grid, const void *X, const void *y, const void *Z, int64_t n, int dtype,
                      const fkski_opts *opts, fkski_stats **out, void *stream) {

@@ -10,12 +10,15 @@
 
 #include "../../include/fkski.h"
 
+namespace fk {
+// Records the failing CUDA call (thread-local) for fkski_last_error_detail(); returns the status.
+int note_cuda_error(cudaError_t e, const char *file, int line);
+}  // namespace fk
+
 #define FK_CUDA(call)                                                  \
     do {                                                               \
         cudaError_t _e = (call);                                       \
-        if (_e != cudaSuccess) {                                       \
-            return _e == cudaErrorMemoryAllocation ? FKSKI_E_OOM : FKSKI_E_CUDA; \
-        }                                                              \
+        if (_e != cudaSuccess) return fk::note_cuda_error(_e, __FILE__, __LINE__); \
     } while (0)
 
 #define FK_TRY(call)                 \

@@ -525,6 +525,8 @@ struct SolveWork {
     double *hist;     // alpha then beta, maxiter x R each
     size_t hist_cap;  // entries per array
     int *hflag;       // pinned host: all_done
+    cudaStream_t ws;  // internal stream for graph capture (the caller's may be the legacy stream)
+    cudaEvent_t ev;
     // stored solutions for the log-likelihood backward pass
     void *sol;
     size_t sol_bytes;
@@ -545,6 +547,8 @@ void free_solve_work(SolveWork *w) {
     if (w->ctl) cudaFree(w->ctl);
     if (w->hist) cudaFree(w->hist);
     if (w->hflag) cudaFreeHost(w->hflag);
+    if (w->ws) cudaStreamDestroy(w->ws);
+    if (w->ev) cudaEventDestroy(w->ev);
     if (w->sol) cudaFree(w->sol);
     delete w;
 }
@@ -575,6 +579,8 @@ static int work_get(fkski_stats *st, SolveWork **out) {
             cudaGetLastError();
             return FKSKI_E_OOM;
         }
+        FK_CUDA(cudaStreamCreateWithFlags(&w->ws, cudaStreamNonBlocking));
+        FK_CUDA(cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming));
     }
     *out = st->work;
     return FKSKI_OK;
@@ -644,16 +650,21 @@ int stats_band_as(fkski_stats *st, int dtype, const void **band, const void **wt
     return stats_as<double>(st, (const double **)band, (const double **)wty, (const double **)wtz, s);
 }
 
-// Run the captured iteration body until convergence or maxiter.
+// Run the captured iteration body (captured on w->ws) until convergence or maxiter; the
+// internal stream first waits for the caller's stream, and the caller's stream waits for it.
 static int run_graph_loop(cudaGraphExec_t exec, SolveWork *w, int maxiter, int check, cudaStream_t s) {
+    FK_CUDA(cudaEventRecord(w->ev, s));
+    FK_CUDA(cudaStreamWaitEvent(w->ws, w->ev, 0));
     int done_iters = 0;
     while (done_iters < maxiter + check) {
-        FK_CUDA(cudaGraphLaunch(exec, s));
+        FK_CUDA(cudaGraphLaunch(exec, w->ws));
         done_iters += check;
-        FK_CUDA(cudaMemcpyAsync(w->hflag, &w->ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, s));
-        FK_CUDA(cudaStreamSynchronize(s));
+        FK_CUDA(cudaMemcpyAsync(w->hflag, &w->ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, w->ws));
+        FK_CUDA(cudaStreamSynchronize(w->ws));
         if (w->hflag[0]) break;
     }
+    FK_CUDA(cudaEventRecord(w->ev, w->ws));
+    FK_CUDA(cudaStreamWaitEvent(s, w->ev, 0));
     return FKSKI_OK;
 }
 
@@ -716,21 +727,22 @@ static int solve_alg5(fkski_stats *st, const fkski_kernel *kern, const fkski_opt
     const int check = std::max(1, o->check_every);
     cudaGraph_t graph;
     cudaGraphExec_t exec;
-    FK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    const cudaStream_t cs = w->ws;
+    FK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     int rc = FKSKI_OK;
     for (int it = 0; it < check && rc == FKSKI_OK; ++it) {
-        k_cg5_xr<T><<<gb, CG_T, 0, s>>>(m, R, xd, r, sv, z, w->S, w->done, w->ctl);
-        rc = launch_spmv<T>(band, st->grid, r, u, m, R, w->part, 1, nullptr, w->ctl, gb, s);
+        k_cg5_xr<T><<<gb, CG_T, 0, cs>>>(m, R, xd, r, sv, z, w->S, w->done, w->ctl);
+        rc = launch_spmv<T>(band, st->grid, r, u, m, R, w->part, 1, nullptr, w->ctl, gb, cs);
         if (rc) break;
-        k_cg5_fin_gamma<<<1, 256, 0, s>>>(w->part, gb, w->S, w->done, w->iters, hb, w->ctl, 0);
-        rc = kgop_apply_dev(kg, u, v, 1, r, sig2_dev, s);
+        k_cg5_fin_gamma<<<1, 256, 0, cs>>>(w->part, gb, w->S, w->done, w->iters, hb, w->ctl, 0);
+        rc = kgop_apply_dev(kg, u, v, 1, r, sig2_dev, cs);
         if (rc) break;
-        k_cg5_sz<T><<<gb, CG_T, 0, s>>>(m, R, u, v, sv, z, w->S, w->done, w->part, w->ctl);
-        k_cg5_fin_delta<<<1, 256, 0, s>>>(w->part, gb, w->S, w->done, w->iters, ha, w->ctl, 0);
+        k_cg5_sz<T><<<gb, CG_T, 0, cs>>>(m, R, u, v, sv, z, w->S, w->done, w->part, w->ctl);
+        k_cg5_fin_delta<<<1, 256, 0, cs>>>(w->part, gb, w->S, w->done, w->iters, ha, w->ctl, 0);
     }
-    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (rc != FKSKI_OK) return rc;
-    if (ce != cudaSuccess) return FKSKI_E_CUDA;
+    FK_CUDA(ce);
     FK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
     rc = run_graph_loop(exec, w, o->maxiter, check, s);
     cudaGraphExecDestroy(exec);
@@ -815,21 +827,22 @@ int solve_alg3_batched(fkski_stats *st, const fkski_kernel *kern, const fkski_op
     const int check = std::max(1, o->check_every);
     cudaGraph_t graph;
     cudaGraphExec_t exec;
-    FK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    const cudaStream_t cs = w->ws;
+    FK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     int rc = FKSKI_OK;
     for (int it = 0; it < check && rc == FKSKI_OK; ++it) {
-        k_cg3_xr<T><<<gb, CG_T, 0, s>>>(m, R, V.x, V.xd, V.r, V.p, V.s, V.z, V.kg, w->S, w->done, w->ctl);
-        rc = launch_spmv<T>(band, st->grid, V.r, V.u, m, R, w->part, 2, V.g, w->ctl, gb, s);
+        k_cg3_xr<T><<<gb, CG_T, 0, cs>>>(m, R, V.x, V.xd, V.r, V.p, V.s, V.z, V.kg, w->S, w->done, w->ctl);
+        rc = launch_spmv<T>(band, st->grid, V.r, V.u, m, R, w->part, 2, V.g, w->ctl, gb, cs);
         if (rc) break;
-        k_cg3_fin_gamma<<<1, 256, 0, s>>>(w->part, gb, w->S, w->done, w->iters, hb, w->ctl);
-        rc = kgop_apply_dev(kg, V.u, V.v, R, V.r, sig2_dev, s);
+        k_cg3_fin_gamma<<<1, 256, 0, cs>>>(w->part, gb, w->S, w->done, w->iters, hb, w->ctl);
+        rc = kgop_apply_dev(kg, V.u, V.v, R, V.r, sig2_dev, cs);
         if (rc) break;
-        k_cg3_psz<T><<<gb, CG_T, 0, s>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->S, w->done, w->part, w->ctl);
-        k_cg3_fin_delta<<<1, 256, 0, s>>>(w->part, gb, w->S, w->done, w->iters, ha, w->ctl);
+        k_cg3_psz<T><<<gb, CG_T, 0, cs>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->S, w->done, w->part, w->ctl);
+        k_cg3_fin_delta<<<1, 256, 0, cs>>>(w->part, gb, w->S, w->done, w->iters, ha, w->ctl);
     }
-    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (rc != FKSKI_OK) return rc;
-    if (ce != cudaSuccess) return FKSKI_E_CUDA;
+    FK_CUDA(ce);
     FK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
     rc = run_graph_loop(exec, w, o->maxiter, check, s);
     cudaGraphExecDestroy(exec);
