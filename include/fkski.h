@@ -57,8 +57,9 @@ extern "C" {
 #define FKSKI_X0_ZERO 0      /* Alg. 3 (EFCG, x0 = 0, r0 = y)                                      */
 #define FKSKI_X0_Y_OVER_S2 1 /* Alg. 5 (simplified EFCG, x0 = y / sigma^2, r0 in span(W))            */
 
-#define FKSKI_MIXED 0  /* FP32 vectors, band, FFT; FP64 inner products and scalars */
-#define FKSKI_DOUBLE 1 /* FP64 throughout                                          */
+#define FKSKI_MIXED 0  /* FP32 band, FFT and Krylov vectors; FP64 solution, scalars, cross-warp
+                          inner-product sums, and the periodic true-residual replacement      */
+#define FKSKI_DOUBLE 1 /* FP64 throughout                                                      */
 
 /* ------------------------------------------------------------------ configuration structs */
 
@@ -174,6 +175,8 @@ FKSKI_API int fkski_band_mvm(const fkski_stats *st, const void *x, void *u, int 
  * statistics: Alg. 5 (x0 = y/sigma^2) or Alg. 3 (x0 = 0), one B(x) = [(K_G W^T W + sigma^2 I)x,
  * W^T W x] per iteration.  Outputs (device, m entries, FP32 for MIXED / FP64 for DOUBLE):
  *   a_out = W^T z   and   v_out = K_G W^T z  (= z_bar, the GSGP posterior mean of theta, Fact 2).
+ * Every opts->check_every iterations the residual is replaced by the true residual of the
+ * FP64 solution (computed with an FP64 SpMV and FP64 K_G); convergence is declared only on it.
  * Stops when ||r_k|| <= rtol ||y||.  info (host, may be NULL) receives iterations and residual.
  * Returns OK, NOT_CONVERGED (outputs written), BREAKDOWN, INVALID_ARG, OOM, CUDA.
  * Synchronizes the stream every opts->check_every iterations to test convergence. */

@@ -136,9 +136,11 @@ void kgop_destroy(KgOp *op);
 // Recompute spectra for the hyperparameters (param as in fkski_kg_mvm).
 int kgop_set(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s);
 // out = K v (or dK v) for nrhs vectors; if addv != nullptr: out = K v + alpha * addv
-// (addv has the same layout as v).  `scratch` must hold kgop_scratch_elems(op, nrhs) elements.
+// (addv has the same layout as v).  Scratch grows on demand (see kgop_reserve).
 int kgop_apply(KgOp *op, const void *v, void *out, int nrhs, const void *addv, double alpha,
                cudaStream_t s);
+// Pre-allocate the scratch for nrhs vectors (call before capturing applications in a graph).
+int kgop_reserve(KgOp *op, int nrhs);
 // Same, with alpha read from device memory (a double) so graphs can be reused.
 int kgop_apply_dev(KgOp *op, const void *v, void *out, int nrhs, const void *addv,
                    const double *alpha_dev, cudaStream_t s);

@@ -4,7 +4,7 @@
 //   L = -1/2 [ logdet A + y^T A^{-1} y + n log 2 pi ],   A = W K_G W^T + sigma^2 I.
 // Solves: batched factorized CG (Alg. 3, x0 = 0) on [y, z_1..z_T], z_p the Rademacher probes
 // whose W^T z_p the precompute accumulated.  From the compressed solution x = W x_hat + c^x b:
-//   W^T x = W^T W x_hat + c^x W^T b     (x_hat_d = W^T W x_hat is carried by the recurrence)
+//   W^T x = W^T W x_hat + c^x W^T b     (x_hat in FP64, one FP64 SpMV at the end)
 //   b^T x = (W^T b)^T x_hat + c^x b^T b
 // logdet A by stochastic Lanczos quadrature: each probe's CG coefficients give the Lanczos
 // tridiagonal T_p (T[0,0] = 1/a_0, T[i,i] = 1/a_i + b_{i-1}/a_{i-1}, T[i,i+1] = sqrt(b_i)/a_i) and
@@ -22,14 +22,8 @@
 
 namespace fk {
 
-template <typename T>
-struct Alg3Vecs {
-    T *r, *p, *x, *xd, *u, *v, *s, *z, *g, *kg;
-};
-int alg3_for_grad_f32(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, Alg3Vecs<float> &V,
-                      int *iters, double *res, int *status, cudaStream_t s);
-int alg3_for_grad_f64(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, Alg3Vecs<double> &V,
-                      int *iters, double *res, int *status, cudaStream_t s);
+int grad_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int dtype, void *sol, double *a64,
+               double *zx, int *iters, double *res, int *status, cudaStream_t s);
 
 // The solve workspace layout is private to solve.cu; grad.cu reaches it through these.
 struct GradView {
@@ -43,7 +37,7 @@ int grad_view(fkski_stats *st, int dtype, GradView *gv);
 int grad_sol_buffer(fkski_stats *st, size_t bytes, void **p);
 void grad_sol_mark(fkski_stats *st, int valid, const fkski_kernel *kern, int dtype);
 int grad_sol_valid(fkski_stats *st, const fkski_kernel *kern, int dtype);
-constexpr int GF_CX = 6, GF_RHO0 = 7;  // must match solve.cu's field enum
+constexpr int GF_RHO0 = 7;  // must match solve.cu's field enum
 int spmv_for_grad(fkski_stats *st, const void *x, void *u, int R, int dtype, cudaStream_t s);
 
 // ------------------------------------------------------------------ SLQ
@@ -168,27 +162,19 @@ static int rowdots(const T *a, const T *b, int64_t m, int R, double *part, doubl
     return FKSKI_OK;
 }
 
-template <typename T>
-__global__ void k_wtx(const T *__restrict__ xd, const T *__restrict__ g, const double *__restrict__ S, int R, int64_t m,
-                      T *__restrict__ out) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / m);
-        out[e] = fma((T)S[GF_CX * R + r], g[e], xd[e]);
-    }
-}
-
-// Forward scalars.  fs layout: [0] L, [1] logdet, [2] quad, [3..3+R) z_p^T x_p (index 0 unused)
-__global__ void k_loglik_assemble(const double *__restrict__ S, const double *__restrict__ gx,
+// Forward scalars.  fs layout: [0] L, [1] logdet, [2] quad, [3 + p] z_p^T x_p (p >= 1).
+// zx[r] = b_r^T x_r from the solve (r = 0: y^T A^{-1} y).
+__global__ void k_loglik_assemble(const double *__restrict__ S, const double *__restrict__ zx,
                                   const double *__restrict__ est, int R, double n, double *__restrict__ fs) {
     if (threadIdx.x != 0) return;
-    const double quad = gx[0] + S[GF_CX * R + 0] * S[GF_RHO0 * R + 0];
+    const double quad = zx[0];
     double ld = 0.0;
     for (int p = 1; p < R; ++p) ld += est[p - 1];
     ld /= (double)(R - 1);
     fs[0] = -0.5 * (ld + quad + n * log(2.0 * 3.14159265358979323846));
     fs[1] = ld;
     fs[2] = quad;
-    for (int p = 1; p < R; ++p) fs[3 + p] = gx[p] + S[GF_CX * R + p] * S[GF_RHO0 * R + p];
+    for (int p = 1; p < R; ++p) fs[3 + p] = zx[p];
 }
 
 // grad[t] for kernel params from dots dd[t*R + r] = sol[r] . dK_t src[r]
@@ -209,48 +195,61 @@ __global__ void k_grad_assemble(const double *__restrict__ dd, int nth, int R, c
 }
 
 template <typename T>
+__global__ void k_widen(const T *__restrict__ a, double *__restrict__ out, int64_t m) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = (double)a[e];
+}
+
+template <typename T>
 __global__ void k_copy_rows(const T *__restrict__ a, const T *__restrict__ wtz, int64_t m, int R, T *__restrict__ out) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x)
         out[e] = e < m ? a[e] : wtz[e - m];
 }
 
 // ------------------------------------------------------------------ forward
-// Buffers kept between forward and backward (in the stats' solution slot):
-//   sol[0..R) : a = W^T A^{-1} y, then W^T x_p (R x m)
-//   fs        : forward scalars (see k_loglik_assemble), 3 + R doubles
+// Slot kept between forward and backward (the stats' solution buffer):
+//   sol : R x m  W^T x_r in the solve precision (row 0 is a = W^T A^{-1} y)
+//   a64 : m      a in FP64 (for the sigma^2 terms)
+//   fs  : 3 + R + 64 forward scalars (see k_loglik_assemble), then zx (R) and partials
+template <typename T>
+struct Slot {
+    T *sol;
+    double *a64, *fs, *zx, *part;
+};
+
+template <typename T>
+static int slot_get(fkski_stats *st, int R, int64_t m, bool alloc, Slot<T> &sl) {
+    const size_t sol_bytes = sizeof(T) * (size_t)R * m;
+    const size_t a_off = (sol_bytes + 255) / 256 * 256;
+    const size_t need = a_off + sizeof(double) * ((size_t)m + 3 + R + 64 + R + (size_t)RD_BLOCKS * R + 16);
+    void *slot;
+    FK_TRY(grad_sol_buffer(st, alloc ? need : 0, &slot));
+    sl.sol = (T *)slot;
+    sl.a64 = (double *)((char *)slot + a_off);
+    sl.fs = sl.a64 + m;
+    sl.zx = sl.fs + 3 + R + 64;
+    sl.part = sl.zx + R;
+    return FKSKI_OK;
+}
+
 template <typename T>
 static int forward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, double *L, fkski_info *info,
                          cudaStream_t s) {
     const int R = 1 + st->nprobes;
     const int64_t m = st->m;
     const int dt = sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64;
-    Alg3Vecs<T> V;
+    Slot<T> sl;
+    FK_TRY(slot_get<T>(st, R, m, true, sl));
     std::vector<int> it(R, 0);
     std::vector<double> res(R, 0.0);
     int status = FKSKI_OK;
-    if (sizeof(T) == 4)
-        FK_TRY(alg3_for_grad_f32(st, kern, o, R, reinterpret_cast<Alg3Vecs<float> &>(V), it.data(), res.data(), &status, s));
-    else
-        FK_TRY(alg3_for_grad_f64(st, kern, o, R, reinterpret_cast<Alg3Vecs<double> &>(V), it.data(), res.data(), &status, s));
+    FK_TRY(grad_solve(st, kern, o, dt, sl.sol, sl.a64, sl.zx, it.data(), res.data(), &status, s));
     GradView gv;
     FK_TRY(grad_view(st, dt, &gv));
-    // solution slot: sol (R x m) + fs (3 + R + 64) + scratch partials
-    const size_t sol_bytes = sizeof(T) * (size_t)R * m;
-    const size_t need = sol_bytes + sizeof(double) * (size_t)(3 + R + 64 + R + RD_BLOCKS * R + 16);
-    void *slot;
-    FK_TRY(grad_sol_buffer(st, need, &slot));
-    T *sol = (T *)slot;
-    double *fs = (double *)((char *)slot + sol_bytes);
-    double *gx = fs + 3 + R + 64;
-    double *part = gx + R;
-    double *est = (double *)V.u;  // free after the solve: reuse as scratch (R doubles)
+    double *est = sl.part;  // R doubles of scratch
     int *dstat;
     FK_CUDA(cudaMallocAsync((void **)&dstat, sizeof(int), s));
     FK_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int), s));
-    const unsigned gb = (unsigned)std::min<int64_t>(cdiv((int64_t)R * m, 256), 152 * 8);
-    k_wtx<T><<<gb, 256, 0, s>>>(V.xd, V.g, gv.S, R, m, sol);
-    FK_LAUNCH();
-    FK_TRY(rowdots<T>(V.g, V.x, m, R, part, gx, s));
     int kmax = 0;
     for (int r = 1; r < R; ++r) kmax = std::max(kmax, it[r]);
     if (kmax > SLQ_MAXK) return FKSKI_E_UNSUPPORTED;
@@ -258,10 +257,10 @@ static int forward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_
     if (slq_sm > 48 * 1024) FK_CUDA(cudaFuncSetAttribute(k_slq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slq_sm));
     k_slq<<<R - 1, 128, slq_sm, s>>>(gv.hist_a, gv.hist_b, gv.iters, gv.S, R, 0, est, dstat);
     FK_LAUNCH();
-    k_loglik_assemble<<<1, 32, 0, s>>>(gv.S, gx, est, R, (double)st->n, fs);
+    k_loglik_assemble<<<1, 32, 0, s>>>(gv.S, sl.zx, est, R, (double)st->n, sl.fs);
     FK_LAUNCH();
     int hst = 0;
-    FK_CUDA(cudaMemcpyAsync(L, fs, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FK_CUDA(cudaMemcpyAsync(L, sl.fs, sizeof(double), cudaMemcpyDeviceToHost, s));
     FK_CUDA(cudaMemcpyAsync(&hst, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
     FK_CUDA(cudaFreeAsync(dstat, s));
     FK_CUDA(cudaStreamSynchronize(s));
@@ -275,7 +274,7 @@ static int forward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_
         }
         info->status = status;
     }
-    const bool keep = 2 * sol_bytes <= o->iterate_budget_bytes;
+    const bool keep = 2 * sizeof(T) * (size_t)R * m <= o->iterate_budget_bytes;
     grad_sol_mark(st, keep ? 1 : 0, kern, dt);
     if (hst & ST_BREAKDOWN) return FKSKI_E_BREAKDOWN;
     return status;
@@ -298,43 +297,52 @@ static int backward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski
     const int d = st->d;
     GradView gv;
     FK_TRY(grad_view(st, dt, &gv));
-    void *slot;
-    const size_t sol_bytes = sizeof(T) * (size_t)R * m;
-    FK_TRY(grad_sol_buffer(st, 0, &slot));
-    T *sol = (T *)slot;
-    double *fs = (double *)((char *)slot + sol_bytes);
-    double *gx = fs + 3 + R + 64;
-    double *part = gx + R;
+    Slot<T> sl;
+    FK_TRY(slot_get<T>(st, R, m, false, sl));
     const void *bandv, *wtyv, *wtzv;
     FK_TRY(stats_band_as(st, dt, &bandv, &wtyv, &wtzv, s));
     const T *wty = (const T *)wtyv, *wtz = (const T *)wtzv;
     T *src, *dK;
-    double *dd;
+    double *dd, *v64;
+    const size_t sol_bytes = sizeof(T) * (size_t)R * m;
     FK_CUDA(cudaMallocAsync((void **)&src, 2 * sol_bytes, s));
     dK = src + (size_t)R * m;
+    FK_CUDA(cudaMallocAsync((void **)&v64, sizeof(double) * 3 * m, s));
     FK_CUDA(cudaMallocAsync((void **)&dd, sizeof(double) * ((d + 1) * R + 8 + 8), s));
     double *s2dots = dd + (d + 1) * R;
     double *dgrad = s2dots + 4;
     const unsigned gb = (unsigned)std::min<int64_t>(cdiv((int64_t)R * m, 256), 152 * 8);
     // src = [a, W^T z_1, ..., W^T z_T]
-    k_copy_rows<T><<<gb, 256, 0, s>>>(sol, wtz, m, R, src);
+    k_copy_rows<T><<<gb, 256, 0, s>>>(sl.sol, wtz, m, R, src);
     FK_LAUNCH();
     KgOp *kg = gv.kg;
     for (int t = 0; t <= d; ++t) {
         FK_TRY(kgop_set(kg, kern, t, s));
         FK_TRY(kgop_apply(kg, src, dK, R, nullptr, 0.0, s));
-        FK_TRY(rowdots<T>(sol, dK, m, R, part, dd + t * R, s));
+        FK_TRY(rowdots<T>(sl.sol, dK, m, R, sl.part, dd + t * R, s));
     }
-    // sigma^2 terms: v = K a, u = W^T W v
     FK_TRY(kgop_set(kg, kern, -1, s));
-    FK_TRY(kgop_apply(kg, sol, dK, 1, nullptr, 0.0, s));
-    FK_TRY(spmv_for_grad(st, dK, dK + m, 1, dt, s));
-    FK_TRY(rowdots<T>(wty, dK, m, 1, part, s2dots, s));
-    FK_TRY(rowdots<T>(dK, dK + m, m, 1, part, s2dots + 1, s));
-    k_grad_assemble<<<1, 32, 0, s>>>(dd, d + 1, R, fs, s2dots, st->yty, kern->noise_var, dgrad);
+    // sigma^2 terms in FP64: v = K_G a, u = W^T W v; (W^T y).v and v.u
+    double *u64 = v64 + m, *g64 = v64 + 2 * m;
+    KgOp *kg64;
+    FK_TRY(kgop_create(&st->grid, FKSKI_F64, &kg64));
+    int rc = kgop_set(kg64, kern, -1, s);
+    if (rc == FKSKI_OK) rc = kgop_apply(kg64, sl.a64, v64, 1, nullptr, 0.0, s);
+    if (rc == FKSKI_OK) rc = spmv_for_grad(st, v64, u64, 1, FKSKI_F64, s);
+    if (rc == FKSKI_OK) {
+        k_widen<T><<<gb, 256, 0, s>>>(wty, g64, m);
+        rc = cudaGetLastError() == cudaSuccess ? FKSKI_OK : FKSKI_E_CUDA;
+    }
+    if (rc == FKSKI_OK) rc = rowdots<double>(g64, v64, m, 1, sl.part, s2dots, s);
+    if (rc == FKSKI_OK) rc = rowdots<double>(v64, u64, m, 1, sl.part, s2dots + 1, s);
+    cudaStreamSynchronize(s);
+    kgop_destroy(kg64);
+    if (rc != FKSKI_OK) return rc;
+    k_grad_assemble<<<1, 32, 0, s>>>(dd, d + 1, R, sl.fs, s2dots, st->yty, kern->noise_var, dgrad);
     FK_LAUNCH();
     FK_CUDA(cudaMemcpyAsync(grad, dgrad, sizeof(double) * (d + 2), cudaMemcpyDeviceToHost, s));
     FK_CUDA(cudaFreeAsync(src, s));
+    FK_CUDA(cudaFreeAsync(v64, s));
     FK_CUDA(cudaFreeAsync(dd, s));
     FK_CUDA(cudaStreamSynchronize(s));
     (void)o;

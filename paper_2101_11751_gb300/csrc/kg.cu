@@ -607,6 +607,23 @@ static int kgop_apply_any(KgOp *op, const void *v, void *out, int nrhs, const vo
     return bttb_apply<double>(op, (const double *)v, (double *)out, nrhs, (const double *)addv, alpha_dev, alpha, s);
 }
 
+// Allocate the scratch an application to nrhs vectors needs (so graph capture allocates nothing).
+int kgop_reserve(KgOp *op, int nrhs) {
+    const size_t es = esz(op->dtype);
+    const int d = op->d;
+    size_t want = 0;
+    if (op->kind == FKSKI_RBF) {
+        if (d > 1) want = es * (size_t)nrhs * op->m;
+    } else {
+        int64_t big = op->g.M[0];
+        for (int k = 1; k < d; ++k) big *= op->L[k];
+        big = std::max(big, op->m);
+        want = 2 * 2 * es * (size_t)((nrhs + 1) / 2) * big;
+    }
+    if (want == 0) return FKSKI_OK;
+    return ensure(&op->scratch, op->scratch_bytes, want);
+}
+
 int kgop_apply(KgOp *op, const void *v, void *out, int nrhs, const void *addv, double alpha, cudaStream_t s) {
     return kgop_apply_any(op, v, out, nrhs, addv, nullptr, alpha, s);
 }

@@ -1,17 +1,28 @@
 // m-space solves from the sufficient statistics (Sec. 4, App. B) and posterior-mean prediction.
 //
 // B(x) = [(K_G W^T W + sigma^2 I) x, W^T W x] is one banded SpMV (Claim 2, 7^d diagonals) feeding
-// one K_G application (kg.cu).  Two factorized CG variants share it:
-//   Alg. 5 (simplified EFCG): r0 in span(W) via x0 = y / sigma^2; returns W^T x directly.
-//   Alg. 3 (EFCG, x0 = 0): compressed iterates v = W v_hat + c v0 with scalar coefficients;
-//     batched over right-hand sides [y, z_1..z_T] so every B(x) reads the band once.
-// Vectors are FP32 (MIXED) or FP64 (DOUBLE); inner products are summed in FP32 inside a warp and
-// in FP64 across warps and blocks, always in the same order (deterministic).  All scalars live in
-// device memory; iterations run as a captured CUDA graph of `check_every` steps with a device
-// convergence flag tested by the host between graph launches.
+// one K_G application (kg.cu).  One factorized-CG engine runs both variants of App. B:
+//   Alg. 5 (simplified EFCG): x0 = y / sigma^2 puts r0 in span(W); iterates r = W r_hat.
+//   Alg. 3 (EFCG, x0 = 0):     r = W r_hat + c^r r0, p = W p_hat + c^p r0, x = W x_hat + c^x r0,
+//     with the inner products of Claim 4 from the stored W^T r0 and r0^T r0; batched over
+//     right-hand sides [y, z_1..z_T] so every B(x) reads the band once.
+// Each iteration applies B once (to r_hat) and carries A p through the recurrences of the
+// paper's EFCG (z_hat, s_hat).
+//
+// Precision.  The Krylov recurrences (r, p, u, v, s, z) run in the solve precision T (FP32 for
+// MIXED).  The solution x_hat is accumulated in FP64, and every `check_every` iterations the
+// residual is replaced by the true one, r_hat = r_hat_0 - (K W^T W + sigma^2 I) x_hat (Alg. 5) or
+// -(A' x_hat + c^x K W^T r0) (Alg. 3), computed with an FP64 SpMV and FP64 K_G; the search
+// direction's products (z_hat, s_hat) are recomputed from p_hat at the same time.  Convergence
+// is declared only on the true residual.  Without this, EFCG's recurrences for A p drift in
+// FP32 (GP systems have condition numbers ~1e6) and the recursive residual detaches from the
+// true one.  Inner products are FP32 within a warp (MIXED) and FP64 across warps and blocks, in
+// a fixed order (deterministic).  All scalars live in device memory; iterations run as a
+// captured CUDA graph of `check_every` steps plus one replacement, tested between launches.
 #include "fkski_internal.cuh"
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 namespace fk {
@@ -23,13 +34,17 @@ enum {
     F_GAMMA = 0, F_GNEW, F_ALPHA, F_BETA, F_CR, F_CP, F_CX, F_RHO0, F_EPS, F_GKG, F_DELTA, F_RES, NF
 };
 
+// per-rhs state: 0 active, 1 converged on the recursive residual (to confirm), 2 finished
+enum { RS_ACTIVE = 0, RS_TENTATIVE = 1, RS_FINAL = 2 };
+
 struct CgCtl {
     int iter;      // completed alpha steps
-    int all_done;
+    int all_done;  // every rhs tentative or final: iteration kernels idle
+    int all_conf;  // every rhs final: replacement idle, host stops
     int status;    // ST_* bits
     int maxiter;
     int R;
-    int pad[3];
+    int pad[2];
     double sig2;
 };
 
@@ -38,12 +53,12 @@ struct BandOffs {
 };
 
 // ------------------------------------------------------------------ reductions
-// Block partial of a per-thread FP32 value: FP32 warp tree, FP64 across warps.
+// Block partial of per-thread values: FP32 warp tree for FP32 data, FP64 above (and for FP64).
 template <typename T>
 __device__ __forceinline__ double block_sum(T v, double *sh) {
-    float f = (float)v;
-    double dv = 0.0;
+    double dv;
     if (sizeof(T) == 4) {
+        float f = (float)v;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xFFFFFFFFu, f, o);
         dv = (double)f;
@@ -74,24 +89,24 @@ __device__ __forceinline__ double warp_sum_partials(const double *part, int npar
 
 // ------------------------------------------------------------------ band SpMV
 // u[r][j] = sum_o band[o][j] * x[r][j + off(o)]  (entries whose neighbour is off-grid are zero,
-// so the neighbour index is only clamped to stay in memory).  Optional partial dots per rhs:
-// q0 = u.x, q1 = x.g (g per rhs, rhs-major).
-template <typename T, int RB>
-__global__ void __launch_bounds__(CG_T) k_band_spmv(const T *__restrict__ band, int nband, const T *__restrict__ x,
-                                                     T *__restrict__ u, int64_t m, int R, BandOffs offs,
-                                                     double *__restrict__ part, int NQ, const T *__restrict__ g,
-                                                     const CgCtl *__restrict__ ctl, int Rtot, int r0) {
-    if (ctl && ctl->all_done) return;
+// so the neighbour index is only clamped to stay in memory).  Band in TB, vectors in TX.
+// Optional partial dots per rhs: q0 = u.x, q1 = x.g.  `gate` skips the launch's work when set.
+template <typename TB, typename TX, int RB>
+__global__ void __launch_bounds__(CG_T) k_band_spmv(const TB *__restrict__ band, int nband, const TX *__restrict__ x,
+                                                     TX *__restrict__ u, int64_t m, int R, BandOffs offs,
+                                                     double *__restrict__ part, int NQ, const TX *__restrict__ g,
+                                                     const int *__restrict__ gate, int Rtot, int r0) {
+    if (gate && *gate) return;
     __shared__ double sh[CG_T / 32];
-    T dq0[RB], dq1[RB];
+    TX dq0[RB], dq1[RB];
 #pragma unroll
-    for (int k = 0; k < RB; ++k) dq0[k] = dq1[k] = T(0);
+    for (int k = 0; k < RB; ++k) dq0[k] = dq1[k] = TX(0);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
-        T acc[RB];
+        TX acc[RB];
 #pragma unroll
-        for (int k = 0; k < RB; ++k) acc[k] = T(0);
+        for (int k = 0; k < RB; ++k) acc[k] = TX(0);
         for (int o = 0; o < nband; ++o) {
-            const T b = band[(int64_t)o * m + j];
+            const TX b = (TX)band[(int64_t)o * m + j];
             int64_t nb = j + offs.off[o];
             nb = nb < 0 ? 0 : (nb >= m ? m - 1 : nb);
 #pragma unroll
@@ -103,7 +118,7 @@ __global__ void __launch_bounds__(CG_T) k_band_spmv(const T *__restrict__ band, 
             if (k < R) {
                 u[(int64_t)k * m + j] = acc[k];
                 if (part) {
-                    const T xv = x[(int64_t)k * m + j];
+                    const TX xv = x[(int64_t)k * m + j];
                     dq0[k] = fma(acc[k], xv, dq0[k]);
                     if (g) dq1[k] = fma(xv, g[(int64_t)k * m + j], dq1[k]);
                 }
@@ -111,10 +126,10 @@ __global__ void __launch_bounds__(CG_T) k_band_spmv(const T *__restrict__ band, 
     }
     if (!part) return;
     for (int k = 0; k < R && k < RB; ++k) {
-        const double s0 = block_sum<T>(dq0[k], sh);
+        const double s0 = block_sum<TX>(dq0[k], sh);
         if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ * Rtot + (r0 + k) * NQ + 0] = s0;
         if (NQ > 1) {
-            const double s1 = block_sum<T>(dq1[k], sh);
+            const double s1 = block_sum<TX>(dq1[k], sh);
             if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ * Rtot + (r0 + k) * NQ + 1] = s1;
         }
     }
@@ -141,17 +156,18 @@ static BandOffs make_offs(const fkski_grid &g) {
 
 static int grid_blocks(int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(work, CG_T), 152 * 4)); }
 
-template <typename T>
-static int launch_spmv(const T *band, const fkski_grid &g, const T *x, T *u, int64_t m, int R, double *part, int NQ,
-                       const T *gv, const CgCtl *ctl, int nblocks, cudaStream_t s) {
+template <typename TB, typename TX>
+static int launch_spmv(const TB *band, const fkski_grid &g, const TX *x, TX *u, int64_t m, int R, double *part, int NQ,
+                       const TX *gv, const int *gate, int nblocks, cudaStream_t s) {
     const BandOffs bo = make_offs(g);
     const int nb = (int)ipow(7, g.d);
     for (int r0 = 0; r0 < R; r0 += 32) {
         const int Rb = std::min(32, R - r0);
-        const T *xb = x + (int64_t)r0 * m;
-        T *ub = u + (int64_t)r0 * m;
-        const T *gb = gv ? gv + (int64_t)r0 * m : nullptr;
-#define FK_SPMV(RBV) k_band_spmv<T, RBV><<<nblocks, CG_T, 0, s>>>(band, nb, xb, ub, m, Rb, bo, part, NQ, gb, ctl, R, r0)
+        const TX *xb = x + (int64_t)r0 * m;
+        TX *ub = u + (int64_t)r0 * m;
+        const TX *gb = gv ? gv + (int64_t)r0 * m : nullptr;
+#define FK_SPMV(RBV) \
+    k_band_spmv<TB, TX, RBV><<<nblocks, CG_T, 0, s>>>(band, nb, xb, ub, m, Rb, bo, part, NQ, gb, gate, R, r0)
         if (Rb <= 1) FK_SPMV(1);
         else if (Rb <= 2) FK_SPMV(2);
         else if (Rb <= 4) FK_SPMV(4);
@@ -165,21 +181,10 @@ static int launch_spmv(const T *band, const fkski_grid &g, const T *x, T *u, int
 }
 
 // ------------------------------------------------------------------ small vector kernels
-template <typename T>
-__global__ void k_scale(const T *__restrict__ a, T *__restrict__ out, int64_t n, double c) {
+template <typename TI, typename TO>
+__global__ void k_convert_t(const TI *__restrict__ in, TO *__restrict__ out, int64_t n, double c) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        out[e] = (T)(c * (double)a[e]);
-}
-
-// out[r][i] = x[r][i] + coef[r] * g[r][i] (coef from S field F of R), or + c0 * g when S == null
-template <typename T>
-__global__ void k_axpy_rhs(const T *__restrict__ x, const T *__restrict__ g, T *__restrict__ out, int64_t m, int R,
-                           const double *__restrict__ S, int F, double c0) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / m);
-        const double c = S ? S[F * R + r] : c0;
-        out[e] = (T)((double)x[e] + c * (double)g[e]);
-    }
+        out[e] = (TO)(c * (double)in[e]);
 }
 
 template <typename T>
@@ -188,29 +193,49 @@ __global__ void k_convert(const void *__restrict__ in, int in_dbl, T *__restrict
         out[e] = in_dbl ? (T)((const double *)in)[e] : (T)((const float *)in)[e];
 }
 
-// partial dots for NQ pairs (a_q, b_q) per rhs: part[blk][r][q]
-template <typename T, int NQ>
-__global__ void __launch_bounds__(CG_T) k_dots(const T *__restrict__ a0, const T *__restrict__ b0, const T *__restrict__ a1,
-                                               const T *__restrict__ b1, int64_t m, int R, double *__restrict__ part) {
+// out[r][i] = x[r][i] + c_r g[r][i]; c_r = S[F * R + r] or the constant c0.  FP64 result.
+template <typename TG>
+__global__ void k_axpy64(const double *__restrict__ x, const TG *__restrict__ g, double *__restrict__ out, int64_t m,
+                         int R, const double *__restrict__ S, int F, double c0) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / m);
+        const double c = S ? S[F * R + r] : c0;
+        out[e] = fma(c, (double)g[e], x[e]);
+    }
+}
+
+// partial dots of up to 4 pairs per rhs: part[blk][r][q] (NQ = 4 layout); unused pairs are null
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(CG_T) k_dots4(const TA *__restrict__ a0, const TB *__restrict__ b0, const TA *__restrict__ a1,
+                                                const TB *__restrict__ b1, const TA *__restrict__ a2, const TB *__restrict__ b2,
+                                                const TA *__restrict__ a3, const TB *__restrict__ b3, int64_t m, int R,
+                                                double *__restrict__ part, const int *__restrict__ gate) {
+    if (gate && *gate) return;
     __shared__ double sh[CG_T / 32];
+    using Acc = typename std::conditional<sizeof(TA) == 8 || sizeof(TB) == 8, double, float>::type;
     for (int r = 0; r < R; ++r) {
-        T acc[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[q] = T(0);
+        Acc acc[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
         for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
             const int64_t e = (int64_t)r * m + j;
-            acc[0] = fma(a0[e], b0[e], acc[0]);
-            if (NQ > 1) acc[1] = fma(a1[e], b1[e], acc[1]);
+            acc[0] = fma((Acc)a0[e], (Acc)b0[e], acc[0]);
+            if (a1) acc[1] = fma((Acc)a1[e], (Acc)b1[e], acc[1]);
+            if (a2) acc[2] = fma((Acc)a2[e], (Acc)b2[e], acc[2]);
+            if (a3) acc[3] = fma((Acc)a3[e], (Acc)b3[e], acc[3]);
         }
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const double s = block_sum<T>(acc[q], sh);
-            if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ * R + r * NQ + q] = s;
+        for (int q = 0; q < 4; ++q) {
+            const double s = block_sum<Acc>(acc[q], sh);
+            if (threadIdx.x == 0) part[(int64_t)blockIdx.x * 4 * R + r * 4 + q] = s;
         }
     }
 }
 
-// Plain FP64 sums of partials into out[r*NQ + q] (one warp per (r, q)).
+__global__ void k_pick(const double *__restrict__ in, int stride, int n, double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[(int64_t)i * stride];
+}
+
+// out[r * NQ + q] = fixed-order sum of partials (one warp per (r, q))
 __global__ void k_fin_sums(const double *__restrict__ part, int nparts, int R, int NQ, double *__restrict__ out) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= R * NQ) return;
@@ -218,152 +243,40 @@ __global__ void k_fin_sums(const double *__restrict__ part, int nparts, int R, i
     if ((threadIdx.x & 31) == 0) out[w] = s;
 }
 
-// ------------------------------------------------------------------ Alg. 5 kernels
-template <typename T>
-__global__ void __launch_bounds__(CG_T) k_cg5_xr(int64_t m, int R, T *__restrict__ xd, T *__restrict__ r,
-                                                  const T *__restrict__ s, const T *__restrict__ z,
-                                                  const double *__restrict__ S, const int *__restrict__ done,
-                                                  const CgCtl *__restrict__ ctl) {
+// ------------------------------------------------------------------ factorized CG kernels
+// GEN = true: Alg. 3 (compressed coefficients, g = W^T r0, kg = K_G g); false: Alg. 5.
+
+// x_hat (FP64) += alpha p_hat;  r_hat -= alpha (z_hat + c^p kg)
+template <typename T, bool GEN>
+__global__ void __launch_bounds__(CG_T) k_cg_xr(int64_t m, int R, double *__restrict__ x, T *__restrict__ r,
+                                                 const T *__restrict__ p, const T *__restrict__ z, const T *__restrict__ kg,
+                                                 const double *__restrict__ S, const int *__restrict__ state,
+                                                 const CgCtl *__restrict__ ctl) {
     if (ctl->all_done) return;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
         const int rr = (int)(e / m);
-        if (done[rr]) continue;
-        const T a = (T)S[F_ALPHA * R + rr];
-        xd[e] = fma(a, s[e], xd[e]);
-        r[e] = fma(-a, z[e], r[e]);
+        if (state[rr] != RS_ACTIVE) continue;
+        const double a = S[F_ALPHA * R + rr];
+        x[e] = fma(a, (double)p[e], x[e]);
+        const T at = (T)a;
+        T zz = z[e];
+        if (GEN) zz = fma((T)S[F_CP * R + rr], kg[e], zz);
+        r[e] = fma(-at, zz, r[e]);
     }
 }
 
-// s = u + beta s; z = v + beta z; partial q0 = s.z
-template <typename T>
-__global__ void __launch_bounds__(CG_T) k_cg5_sz(int64_t m, int R, const T *__restrict__ u, const T *__restrict__ v,
-                                                  T *__restrict__ s, T *__restrict__ z, const double *__restrict__ S,
-                                                  const int *__restrict__ done, double *__restrict__ part,
-                                                  const CgCtl *__restrict__ ctl) {
-    if (ctl->all_done) return;
-    __shared__ double sh[CG_T / 32];
-    for (int r = 0; r < R; ++r) {
-        T acc = T(0);
-        if (!done[r]) {
-            const T b = (T)S[F_BETA * R + r];
-            for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
-                const int64_t e = (int64_t)r * m + j;
-                const T sn = fma(b, s[e], u[e]);
-                const T zn = fma(b, z[e], v[e]);
-                s[e] = sn;
-                z[e] = zn;
-                acc = fma(sn, zn, acc);
-            }
-        }
-        const double tot = block_sum<T>(acc, sh);
-        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * R + r] = tot;
-    }
-}
-
-// gamma_new = u.r; convergence; beta.  init: first pass (no alpha step taken yet).
-__global__ void k_cg5_fin_gamma(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ done,
-                                int *__restrict__ iters, double *__restrict__ hist_beta, CgCtl *__restrict__ ctl, int init) {
-    if (ctl->all_done) return;
-    const int R = ctl->R;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int r = w; r < R; r += blockDim.x >> 5) {
-        const double g = warp_sum_partials(part, nparts, R, 1, r, 0);
-        if (lane == 0 && !done[r]) {
-            S[F_GNEW * R + r] = g;
-            S[F_RES * R + r] = g;
-            if (!isfinite(g)) {
-                done[r] = 1;
-                iters[r] = init ? 0 : ctl->iter + 1;
-                atomicOr(&ctl->status, ST_BREAKDOWN);
-            } else if (g <= S[F_EPS * R + r]) {
-                done[r] = 1;
-                iters[r] = init ? 0 : ctl->iter + 1;
-            } else if (init) {
-                S[F_BETA * R + r] = 0.0;
-            } else {
-                const double be = g / S[F_GAMMA * R + r];
-                S[F_BETA * R + r] = be;
-                hist_beta[(int64_t)ctl->iter * R + r] = be;
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int all = 1;
-        for (int r = 0; r < R; ++r) all &= done[r];
-        if (all) ctl->all_done = 1;
-    }
-}
-
-// delta = s.z; alpha = gamma_new / delta; iteration counter.
-__global__ void k_cg5_fin_delta(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ done,
-                                int *__restrict__ iters, double *__restrict__ hist_alpha, CgCtl *__restrict__ ctl, int init) {
-    if (ctl->all_done) return;
-    const int R = ctl->R;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = init ? 0 : ctl->iter + 1;
-    for (int r = w; r < R; r += blockDim.x >> 5) {
-        const double dl = warp_sum_partials(part, nparts, R, 1, r, 0);
-        if (lane == 0 && !done[r]) {
-            const double gn = S[F_GNEW * R + r];
-            S[F_DELTA * R + r] = dl;
-            if (!(dl > 0.0) || !isfinite(dl)) {
-                done[r] = 1;
-                iters[r] = k;
-                atomicOr(&ctl->status, ST_BREAKDOWN);
-            } else {
-                const double a = gn / dl;
-                S[F_ALPHA * R + r] = a;
-                S[F_GAMMA * R + r] = gn;
-                if (k < ctl->maxiter) hist_alpha[(int64_t)k * R + r] = a;
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (!init) ctl->iter += 1;
-        int all = 1;
-        for (int r = 0; r < R; ++r) all &= done[r];
-        if (ctl->iter >= ctl->maxiter) {
-            for (int r = 0; r < R; ++r)
-                if (!done[r]) { done[r] = 1; iters[r] = ctl->maxiter; }
-            all = 1;
-        }
-        if (all) ctl->all_done = 1;
-    }
-}
-
-// ------------------------------------------------------------------ Alg. 3 kernels
-// x += a p; xd += a s; r -= a (z + cp kg)
-template <typename T>
-__global__ void __launch_bounds__(CG_T) k_cg3_xr(int64_t m, int R, T *__restrict__ x, T *__restrict__ xd, T *__restrict__ r,
-                                                  const T *__restrict__ p, const T *__restrict__ s, const T *__restrict__ z,
-                                                  const T *__restrict__ kg, const double *__restrict__ S,
-                                                  const int *__restrict__ done, const CgCtl *__restrict__ ctl) {
-    if (ctl->all_done) return;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
-        const int rr = (int)(e / m);
-        if (done[rr]) continue;
-        const T a = (T)S[F_ALPHA * R + rr];
-        const T cp = (T)S[F_CP * R + rr];
-        x[e] = fma(a, p[e], x[e]);
-        xd[e] = fma(a, s[e], xd[e]);
-        r[e] = fma(-a, fma(cp, kg[e], z[e]), r[e]);
-    }
-}
-
-// p = r + beta p; s = u + beta s; z = v + beta z; partial dots s.z, s.kg, p.g, z.g
-template <typename T>
-__global__ void __launch_bounds__(CG_T) k_cg3_psz(int64_t m, int R, const T *__restrict__ r, const T *__restrict__ u,
-                                                   const T *__restrict__ v, T *__restrict__ p, T *__restrict__ s, T *__restrict__ z,
-                                                   const T *__restrict__ g, const T *__restrict__ kg,
-                                                   const double *__restrict__ S, const int *__restrict__ done,
-                                                   double *__restrict__ part, const CgCtl *__restrict__ ctl) {
+// p = r + beta p; s = u + beta s; z = v + beta z; partial dots s.z, s.kg, p.g, z.g (layout NQ = 4)
+template <typename T, bool GEN>
+__global__ void __launch_bounds__(CG_T) k_cg_psz(int64_t m, int R, const T *__restrict__ r, const T *__restrict__ u,
+                                                  const T *__restrict__ v, T *__restrict__ p, T *__restrict__ s, T *__restrict__ z,
+                                                  const T *__restrict__ g, const T *__restrict__ kg,
+                                                  const double *__restrict__ S, const int *__restrict__ state,
+                                                  double *__restrict__ part, const CgCtl *__restrict__ ctl) {
     if (ctl->all_done) return;
     __shared__ double sh[CG_T / 32];
     for (int rr = 0; rr < R; ++rr) {
         T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-        if (!done[rr]) {
+        if (state[rr] == RS_ACTIVE) {
             const T b = (T)S[F_BETA * R + rr];
             for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
                 const int64_t e = (int64_t)rr * m + j;
@@ -374,15 +287,20 @@ __global__ void __launch_bounds__(CG_T) k_cg3_psz(int64_t m, int R, const T *__r
                 s[e] = sn;
                 z[e] = zn;
                 a0 = fma(sn, zn, a0);
-                a1 = fma(sn, kg[e], a1);
-                a2 = fma(pn, g[e], a2);
-                a3 = fma(zn, g[e], a3);
+                if (GEN) {
+                    a1 = fma(sn, kg[e], a1);
+                    a2 = fma(pn, g[e], a2);
+                    a3 = fma(zn, g[e], a3);
+                }
             }
         }
         const double t0 = block_sum<T>(a0, sh);
-        const double t1 = block_sum<T>(a1, sh);
-        const double t2 = block_sum<T>(a2, sh);
-        const double t3 = block_sum<T>(a3, sh);
+        double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+        if (GEN) {
+            t1 = block_sum<T>(a1, sh);
+            t2 = block_sum<T>(a2, sh);
+            t3 = block_sum<T>(a3, sh);
+        }
         if (threadIdx.x == 0) {
             double *pp = part + (int64_t)blockIdx.x * 4 * R + rr * 4;
             pp[0] = t0; pp[1] = t1; pp[2] = t2; pp[3] = t3;
@@ -390,93 +308,138 @@ __global__ void __launch_bounds__(CG_T) k_cg3_psz(int64_t m, int R, const T *__r
     }
 }
 
-// gamma_new = u.r + 2 cr (r.g) + cr^2 rho0 (Claim 4 with the stored W^T r0 and r0^T r0)
-__global__ void k_cg3_fin_gamma(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ done,
-                                int *__restrict__ iters, double *__restrict__ hist_beta, CgCtl *__restrict__ ctl) {
-    if (ctl->all_done) return;
-    const int R = ctl->R;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int r = w; r < R; r += blockDim.x >> 5) {
-        const double ur = warp_sum_partials(part, nparts, R, 2, r, 0);
-        const double rg = warp_sum_partials(part, nparts, R, 2, r, 1);
-        if (lane == 0 && !done[r]) {
-            // the step x += alpha p, r -= alpha A p has just been taken: update the coefficients
-            const double a = S[F_ALPHA * R + r], cp0 = S[F_CP * R + r];
-            S[F_CX * R + r] += a * cp0;
-            const double cr = S[F_CR * R + r] - a * ctl->sig2 * cp0;
-            S[F_CR * R + r] = cr;
-            const double g = ur + 2.0 * cr * rg + cr * cr * S[F_RHO0 * R + r];
-            S[F_GNEW * R + r] = g;
-            S[F_RES * R + r] = g;
-            if (!isfinite(g)) {
-                done[r] = 1;
-                iters[r] = ctl->iter + 1;
-                atomicOr(&ctl->status, ST_BREAKDOWN);
-            } else if (g <= S[F_EPS * R + r]) {
-                done[r] = 1;
-                iters[r] = ctl->iter + 1;
-            } else {
-                const double be = g / S[F_GAMMA * R + r];
-                S[F_BETA * R + r] = be;
-                hist_beta[(int64_t)ctl->iter * R + r] = be;
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int all = 1;
-        for (int r = 0; r < R; ++r) all &= done[r];
-        if (all) ctl->all_done = 1;
-    }
-}
-
-// cp' = cr + beta cp; denom = <p, A p> (Claim 4); alpha for the next step.
-__global__ void k_cg3_fin_delta(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ done,
-                                int *__restrict__ iters, double *__restrict__ hist_alpha, CgCtl *__restrict__ ctl) {
-    if (ctl->all_done) return;
+// gamma = <r, r> from u.r (q0) and r.g (q1) (Claim 4).  step: the x/r update of this iteration was
+// applied (GEN: update c^x, c^r first).  replace: r was just replaced by the true residual
+// (GEN: c^r = 1 - sigma^2 c^x); decide final / resume on it.  Otherwise: recursive test, beta.
+template <bool GEN>
+__global__ void k_cg_fin_gamma(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ state,
+                               int *__restrict__ iters, double *__restrict__ hist_beta, CgCtl *__restrict__ ctl,
+                               int mode /*0 iterate, 1 init, 2 replace*/) {
+    if (mode == 2 ? ctl->all_conf : ctl->all_done) return;
     const int R = ctl->R;
     const double s2 = ctl->sig2;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = ctl->iter + 1;
+    const int NQ = GEN ? 2 : 1;
     for (int r = w; r < R; r += blockDim.x >> 5) {
-        const double sz = warp_sum_partials(part, nparts, R, 4, r, 0);
-        const double skg = warp_sum_partials(part, nparts, R, 4, r, 1);
-        const double pg = warp_sum_partials(part, nparts, R, 4, r, 2);
-        const double zg = warp_sum_partials(part, nparts, R, 4, r, 3);
-        if (lane == 0 && !done[r]) {
-            const double cp = S[F_CR * R + r] + S[F_BETA * R + r] * S[F_CP * R + r];
-            const double cq = s2 * cp;
-            const double den = sz + cp * skg + cq * pg + cp * zg + cp * cp * S[F_GKG * R + r] + cp * cq * S[F_RHO0 * R + r];
-            if (!(den > 0.0) || !isfinite(den)) {
-                done[r] = 1;
-                iters[r] = k;
-                atomicOr(&ctl->status, ST_BREAKDOWN);
+        const double ur = warp_sum_partials(part, nparts, R, NQ, r, 0);
+        const double rg = GEN ? warp_sum_partials(part, nparts, R, NQ, r, 1) : 0.0;
+        if (lane != 0) continue;
+        const int stt = state[r];
+        if (mode == 2 ? stt == RS_FINAL : stt != RS_ACTIVE) continue;
+        double cr = 0.0;
+        if (GEN) {
+            if (mode == 0) {
+                const double a = S[F_ALPHA * R + r], cp0 = S[F_CP * R + r];
+                S[F_CX * R + r] += a * cp0;
+                cr = S[F_CR * R + r] - a * s2 * cp0;
+            } else if (mode == 2) {
+                cr = 1.0 - s2 * S[F_CX * R + r];
             } else {
-                const double gn = S[F_GNEW * R + r];
-                const double a = gn / den;
-                S[F_CP * R + r] = cp;
-                S[F_ALPHA * R + r] = a;
-                S[F_GAMMA * R + r] = gn;
-                if (k < ctl->maxiter) hist_alpha[(int64_t)k * R + r] = a;
+                cr = S[F_CR * R + r];
             }
+            S[F_CR * R + r] = cr;
+        }
+        const double g = ur + (GEN ? 2.0 * cr * rg + cr * cr * S[F_RHO0 * R + r] : 0.0);
+        S[F_RES * R + r] = g;
+        if (!isfinite(g)) {
+            state[r] = RS_FINAL;
+            iters[r] = ctl->iter;
+            atomicOr(&ctl->status, ST_BREAKDOWN);
+            continue;
+        }
+        const bool conv = g <= S[F_EPS * R + r];
+        if (mode == 2) {
+            // true residual: finish, or resume the iteration from it
+            S[F_GAMMA * R + r] = g;
+            S[F_GNEW * R + r] = g;
+            if (conv) {
+                if (stt == RS_ACTIVE) iters[r] = ctl->iter;
+                state[r] = RS_FINAL;
+            } else {
+                state[r] = RS_ACTIVE;
+            }
+            continue;
+        }
+        S[F_GNEW * R + r] = g;
+        if (conv) {
+            state[r] = RS_TENTATIVE;
+            iters[r] = mode == 1 ? 0 : ctl->iter + 1;
+        } else if (mode == 1) {
+            S[F_BETA * R + r] = 0.0;
+        } else {
+            const double be = g / S[F_GAMMA * R + r];
+            S[F_BETA * R + r] = be;
+            hist_beta[(int64_t)ctl->iter * R + r] = be;
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        ctl->iter += 1;
         int all = 1;
-        for (int r = 0; r < R; ++r) all &= done[r];
-        if (ctl->iter >= ctl->maxiter) {
-            for (int r = 0; r < R; ++r)
-                if (!done[r]) { done[r] = 1; iters[r] = ctl->maxiter; }
-            all = 1;
-        }
-        if (all) ctl->all_done = 1;
+        for (int r = 0; r < R; ++r) all &= state[r] != RS_ACTIVE;
+        ctl->all_done = all;
     }
 }
 
-// Alg. 3 start: x0 = 0, r0 = b: cr = cp = 1, cx = 0, gamma = rho0, alpha_0 = rho0 / (g.Kg + s2 rho0).
-__global__ void k_cg3_init(double *__restrict__ S, const double *__restrict__ gkg, int *__restrict__ done,
+// alpha = gamma / <p, A p> (Claim 4 terms for GEN).  mode 0: after an iteration (records the
+// next alpha and advances the counter); 1: init; 2: after a replacement (same step index).
+template <bool GEN>
+__global__ void k_cg_fin_delta(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ state,
+                               int *__restrict__ iters, double *__restrict__ hist_alpha, CgCtl *__restrict__ ctl, int mode) {
+    if (mode == 2 ? ctl->all_conf : ctl->all_done) return;
+    const int R = ctl->R;
+    const double s2 = ctl->sig2;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = mode == 0 ? ctl->iter + 1 : ctl->iter;
+    for (int r = w; r < R; r += blockDim.x >> 5) {
+        const double sz = warp_sum_partials(part, nparts, R, 4, r, 0);
+        const double skg = GEN ? warp_sum_partials(part, nparts, R, 4, r, 1) : 0.0;
+        const double pg = GEN ? warp_sum_partials(part, nparts, R, 4, r, 2) : 0.0;
+        const double zg = GEN ? warp_sum_partials(part, nparts, R, 4, r, 3) : 0.0;
+        if (lane != 0 || state[r] != RS_ACTIVE) continue;
+        double den = sz;
+        if (GEN) {
+            const double cp = mode == 2 ? S[F_CP * R + r] : S[F_CR * R + r] + S[F_BETA * R + r] * S[F_CP * R + r];
+            const double cq = s2 * cp;
+            den += cp * skg + cq * pg + cp * zg + cp * cp * S[F_GKG * R + r] + cp * cq * S[F_RHO0 * R + r];
+            S[F_CP * R + r] = cp;
+        }
+        S[F_DELTA * R + r] = den;
+        if (!(den > 0.0) || !isfinite(den)) {
+            state[r] = RS_FINAL;
+            iters[r] = k;
+            atomicOr(&ctl->status, ST_BREAKDOWN);
+            continue;
+        }
+        const double gn = S[F_GNEW * R + r];
+        const double a = gn / den;
+        S[F_ALPHA * R + r] = a;
+        S[F_GAMMA * R + r] = gn;
+        if (k < ctl->maxiter) hist_alpha[(int64_t)k * R + r] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (mode == 0) ctl->iter += 1;
+        int all = 1, conf = 1;
+        for (int r = 0; r < R; ++r) {
+            all &= state[r] != RS_ACTIVE;
+            conf &= state[r] == RS_FINAL;
+        }
+        if (ctl->iter >= ctl->maxiter) all = 1;  // stop iterating; the replacement finalises
+        ctl->all_done = all;
+        if (mode == 2) {
+            if (ctl->iter >= ctl->maxiter) {
+                for (int r = 0; r < R; ++r)
+                    if (state[r] != RS_FINAL) { state[r] = RS_FINAL; iters[r] = ctl->maxiter; }
+                conf = 1;
+            }
+            ctl->all_conf = conf;
+        }
+    }
+}
+
+// Alg. 3 start (x0 = 0, r0 = b): c^r = c^p = 1, c^x = 0, gamma = rho0,
+// alpha_0 = rho0 / (g.K_G g + sigma^2 rho0).
+__global__ void k_cg3_init(double *__restrict__ S, const double *__restrict__ gkg, int *__restrict__ state,
                            int *__restrict__ iters, double *__restrict__ hist_alpha, CgCtl *__restrict__ ctl) {
     const int R = ctl->R;
     const double s2 = ctl->sig2;
@@ -485,30 +448,49 @@ __global__ void k_cg3_init(double *__restrict__ S, const double *__restrict__ gk
         const double den = gkg[r] + s2 * rho0;
         S[F_GKG * R + r] = gkg[r];
         S[F_GAMMA * R + r] = rho0;
+        S[F_GNEW * R + r] = rho0;
         S[F_RES * R + r] = rho0;
         S[F_CP * R + r] = 1.0;
-        done[r] = 0;
+        S[F_CR * R + r] = 1.0;
+        S[F_CX * R + r] = 0.0;
+        state[r] = RS_ACTIVE;
         iters[r] = 0;
         if (rho0 <= S[F_EPS * R + r]) {
-            done[r] = 1;
+            state[r] = RS_FINAL;
             continue;
         }
         if (!(den > 0.0) || !isfinite(den)) {
-            done[r] = 1;
+            state[r] = RS_FINAL;
             atomicOr(&ctl->status, ST_BREAKDOWN);
             continue;
         }
         const double a = rho0 / den;
         S[F_ALPHA * R + r] = a;
-        S[F_CX * R + r] = 0.0;
-        S[F_CR * R + r] = 1.0;
         hist_alpha[r] = a;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         int all = 1;
-        for (int r = 0; r < R; ++r) all &= done[r];
+        for (int r = 0; r < R; ++r) all &= state[r] == RS_FINAL;
         ctl->all_done = all;
+        ctl->all_conf = all;
+    }
+}
+
+// True residual from w64 = (K W^T W + sigma^2 I) x_hat (FP64):
+//   Alg. 5: r_hat = r_hat_0 - w64;   Alg. 3: r_hat = -(w64 + c^x kg)
+template <typename T, bool GEN>
+__global__ void k_cg_resid(int64_t m, int R, const double *__restrict__ w64, const double *__restrict__ r0,
+                           const T *__restrict__ kg, T *__restrict__ r, const double *__restrict__ S,
+                           const int *__restrict__ state, const CgCtl *__restrict__ ctl) {
+    if (ctl->all_conf) return;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int rr = (int)(e / m);
+        if (state[rr] == RS_FINAL) continue;
+        double v;
+        if (GEN) v = -fma(S[F_CX * R + rr], (double)kg[e], w64[e]);
+        else v = r0[e] - w64[e];
+        r[e] = (T)v;
     }
 }
 
@@ -519,12 +501,12 @@ struct SolveWork {
     size_t buf_bytes;
     double *S;
     double *part;
-    int *done;
+    int *state;
     int *iters;
     CgCtl *ctl;
-    double *hist;     // alpha then beta, maxiter x R each
+    double *hist;     // alpha then beta, (maxiter + 1) x R each
     size_t hist_cap;  // entries per array
-    int *hflag;       // pinned host: all_done
+    int *hflag;       // pinned host: all_conf
     cudaStream_t ws;  // internal stream for graph capture (the caller's may be the legacy stream)
     cudaEvent_t ev;
     // stored solutions for the log-likelihood backward pass
@@ -542,7 +524,7 @@ void free_solve_work(SolveWork *w) {
     if (w->buf) cudaFree(w->buf);
     if (w->S) cudaFree(w->S);
     if (w->part) cudaFree(w->part);
-    if (w->done) cudaFree(w->done);
+    if (w->state) cudaFree(w->state);
     if (w->iters) cudaFree(w->iters);
     if (w->ctl) cudaFree(w->ctl);
     if (w->hist) cudaFree(w->hist);
@@ -572,7 +554,7 @@ static int work_get(fkski_stats *st, SolveWork **out) {
         st->work = w;
         FK_TRY(dev_alloc((void **)&w->S, sizeof(double) * (NF * MAX_R + MAX_R + 8)));
         FK_TRY(dev_alloc((void **)&w->part, sizeof(double) * NPART * 4 * MAX_R));
-        FK_TRY(dev_alloc((void **)&w->done, sizeof(int) * MAX_R));
+        FK_TRY(dev_alloc((void **)&w->state, sizeof(int) * MAX_R));
         FK_TRY(dev_alloc((void **)&w->iters, sizeof(int) * MAX_R));
         FK_TRY(dev_alloc((void **)&w->ctl, sizeof(CgCtl)));
         if (cudaMallocHost((void **)&w->hflag, sizeof(int) * 4) != cudaSuccess) {
@@ -650,16 +632,16 @@ int stats_band_as(fkski_stats *st, int dtype, const void **band, const void **wt
     return stats_as<double>(st, (const double **)band, (const double **)wty, (const double **)wtz, s);
 }
 
-// Run the captured iteration body (captured on w->ws) until convergence or maxiter; the
-// internal stream first waits for the caller's stream, and the caller's stream waits for it.
+// Run the captured chunk (captured on w->ws) until every rhs is final; the internal stream first
+// waits for the caller's stream, and the caller's stream waits for it at the end.
 static int run_graph_loop(cudaGraphExec_t exec, SolveWork *w, int maxiter, int check, cudaStream_t s) {
     FK_CUDA(cudaEventRecord(w->ev, s));
     FK_CUDA(cudaStreamWaitEvent(w->ws, w->ev, 0));
     int done_iters = 0;
-    while (done_iters < maxiter + check) {
+    while (done_iters <= maxiter + check) {
         FK_CUDA(cudaGraphLaunch(exec, w->ws));
         done_iters += check;
-        FK_CUDA(cudaMemcpyAsync(w->hflag, &w->ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, w->ws));
+        FK_CUDA(cudaMemcpyAsync(w->hflag, &w->ctl->all_conf, sizeof(int), cudaMemcpyDeviceToHost, w->ws));
         FK_CUDA(cudaStreamSynchronize(w->ws));
         if (w->hflag[0]) break;
     }
@@ -669,138 +651,38 @@ static int run_graph_loop(cudaGraphExec_t exec, SolveWork *w, int maxiter, int c
 }
 
 template <typename T>
-struct Alg3Vecs {
-    T *r, *p, *x, *xd, *u, *v, *s, *z, *g, *kg;
+struct CgVecs {
+    T *r, *p, *u, *v, *s, *z, *g, *kg;     // solve precision
+    double *x, *r0, *t64, *w64;             // FP64: solution, Alg. 5 r_hat_0, temporaries
 };
 
-// ------------------------------------------------------------------ Alg. 5 solve
-template <typename T>
-static int solve_alg5(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, T *a_out, T *v_out,
-                      fkski_info *info, cudaStream_t s) {
+// One factorized-CG solve (R right-hand sides).  GEN: Alg. 3 on b = [y, z_1..] with
+// g = [W^T y, W^T z_1..], rho0 = [y^T y, z_p^T z_p]; else Alg. 5 on y (R = 1).
+// On return V.x holds x_hat (FP64) and the scalars / histories stay in the workspace.
+template <typename T, bool GEN>
+static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, CgVecs<T> &V,
+                     int *iters_host, double *res_host, int *status_out, cudaStream_t s) {
     SolveWork *w;
     FK_TRY(work_get(st, &w));
     const int dt = sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64;
-    KgOp *kg;
+    KgOp *kg, *kg64;
     FK_TRY(work_kg(st, w, dt, &kg));
+    FK_TRY(work_kg(st, w, FKSKI_F64, &kg64));
     FK_TRY(kgop_set(kg, kern, -1, s));
+    if (kg64 != kg) FK_TRY(kgop_set(kg64, kern, -1, s));
     const T *band, *wty, *wtz;
     FK_TRY(stats_as<T>(st, &band, &wty, &wtz, s));
     const int64_t m = st->m;
-    const int R = 1;
-    FK_TRY(work_buf(w, sizeof(T) * 6 * m));
-    T *r = (T *)w->buf, *u = r + m, *v = u + m, *sv = v + m, *z = sv + m, *xd = z + m;
-    FK_TRY(work_hist(w, R, o->maxiter));
-    double *ha = w->hist, *hb = w->hist + w->hist_cap;
-    const double s2 = kern->noise_var;
-    // scalars
-    CgCtl hc;
-    memset(&hc, 0, sizeof(hc));
-    hc.maxiter = o->maxiter;
-    hc.R = R;
-    hc.sig2 = s2;
-    FK_CUDA(cudaMemcpyAsync(w->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, s));
-    double hS[NF];
-    memset(hS, 0, sizeof(hS));
-    hS[F_EPS] = o->rtol * o->rtol * st->yty;
-    hS[F_RHO0] = st->yty;
-    FK_CUDA(cudaMemcpyAsync(w->S, hS, sizeof(hS), cudaMemcpyHostToDevice, s));
-    FK_CUDA(cudaMemsetAsync(w->done, 0, sizeof(int) * R, s));
-    FK_CUDA(cudaMemsetAsync(w->iters, 0, sizeof(int) * R, s));
-    FK_CUDA(cudaMemsetAsync(sv, 0, sizeof(T) * 2 * m, s));  // s, z
-    FK_CUDA(cudaMemsetAsync(xd, 0, sizeof(T) * m, s));
-    // r0_hat = -K_G W^T y / sigma^2
-    FK_TRY(kgop_apply(kg, wty, u, 1, nullptr, 0.0, s));
-    const unsigned gb = (unsigned)grid_blocks(m);
-    k_scale<T><<<gb, CG_T, 0, s>>>(u, r, m, -1.0 / s2);
-    FK_LAUNCH();
-    const double *sig2_dev = &w->ctl->sig2;
-    // init pass: B(r0), gamma0, s0 = u0, z0 = v0, delta0, alpha0
-    FK_TRY(launch_spmv<T>(band, st->grid, r, u, m, R, w->part, 1, nullptr, w->ctl, gb, s));
-    k_cg5_fin_gamma<<<1, 256, 0, s>>>(w->part, gb, w->S, w->done, w->iters, hb, w->ctl, 1);
-    FK_LAUNCH();
-    FK_TRY(kgop_apply_dev(kg, u, v, 1, r, sig2_dev, s));
-    k_cg5_sz<T><<<gb, CG_T, 0, s>>>(m, R, u, v, sv, z, w->S, w->done, w->part, w->ctl);
-    FK_LAUNCH();
-    k_cg5_fin_delta<<<1, 256, 0, s>>>(w->part, gb, w->S, w->done, w->iters, ha, w->ctl, 1);
-    FK_LAUNCH();
-    // capture `check` iterations
-    const int check = std::max(1, o->check_every);
-    cudaGraph_t graph;
-    cudaGraphExec_t exec;
-    const cudaStream_t cs = w->ws;
-    FK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
-    int rc = FKSKI_OK;
-    for (int it = 0; it < check && rc == FKSKI_OK; ++it) {
-        k_cg5_xr<T><<<gb, CG_T, 0, cs>>>(m, R, xd, r, sv, z, w->S, w->done, w->ctl);
-        rc = launch_spmv<T>(band, st->grid, r, u, m, R, w->part, 1, nullptr, w->ctl, gb, cs);
-        if (rc) break;
-        k_cg5_fin_gamma<<<1, 256, 0, cs>>>(w->part, gb, w->S, w->done, w->iters, hb, w->ctl, 0);
-        rc = kgop_apply_dev(kg, u, v, 1, r, sig2_dev, cs);
-        if (rc) break;
-        k_cg5_sz<T><<<gb, CG_T, 0, cs>>>(m, R, u, v, sv, z, w->S, w->done, w->part, w->ctl);
-        k_cg5_fin_delta<<<1, 256, 0, cs>>>(w->part, gb, w->S, w->done, w->iters, ha, w->ctl, 0);
-    }
-    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-    if (rc != FKSKI_OK) return rc;
-    FK_CUDA(ce);
-    FK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-    rc = run_graph_loop(exec, w, o->maxiter, check, s);
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
-    if (rc) return rc;
-    // a = xd + W^T y / sigma^2 ; v = K a
-    k_axpy_rhs<T><<<gb, CG_T, 0, s>>>(xd, wty, a_out, m, 1, nullptr, 0, 1.0 / s2);
-    FK_LAUNCH();
-    FK_TRY(kgop_apply(kg, a_out, v_out, 1, nullptr, 0.0, s));
-    // report
-    CgCtl hc2;
-    int hit = 0;
-    double hS2[NF * 1];
-    FK_CUDA(cudaMemcpyAsync(&hc2, w->ctl, sizeof(hc2), cudaMemcpyDeviceToHost, s));
-    FK_CUDA(cudaMemcpyAsync(&hit, w->iters, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FK_CUDA(cudaMemcpyAsync(hS2, w->S, sizeof(hS2), cudaMemcpyDeviceToHost, s));
-    FK_CUDA(cudaStreamSynchronize(s));
-    const double res = std::sqrt(std::max(hS2[F_RES], 0.0) / std::max(st->yty, 1e-300));
-    int status = FKSKI_OK;
-    if (hc2.status & ST_BREAKDOWN) status = FKSKI_E_BREAKDOWN;
-    else if (hS2[F_RES] > hS2[F_EPS]) status = FKSKI_E_NOT_CONVERGED;
-    if (info) {
-        info->iters = hit;
-        info->iters_rhs[0] = hit;
-        info->rel_residual = res;
-        info->status = status;
-    }
-    return status;
-}
-
-// ------------------------------------------------------------------ Alg. 3 batched solve
-// Right-hand sides: b_0 = y (g = W^T y, rho0 = y^T y) and b_p = z_p (g = W^T z_p, rho0 = z_p^T z_p).
-// Leaves the compressed solutions in the work buffer (see Alg3Vecs) and the CG coefficients in
-// the history arrays.
-template <typename T>
-int solve_alg3_batched(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, Alg3Vecs<T> &V,
-                       int *iters_host, double *res_host, int *status_out, cudaStream_t s) {
-    SolveWork *w;
-    FK_TRY(work_get(st, &w));
-    const int dt = sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64;
-    KgOp *kg;
-    FK_TRY(work_kg(st, w, dt, &kg));
-    FK_TRY(kgop_set(kg, kern, -1, s));
-    const T *band, *wty, *wtz;
-    FK_TRY(stats_as<T>(st, &band, &wty, &wtz, s));
-    const int64_t m = st->m;
-    FK_TRY(work_buf(w, sizeof(T) * 10 * (size_t)R * m));
+    const size_t nT = (size_t)R * m;
+    FK_TRY(work_buf(w, sizeof(T) * 8 * nT + sizeof(double) * 4 * nT + 256));
     T *b = (T *)w->buf;
-    V.r = b; V.p = b + R * m; V.x = b + 2 * R * m; V.xd = b + 3 * R * m; V.u = b + 4 * R * m;
-    V.v = b + 5 * R * m; V.s = b + 6 * R * m; V.z = b + 7 * R * m; V.g = b + 8 * R * m; V.kg = b + 9 * R * m;
+    V.r = b; V.p = b + nT; V.u = b + 2 * nT; V.v = b + 3 * nT; V.s = b + 4 * nT; V.z = b + 5 * nT;
+    V.g = b + 6 * nT; V.kg = b + 7 * nT;
+    double *d64 = (double *)((char *)w->buf + ((sizeof(T) * 8 * nT + 255) / 256) * 256);
+    V.x = d64; V.r0 = d64 + nT; V.t64 = d64 + 2 * nT; V.w64 = d64 + 3 * nT;
     FK_TRY(work_hist(w, R, o->maxiter));
     double *ha = w->hist, *hb = w->hist + w->hist_cap;
     const double s2 = kern->noise_var;
-    // g = [W^T y, W^T z_1..]
-    FK_CUDA(cudaMemcpyAsync(V.g, wty, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
-    if (R > 1) FK_CUDA(cudaMemcpyAsync(V.g + m, wtz, sizeof(T) * (R - 1) * m, cudaMemcpyDeviceToDevice, s));
-    FK_CUDA(cudaMemsetAsync(b, 0, sizeof(T) * 8 * (size_t)R * m, s));
-    FK_TRY(kgop_apply(kg, V.g, V.kg, R, nullptr, 0.0, s));
     CgCtl hc;
     memset(&hc, 0, sizeof(hc));
     hc.maxiter = o->maxiter;
@@ -814,31 +696,90 @@ int solve_alg3_batched(fkski_stats *st, const fkski_kernel *kern, const fkski_op
         hS[F_EPS * R + r] = o->rtol * o->rtol * rho;
     }
     FK_CUDA(cudaMemcpyAsync(w->S, hS.data(), sizeof(double) * NF * R, cudaMemcpyHostToDevice, s));
+    FK_CUDA(cudaMemsetAsync(w->state, 0, sizeof(int) * R, s));
+    FK_CUDA(cudaMemsetAsync(w->iters, 0, sizeof(int) * R, s));
+    FK_CUDA(cudaMemsetAsync(b, 0, sizeof(T) * 6 * nT, s));
+    FK_CUDA(cudaMemsetAsync(V.x, 0, sizeof(double) * nT, s));
     const unsigned gb = (unsigned)grid_blocks(m);
-    double *gkg = w->S + NF * MAX_R;  // scratch after the fields
-    k_dots<T, 1><<<gb, CG_T, 0, s>>>(V.g, V.kg, nullptr, nullptr, m, R, w->part);
-    FK_LAUNCH();
-    // reuse w->part tail for the sums
-    k_fin_sums<<<(unsigned)cdiv(R * 32, 256), 256, 0, s>>>(w->part, gb, R, 1, gkg);
-    FK_LAUNCH();
-    k_cg3_init<<<1, 256, 0, s>>>(w->S, gkg, w->done, w->iters, ha, w->ctl);
-    FK_LAUNCH();
+    const unsigned gv = (unsigned)std::min<int64_t>(cdiv((int64_t)nT, 256), 152 * 8);
     const double *sig2_dev = &w->ctl->sig2;
+    const int *gate_done = &w->ctl->all_done;
+    const int *gate_conf = &w->ctl->all_conf;
+    if (GEN) {
+        FK_CUDA(cudaMemcpyAsync(V.g, wty, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
+        if (R > 1) FK_CUDA(cudaMemcpyAsync(V.g + m, wtz, sizeof(T) * (R - 1) * m, cudaMemcpyDeviceToDevice, s));
+        FK_TRY(kgop_apply(kg, V.g, V.kg, R, nullptr, 0.0, s));
+        double *gkg = w->S + NF * MAX_R;
+        k_dots4<T, T><<<gb, CG_T, 0, s>>>(V.g, V.kg, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R, w->part,
+                                          nullptr);
+        FK_LAUNCH();
+        k_fin_sums<<<(unsigned)cdiv(R * 4 * 32, 256), 256, 0, s>>>(w->part, gb, R, 4, V.t64);
+        FK_LAUNCH();
+        k_pick<<<1, 128, 0, s>>>(V.t64, 4, R, gkg);
+        FK_LAUNCH();
+        k_cg3_init<<<1, 128, 0, s>>>(w->S, gkg, w->state, w->iters, ha, w->ctl);
+        FK_LAUNCH();
+    } else {
+        // r_hat_0 = -K_G W^T y / sigma^2 in FP64; r_hat = r_hat_0 in T
+        k_convert_t<T, double><<<gv, 256, 0, s>>>(wty, V.t64, m, 1.0);
+        FK_LAUNCH();
+        FK_TRY(kgop_apply(kg64, V.t64, V.w64, 1, nullptr, 0.0, s));
+        k_convert_t<double, double><<<gv, 256, 0, s>>>(V.w64, V.r0, m, -1.0 / s2);
+        FK_LAUNCH();
+        k_convert_t<double, T><<<gv, 256, 0, s>>>(V.r0, V.r, m, 1.0);
+        FK_LAUNCH();
+        FK_TRY((launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, 1, (const T *)nullptr, nullptr, gb, s)));
+        k_cg_fin_gamma<false><<<1, 256, 0, s>>>(w->part, gb, w->S, w->state, w->iters, hb, w->ctl, 1);
+        FK_LAUNCH();
+        FK_TRY(kgop_apply_dev(kg, V.u, V.v, R, V.r, sig2_dev, s));
+        k_cg_psz<T, false><<<gb, CG_T, 0, s>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->S, w->state, w->part, w->ctl);
+        FK_LAUNCH();
+        k_cg_fin_delta<false><<<1, 256, 0, s>>>(w->part, gb, w->S, w->state, w->iters, ha, w->ctl, 1);
+        FK_LAUNCH();
+    }
+    FK_TRY(kgop_reserve(kg, R));
+    FK_TRY(kgop_reserve(kg64, R));
+    // capture: `check` iterations + one residual replacement
     const int check = std::max(1, o->check_every);
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     const cudaStream_t cs = w->ws;
+    const int NQ = GEN ? 2 : 1;
     FK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     int rc = FKSKI_OK;
     for (int it = 0; it < check && rc == FKSKI_OK; ++it) {
-        k_cg3_xr<T><<<gb, CG_T, 0, cs>>>(m, R, V.x, V.xd, V.r, V.p, V.s, V.z, V.kg, w->S, w->done, w->ctl);
-        rc = launch_spmv<T>(band, st->grid, V.r, V.u, m, R, w->part, 2, V.g, w->ctl, gb, cs);
+        k_cg_xr<T, GEN><<<gv, CG_T, 0, cs>>>(m, R, V.x, V.r, V.p, V.z, V.kg, w->S, w->state, w->ctl);
+        rc = launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, gate_done, gb, cs);
         if (rc) break;
-        k_cg3_fin_gamma<<<1, 256, 0, cs>>>(w->part, gb, w->S, w->done, w->iters, hb, w->ctl);
+        k_cg_fin_gamma<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->iters, hb, w->ctl, 0);
         rc = kgop_apply_dev(kg, V.u, V.v, R, V.r, sig2_dev, cs);
         if (rc) break;
-        k_cg3_psz<T><<<gb, CG_T, 0, cs>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->S, w->done, w->part, w->ctl);
-        k_cg3_fin_delta<<<1, 256, 0, cs>>>(w->part, gb, w->S, w->done, w->iters, ha, w->ctl);
+        k_cg_psz<T, GEN><<<gb, CG_T, 0, cs>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->S, w->state, w->part, w->ctl);
+        k_cg_fin_delta<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->iters, ha, w->ctl, 0);
+    }
+    if (rc == FKSKI_OK) {
+        // true residual in FP64: w64 = K (W^T W x_hat) + sigma^2 x_hat
+        rc = launch_spmv<T, double>(band, st->grid, V.x, V.t64, m, R, nullptr, 1, nullptr, gate_conf, gb, cs);
+        if (rc == FKSKI_OK) rc = kgop_apply_dev(kg64, V.t64, V.w64, R, V.x, sig2_dev, cs);
+        if (rc == FKSKI_OK) {
+            k_cg_resid<T, GEN><<<gv, CG_T, 0, cs>>>(m, R, V.w64, V.r0, V.kg, V.r, w->S, w->state, w->ctl);
+            rc = launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, gate_conf, gb, cs);
+        }
+        if (rc == FKSKI_OK) {
+            k_cg_fin_gamma<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->iters, hb, w->ctl, 2);
+            rc = kgop_apply_dev(kg, V.u, V.v, R, V.r, sig2_dev, cs);
+        }
+        // search direction products recomputed from p_hat: s = W^T W p, z = (K W^T W + sigma^2) p
+        if (rc == FKSKI_OK) rc = launch_spmv<T, T>(band, st->grid, V.p, V.s, m, R, nullptr, 1, nullptr, gate_conf, gb, cs);
+        if (rc == FKSKI_OK) rc = kgop_apply_dev(kg, V.s, V.z, R, V.p, sig2_dev, cs);
+        if (rc == FKSKI_OK) {
+            if (GEN)
+                k_dots4<T, T><<<gb, CG_T, 0, cs>>>(V.s, V.z, V.s, V.kg, V.p, V.g, V.z, V.g, m, R, w->part, gate_conf);
+            else
+                k_dots4<T, T><<<gb, CG_T, 0, cs>>>(V.s, V.z, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R,
+                                                   w->part, gate_conf);
+            k_cg_fin_delta<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->iters, ha, w->ctl, 2);
+        }
     }
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (rc != FKSKI_OK) return rc;
@@ -864,26 +805,44 @@ int solve_alg3_batched(fkski_stats *st, const fkski_kernel *kern, const fkski_op
     return FKSKI_OK;
 }
 
-template int solve_alg3_batched<float>(fkski_stats *, const fkski_kernel *, const fkski_opts *, int, Alg3Vecs<float> &,
-                                       int *, double *, int *, cudaStream_t);
-template int solve_alg3_batched<double>(fkski_stats *, const fkski_kernel *, const fkski_opts *, int, Alg3Vecs<double> &,
-                                        int *, double *, int *, cudaStream_t);
-
-template <typename T>
-static int solve_alg3_mean(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, T *a_out, T *v_out,
-                           fkski_info *info, cudaStream_t s) {
-    Alg3Vecs<T> V;
-    int it = 0, status = 0;
-    double res = 0.0;
-    FK_TRY(solve_alg3_batched<T>(st, kern, o, 1, V, &it, &res, &status, s));
+// W^T x for each rhs in FP64: W^T W x_hat (+ c^x g for Alg. 3, + W^T y / sigma^2 for Alg. 5)
+template <typename T, bool GEN>
+static int fcg_wtx64(fkski_stats *st, CgVecs<T> &V, int R, double s2, double *out64, cudaStream_t s) {
     SolveWork *w = st->work;
+    const T *band, *wty, *wtz;
+    FK_TRY(stats_as<T>(st, &band, &wty, &wtz, s));
     const int64_t m = st->m;
     const unsigned gb = (unsigned)grid_blocks(m);
-    // W^T x = xd + cx W^T y
-    k_axpy_rhs<T><<<gb, CG_T, 0, s>>>(V.xd, V.g, a_out, m, 1, w->S, F_CX, 0.0);
+    const unsigned gv = (unsigned)std::min<int64_t>(cdiv((int64_t)R * m, 256), 152 * 8);
+    FK_TRY((launch_spmv<T, double>(band, st->grid, V.x, V.t64, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
+    if (GEN)
+        k_axpy64<T><<<gv, 256, 0, s>>>(V.t64, V.g, out64, m, R, w->S, F_CX, 0.0);
+    else
+        k_axpy64<T><<<gv, 256, 0, s>>>(V.t64, wty, out64, m, 1, nullptr, 0, 1.0 / s2);
     FK_LAUNCH();
-    KgOp *kg = w->kg[sizeof(T) == 4 ? 0 : 1];
-    FK_TRY(kgop_apply(kg, a_out, v_out, 1, nullptr, 0.0, s));
+    return FKSKI_OK;
+}
+
+template <typename T>
+static int solve_mean(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, bool gen, T *a_out, T *v_out,
+                      fkski_info *info, cudaStream_t s) {
+    CgVecs<T> V;
+    int it = 0, status = 0;
+    double res = 0.0;
+    if (gen) FK_TRY((fcg_solve<T, true>(st, kern, o, 1, V, &it, &res, &status, s)));
+    else FK_TRY((fcg_solve<T, false>(st, kern, o, 1, V, &it, &res, &status, s)));
+    SolveWork *w = st->work;
+    const int64_t m = st->m;
+    // a = W^T z (FP64) -> w64; v = K_G a (FP64) -> r0 slot
+    if (gen) FK_TRY((fcg_wtx64<T, true>(st, V, 1, kern->noise_var, V.w64, s)));
+    else FK_TRY((fcg_wtx64<T, false>(st, V, 1, kern->noise_var, V.w64, s)));
+    KgOp *kg64 = w->kg[1];
+    FK_TRY(kgop_apply(kg64, V.w64, V.r0, 1, nullptr, 0.0, s));
+    const unsigned gv = (unsigned)std::min<int64_t>(cdiv(m, 256), 152 * 8);
+    k_convert_t<double, T><<<gv, 256, 0, s>>>(V.w64, a_out, m, 1.0);
+    FK_LAUNCH();
+    k_convert_t<double, T><<<gv, 256, 0, s>>>(V.r0, v_out, m, 1.0);
+    FK_LAUNCH();
     FK_CUDA(cudaStreamSynchronize(s));
     if (info) {
         info->iters = it;
@@ -901,15 +860,12 @@ int solve_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts
     if (opts) o = *opts; else fkski_default_opts(&o);
     if (!(kern->noise_var > 0.0) || !std::isfinite(kern->noise_var)) return FKSKI_E_INVALID_ARG;
     if (o.maxiter < 1 || !(o.rtol >= 0.0)) return FKSKI_E_INVALID_ARG;
+    if (o.x0_mode != FKSKI_X0_ZERO && o.x0_mode != FKSKI_X0_Y_OVER_S2) return FKSKI_E_INVALID_ARG;
     if (info) memset(info, 0, sizeof(*info));
-    const bool dbl = o.precision == FKSKI_DOUBLE;
-    if (o.x0_mode == FKSKI_X0_Y_OVER_S2) {
-        return dbl ? solve_alg5<double>(st, kern, &o, (double *)a_out, (double *)v_out, info, s)
-                   : solve_alg5<float>(st, kern, &o, (float *)a_out, (float *)v_out, info, s);
-    }
-    if (o.x0_mode != FKSKI_X0_ZERO) return FKSKI_E_INVALID_ARG;
-    return dbl ? solve_alg3_mean<double>(st, kern, &o, (double *)a_out, (double *)v_out, info, s)
-               : solve_alg3_mean<float>(st, kern, &o, (float *)a_out, (float *)v_out, info, s);
+    const bool gen = o.x0_mode == FKSKI_X0_ZERO;
+    if (o.precision == FKSKI_DOUBLE)
+        return solve_mean<double>(st, kern, &o, gen, (double *)a_out, (double *)v_out, info, s);
+    return solve_mean<float>(st, kern, &o, gen, (float *)a_out, (float *)v_out, info, s);
 }
 
 int band_mvm_impl(const fkski_stats *stc, const void *x, void *u, int nrhs, int dtype, cudaStream_t s) {
@@ -919,24 +875,56 @@ int band_mvm_impl(const fkski_stats *stc, const void *x, void *u, int nrhs, int 
     if (dtype == FKSKI_F32) {
         const float *band, *wty, *wtz;
         FK_TRY(stats_as<float>(st, &band, &wty, &wtz, s));
-        return launch_spmv<float>(band, st->grid, (const float *)x, (float *)u, st->m, nrhs, nullptr, 1, nullptr,
-                                  nullptr, gb, s);
+        return launch_spmv<float, float>(band, st->grid, (const float *)x, (float *)u, st->m, nrhs, nullptr, 1, nullptr,
+                                         nullptr, gb, s);
     }
     if (dtype != FKSKI_F64) return FKSKI_E_INVALID_ARG;
-    const double *band, *wty, *wtz;
-    FK_TRY(stats_as<double>(st, &band, &wty, &wtz, s));
-    return launch_spmv<double>(band, st->grid, (const double *)x, (double *)u, st->m, nrhs, nullptr, 1, nullptr,
-                               nullptr, gb, s);
+    // FP64 vectors against the stored band (FP32 values promoted when the statistics are FP32)
+    if (st->dtype == FKSKI_F32)
+        return launch_spmv<float, double>((const float *)st->band, st->grid, (const double *)x, (double *)u, st->m, nrhs,
+                                          nullptr, 1, nullptr, nullptr, gb, s);
+    return launch_spmv<double, double>((const double *)st->band, st->grid, (const double *)x, (double *)u, st->m, nrhs,
+                                       nullptr, 1, nullptr, nullptr, gb, s);
 }
 
-// exported for grad.cu
-int alg3_for_grad_f32(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, Alg3Vecs<float> &V,
-                      int *iters, double *res, int *status, cudaStream_t s) {
-    return solve_alg3_batched<float>(st, kern, o, R, V, iters, res, status, s);
+// ------------------------------------------------------------------ log-likelihood solves
+// Batched Alg. 3 on [y, z_1..z_T]; outputs for the gradient:
+//   sol[r] = W^T x_r (solve precision, R x m), a64 = W^T x_0 (FP64, m),
+//   zx[r] = b_r^T x_r = g_r . x_hat_r + c^x_r rho0_r (FP64, device, R).
+template <typename T>
+__global__ void k_zx(const double *__restrict__ sums, const double *__restrict__ S, int R, double *__restrict__ zx) {
+    const int r = threadIdx.x;
+    if (r < R) zx[r] = sums[r * 4] + S[F_CX * R + r] * S[F_RHO0 * R + r];
 }
-int alg3_for_grad_f64(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, Alg3Vecs<double> &V,
-                      int *iters, double *res, int *status, cudaStream_t s) {
-    return solve_alg3_batched<double>(st, kern, o, R, V, iters, res, status, s);
+
+template <typename T>
+static int grad_solve_t(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, T *sol, double *a64, double *zx,
+                        int *iters, double *res, int *status, cudaStream_t s) {
+    const int R = 1 + st->nprobes;
+    CgVecs<T> V;
+    FK_TRY((fcg_solve<T, true>(st, kern, o, R, V, iters, res, status, s)));
+    SolveWork *w = st->work;
+    const int64_t m = st->m;
+    FK_TRY((fcg_wtx64<T, true>(st, V, R, kern->noise_var, V.w64, s)));
+    const unsigned gv = (unsigned)std::min<int64_t>(cdiv((int64_t)R * m, 256), 152 * 8);
+    k_convert_t<double, T><<<gv, 256, 0, s>>>(V.w64, sol, (int64_t)R * m, 1.0);
+    FK_LAUNCH();
+    FK_CUDA(cudaMemcpyAsync(a64, V.w64, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    const unsigned gb = (unsigned)grid_blocks(m);
+    k_dots4<T, double><<<gb, CG_T, 0, s>>>(V.g, V.x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R, w->part,
+                                           nullptr);
+    FK_LAUNCH();
+    k_fin_sums<<<(unsigned)cdiv(R * 4 * 32, 256), 256, 0, s>>>(w->part, gb, R, 4, V.t64);
+    FK_LAUNCH();
+    k_zx<T><<<1, 128, 0, s>>>(V.t64, w->S, R, zx);
+    FK_LAUNCH();
+    return FKSKI_OK;
+}
+
+int grad_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int dtype, void *sol, double *a64,
+               double *zx, int *iters, double *res, int *status, cudaStream_t s) {
+    if (dtype == FKSKI_F32) return grad_solve_t<float>(st, kern, o, (float *)sol, a64, zx, iters, res, status, s);
+    return grad_solve_t<double>(st, kern, o, (double *)sol, a64, zx, iters, res, status, s);
 }
 
 // ------------------------------------------------------------------ predict
