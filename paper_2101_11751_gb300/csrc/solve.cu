@@ -9,16 +9,18 @@
 // Each iteration applies B once (to r_hat) and carries A p through the recurrences of the
 // paper's EFCG (z_hat, s_hat).
 //
-// Precision.  The Krylov recurrences (r, p, u, v, s, z) run in the solve precision T (FP32 for
-// MIXED).  The solution x_hat is accumulated in FP64, and every `check_every` iterations the
-// residual is replaced by the true one, r_hat = r_hat_0 - (K W^T W + sigma^2 I) x_hat (Alg. 5) or
-// -(A' x_hat + c^x K W^T r0) (Alg. 3), computed with an FP64 SpMV and FP64 K_G; the search
-// direction's products (z_hat, s_hat) are recomputed from p_hat at the same time.  Convergence
-// is declared only on the true residual.  Without this, EFCG's recurrences for A p drift in
-// FP32 (GP systems have condition numbers ~1e6) and the recursive residual detaches from the
-// true one.  Inner products are FP32 within a warp (MIXED) and FP64 across warps and blocks, in
-// a fixed order (deterministic).  All scalars live in device memory; iterations run as a
-// captured CUDA graph of `check_every` steps plus one replacement, tested between launches.
+// Precision.  DOUBLE runs the paper's EFCG in FP64 exactly, testing the recursive residual.
+// MIXED keeps the Krylov recurrences (r, p, u, v, s, z) in FP32 and the solution x_hat in FP64,
+// with "reliable updates": at the end of a captured chunk of `check_every` iterations, every
+// right-hand side whose recursive residual fell below delta^2 = 0.01 times its value at the last
+// replacement (or below the tolerance) gets its residual replaced by the true one,
+//   r_hat = r_hat_0 - (K W^T W + sigma^2 I) x_hat              (Alg. 5)
+//   r_hat = -((K W^T W + sigma^2 I) x_hat + c^x K W^T r0)      (Alg. 3),
+// computed with an FP64 SpMV and an FP64 K_G; convergence is declared only on that true
+// residual.  Without this the FP32 recurrences for A p drift (GP systems have condition numbers
+// ~1e6) and the recursive residual detaches from the true one.  Inner products are FP32 within a
+// warp (MIXED) and FP64 across warps and blocks, in a fixed order (deterministic).  All scalars
+// live in device memory; iterations run as captured CUDA graphs with flags read between launches.
 #include "fkski_internal.cuh"
 
 #include <algorithm>
@@ -31,7 +33,7 @@ constexpr int CG_T = 256;
 
 // per-rhs scalar fields (double S[F * R + r])
 enum {
-    F_GAMMA = 0, F_GNEW, F_ALPHA, F_BETA, F_CR, F_CP, F_CX, F_RHO0, F_EPS, F_GKG, F_DELTA, F_RES, NF
+    F_GAMMA = 0, F_GNEW, F_ALPHA, F_BETA, F_CR, F_CP, F_CX, F_RHO0, F_EPS, F_GKG, F_DELTA, F_RES, F_GLAST, NF
 };
 
 // per-rhs state: 0 active, 1 converged on the recursive residual (to confirm), 2 finished
@@ -40,12 +42,14 @@ enum { RS_ACTIVE = 0, RS_TENTATIVE = 1, RS_FINAL = 2 };
 struct CgCtl {
     int iter;      // completed alpha steps
     int all_done;  // every rhs tentative or final: iteration kernels idle
-    int all_conf;  // every rhs final: replacement idle, host stops
+    int all_conf;  // every rhs final: the host stops
+    int any_rep;   // some rhs asks for a residual replacement (read by the host after a chunk)
     int status;    // ST_* bits
     int maxiter;
     int R;
-    int pad[2];
+    int replace;   // MIXED: reliable updates on; DOUBLE: off
     double sig2;
+    double delta2; // replacement trigger: gamma < delta2 * gamma at the last replacement
 };
 
 struct BandOffs {
@@ -308,14 +312,14 @@ __global__ void __launch_bounds__(CG_T) k_cg_psz(int64_t m, int R, const T *__re
     }
 }
 
-// gamma = <r, r> from u.r (q0) and r.g (q1) (Claim 4).  step: the x/r update of this iteration was
-// applied (GEN: update c^x, c^r first).  replace: r was just replaced by the true residual
-// (GEN: c^r = 1 - sigma^2 c^x); decide final / resume on it.  Otherwise: recursive test, beta.
+// gamma = <r, r> from u.r (q0) and r.g (q1) (Claim 4), after this iteration's x/r step
+// (GEN: c^x, c^r follow the step first).  mode 0: iterate; 1: init (no step taken).
+// Converged rhs become final (DOUBLE) or tentative, awaiting the true residual (MIXED).
 template <bool GEN>
 __global__ void k_cg_fin_gamma(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ state,
-                               int *__restrict__ iters, double *__restrict__ hist_beta, CgCtl *__restrict__ ctl,
-                               int mode /*0 iterate, 1 init, 2 replace*/) {
-    if (mode == 2 ? ctl->all_conf : ctl->all_done) return;
+                               int *__restrict__ want, int *__restrict__ iters, double *__restrict__ hist_beta,
+                               CgCtl *__restrict__ ctl, int mode) {
+    if (ctl->all_done) return;
     const int R = ctl->R;
     const double s2 = ctl->sig2;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -323,17 +327,13 @@ __global__ void k_cg_fin_gamma(const double *__restrict__ part, int nparts, doub
     for (int r = w; r < R; r += blockDim.x >> 5) {
         const double ur = warp_sum_partials(part, nparts, R, NQ, r, 0);
         const double rg = GEN ? warp_sum_partials(part, nparts, R, NQ, r, 1) : 0.0;
-        if (lane != 0) continue;
-        const int stt = state[r];
-        if (mode == 2 ? stt == RS_FINAL : stt != RS_ACTIVE) continue;
+        if (lane != 0 || state[r] != RS_ACTIVE) continue;
         double cr = 0.0;
         if (GEN) {
             if (mode == 0) {
                 const double a = S[F_ALPHA * R + r], cp0 = S[F_CP * R + r];
                 S[F_CX * R + r] += a * cp0;
                 cr = S[F_CR * R + r] - a * s2 * cp0;
-            } else if (mode == 2) {
-                cr = 1.0 - s2 * S[F_CX * R + r];
             } else {
                 cr = S[F_CR * R + r];
             }
@@ -341,30 +341,21 @@ __global__ void k_cg_fin_gamma(const double *__restrict__ part, int nparts, doub
         }
         const double g = ur + (GEN ? 2.0 * cr * rg + cr * cr * S[F_RHO0 * R + r] : 0.0);
         S[F_RES * R + r] = g;
+        S[F_GNEW * R + r] = g;
+        if (mode == 1) S[F_GLAST * R + r] = g;
         if (!isfinite(g)) {
             state[r] = RS_FINAL;
             iters[r] = ctl->iter;
             atomicOr(&ctl->status, ST_BREAKDOWN);
             continue;
         }
-        const bool conv = g <= S[F_EPS * R + r];
-        if (mode == 2) {
-            // true residual: finish, or resume the iteration from it
-            S[F_GAMMA * R + r] = g;
-            S[F_GNEW * R + r] = g;
-            if (conv) {
-                if (stt == RS_ACTIVE) iters[r] = ctl->iter;
-                state[r] = RS_FINAL;
-            } else {
-                state[r] = RS_ACTIVE;
-            }
+        if (g <= S[F_EPS * R + r]) {
+            state[r] = ctl->replace ? RS_TENTATIVE : RS_FINAL;
+            iters[r] = mode == 1 ? 0 : ctl->iter + 1;
             continue;
         }
-        S[F_GNEW * R + r] = g;
-        if (conv) {
-            state[r] = RS_TENTATIVE;
-            iters[r] = mode == 1 ? 0 : ctl->iter + 1;
-        } else if (mode == 1) {
+        if (ctl->replace && g < ctl->delta2 * S[F_GLAST * R + r]) want[r] = 1;
+        if (mode == 1) {
             S[F_BETA * R + r] = 0.0;
         } else {
             const double be = g / S[F_GAMMA * R + r];
@@ -374,18 +365,23 @@ __global__ void k_cg_fin_gamma(const double *__restrict__ part, int nparts, doub
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int all = 1;
-        for (int r = 0; r < R; ++r) all &= state[r] != RS_ACTIVE;
+        int all = 1, conf = 1;
+        for (int r = 0; r < R; ++r) {
+            all &= state[r] != RS_ACTIVE;
+            conf &= state[r] == RS_FINAL;
+        }
         ctl->all_done = all;
+        ctl->all_conf = conf;
     }
 }
 
-// alpha = gamma / <p, A p> (Claim 4 terms for GEN).  mode 0: after an iteration (records the
-// next alpha and advances the counter); 1: init; 2: after a replacement (same step index).
+// alpha = gamma / <p, A p> (Claim 4 terms for GEN) for the next step.  mode 0: after an
+// iteration (records the next alpha, advances the counter); 1: init.
 template <bool GEN>
 __global__ void k_cg_fin_delta(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ state,
-                               int *__restrict__ iters, double *__restrict__ hist_alpha, CgCtl *__restrict__ ctl, int mode) {
-    if (mode == 2 ? ctl->all_conf : ctl->all_done) return;
+                               const int *__restrict__ want, int *__restrict__ iters, double *__restrict__ hist_alpha,
+                               CgCtl *__restrict__ ctl, int mode) {
+    if (ctl->all_done) return;
     const int R = ctl->R;
     const double s2 = ctl->sig2;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -398,7 +394,7 @@ __global__ void k_cg_fin_delta(const double *__restrict__ part, int nparts, doub
         if (lane != 0 || state[r] != RS_ACTIVE) continue;
         double den = sz;
         if (GEN) {
-            const double cp = mode == 2 ? S[F_CP * R + r] : S[F_CR * R + r] + S[F_BETA * R + r] * S[F_CP * R + r];
+            const double cp = S[F_CR * R + r] + S[F_BETA * R + r] * S[F_CP * R + r];
             const double cq = s2 * cp;
             den += cp * skg + cq * pg + cp * zg + cp * cp * S[F_GKG * R + r] + cp * cq * S[F_RHO0 * R + r];
             S[F_CP * R + r] = cp;
@@ -419,28 +415,99 @@ __global__ void k_cg_fin_delta(const double *__restrict__ part, int nparts, doub
     __syncthreads();
     if (threadIdx.x == 0) {
         if (mode == 0) ctl->iter += 1;
-        int all = 1, conf = 1;
+        int all = 1, conf = 1, rep = 0;
         for (int r = 0; r < R; ++r) {
             all &= state[r] != RS_ACTIVE;
             conf &= state[r] == RS_FINAL;
+            rep |= want[r] || state[r] == RS_TENTATIVE;
         }
-        if (ctl->iter >= ctl->maxiter) all = 1;  // stop iterating; the replacement finalises
-        ctl->all_done = all;
-        if (mode == 2) {
-            if (ctl->iter >= ctl->maxiter) {
+        if (ctl->iter >= ctl->maxiter) {
+            all = 1;  // stop iterating
+            if (ctl->replace) {
+                rep = 1;  // the replacement pass confirms or finalises
+            } else {
                 for (int r = 0; r < R; ++r)
                     if (state[r] != RS_FINAL) { state[r] = RS_FINAL; iters[r] = ctl->maxiter; }
                 conf = 1;
             }
-            ctl->all_conf = conf;
         }
+        ctl->all_done = all;
+        ctl->all_conf = conf;
+        ctl->any_rep = rep;
+    }
+}
+
+// After a residual replacement (MIXED): gamma from the true residual for the flagged rhs;
+// finish those that meet the tolerance, resume the others with alpha = gamma / <p, A p>
+// (p, s, z unchanged).  Finalises everything at maxiter.
+template <bool GEN>
+__global__ void k_cg_fin_replace(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ state,
+                                 int *__restrict__ want, int *__restrict__ iters, double *__restrict__ hist_alpha,
+                                 CgCtl *__restrict__ ctl) {
+    if (ctl->all_conf) return;
+    const int R = ctl->R;
+    const double s2 = ctl->sig2;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NQ = GEN ? 2 : 1;
+    for (int r = w; r < R; r += blockDim.x >> 5) {
+        const double ur = warp_sum_partials(part, nparts, R, NQ, r, 0);
+        const double rg = GEN ? warp_sum_partials(part, nparts, R, NQ, r, 1) : 0.0;
+        if (lane != 0) continue;
+        const int stt = state[r];
+        if (stt == RS_FINAL || !(want[r] || stt == RS_TENTATIVE)) continue;
+        want[r] = 0;
+        double cr = 0.0;
+        if (GEN) {
+            cr = 1.0 - s2 * S[F_CX * R + r];
+            S[F_CR * R + r] = cr;
+        }
+        const double g = ur + (GEN ? 2.0 * cr * rg + cr * cr * S[F_RHO0 * R + r] : 0.0);
+        S[F_RES * R + r] = g;
+        S[F_GLAST * R + r] = g;
+        S[F_GAMMA * R + r] = g;
+        S[F_GNEW * R + r] = g;
+        if (!isfinite(g)) {
+            state[r] = RS_FINAL;
+            atomicOr(&ctl->status, ST_BREAKDOWN);
+            continue;
+        }
+        if (g <= S[F_EPS * R + r]) {
+            if (stt == RS_ACTIVE) iters[r] = ctl->iter;
+            state[r] = RS_FINAL;
+            continue;
+        }
+        state[r] = RS_ACTIVE;
+        const double den = S[F_DELTA * R + r];
+        if (!(den > 0.0)) {
+            state[r] = RS_FINAL;
+            atomicOr(&ctl->status, ST_BREAKDOWN);
+            continue;
+        }
+        const double a = g / den;
+        S[F_ALPHA * R + r] = a;
+        if (ctl->iter < ctl->maxiter) hist_alpha[(int64_t)ctl->iter * R + r] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int all = 1, conf = 1;
+        if (ctl->iter >= ctl->maxiter)
+            for (int r = 0; r < R; ++r)
+                if (state[r] != RS_FINAL) { state[r] = RS_FINAL; iters[r] = ctl->maxiter; }
+        for (int r = 0; r < R; ++r) {
+            all &= state[r] != RS_ACTIVE;
+            conf &= state[r] == RS_FINAL;
+        }
+        ctl->all_done = all;
+        ctl->all_conf = conf;
+        ctl->any_rep = 0;
     }
 }
 
 // Alg. 3 start (x0 = 0, r0 = b): c^r = c^p = 1, c^x = 0, gamma = rho0,
 // alpha_0 = rho0 / (g.K_G g + sigma^2 rho0).
 __global__ void k_cg3_init(double *__restrict__ S, const double *__restrict__ gkg, int *__restrict__ state,
-                           int *__restrict__ iters, double *__restrict__ hist_alpha, CgCtl *__restrict__ ctl) {
+                           int *__restrict__ want, int *__restrict__ iters, double *__restrict__ hist_alpha,
+                           CgCtl *__restrict__ ctl) {
     const int R = ctl->R;
     const double s2 = ctl->sig2;
     for (int r = threadIdx.x; r < R; r += blockDim.x) {
@@ -450,10 +517,12 @@ __global__ void k_cg3_init(double *__restrict__ S, const double *__restrict__ gk
         S[F_GAMMA * R + r] = rho0;
         S[F_GNEW * R + r] = rho0;
         S[F_RES * R + r] = rho0;
+        S[F_GLAST * R + r] = rho0;
         S[F_CP * R + r] = 1.0;
         S[F_CR * R + r] = 1.0;
         S[F_CX * R + r] = 0.0;
         state[r] = RS_ACTIVE;
+        want[r] = 0;
         iters[r] = 0;
         if (rho0 <= S[F_EPS * R + r]) {
             state[r] = RS_FINAL;
@@ -474,6 +543,7 @@ __global__ void k_cg3_init(double *__restrict__ S, const double *__restrict__ gk
         for (int r = 0; r < R; ++r) all &= state[r] == RS_FINAL;
         ctl->all_done = all;
         ctl->all_conf = all;
+        ctl->any_rep = 0;
     }
 }
 
@@ -482,11 +552,11 @@ __global__ void k_cg3_init(double *__restrict__ S, const double *__restrict__ gk
 template <typename T, bool GEN>
 __global__ void k_cg_resid(int64_t m, int R, const double *__restrict__ w64, const double *__restrict__ r0,
                            const T *__restrict__ kg, T *__restrict__ r, const double *__restrict__ S,
-                           const int *__restrict__ state, const CgCtl *__restrict__ ctl) {
+                           const int *__restrict__ state, const int *__restrict__ want, const CgCtl *__restrict__ ctl) {
     if (ctl->all_conf) return;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
         const int rr = (int)(e / m);
-        if (state[rr] == RS_FINAL) continue;
+        if (state[rr] == RS_FINAL || !(want[rr] || state[rr] == RS_TENTATIVE)) continue;
         double v;
         if (GEN) v = -fma(S[F_CX * R + rr], (double)kg[e], w64[e]);
         else v = r0[e] - w64[e];
@@ -502,6 +572,7 @@ struct SolveWork {
     double *S;
     double *part;
     int *state;
+    int *want;
     int *iters;
     CgCtl *ctl;
     double *hist;     // alpha then beta, (maxiter + 1) x R each
@@ -525,6 +596,7 @@ void free_solve_work(SolveWork *w) {
     if (w->S) cudaFree(w->S);
     if (w->part) cudaFree(w->part);
     if (w->state) cudaFree(w->state);
+    if (w->want) cudaFree(w->want);
     if (w->iters) cudaFree(w->iters);
     if (w->ctl) cudaFree(w->ctl);
     if (w->hist) cudaFree(w->hist);
@@ -555,6 +627,7 @@ static int work_get(fkski_stats *st, SolveWork **out) {
         FK_TRY(dev_alloc((void **)&w->S, sizeof(double) * (NF * MAX_R + MAX_R + 8)));
         FK_TRY(dev_alloc((void **)&w->part, sizeof(double) * NPART * 4 * MAX_R));
         FK_TRY(dev_alloc((void **)&w->state, sizeof(int) * MAX_R));
+        FK_TRY(dev_alloc((void **)&w->want, sizeof(int) * MAX_R));
         FK_TRY(dev_alloc((void **)&w->iters, sizeof(int) * MAX_R));
         FK_TRY(dev_alloc((void **)&w->ctl, sizeof(CgCtl)));
         if (cudaMallocHost((void **)&w->hflag, sizeof(int) * 4) != cudaSuccess) {
@@ -632,18 +705,26 @@ int stats_band_as(fkski_stats *st, int dtype, const void **band, const void **wt
     return stats_as<double>(st, (const double **)band, (const double **)wty, (const double **)wtz, s);
 }
 
-// Run the captured chunk (captured on w->ws) until every rhs is final; the internal stream first
-// waits for the caller's stream, and the caller's stream waits for it at the end.
-static int run_graph_loop(cudaGraphExec_t exec, SolveWork *w, int maxiter, int check, cudaStream_t s) {
+// Launch the captured iteration chunk (captured on w->ws) until every rhs is final, running the
+// captured residual-replacement pass whenever a chunk leaves a request for it.  The internal
+// stream first waits for the caller's stream, and the caller's stream waits for it at the end.
+static int run_graph_loop(cudaGraphExec_t body, cudaGraphExec_t rep, SolveWork *w, int maxiter, int check,
+                          cudaStream_t s) {
     FK_CUDA(cudaEventRecord(w->ev, s));
     FK_CUDA(cudaStreamWaitEvent(w->ws, w->ev, 0));
-    int done_iters = 0;
-    while (done_iters <= maxiter + check) {
-        FK_CUDA(cudaGraphLaunch(exec, w->ws));
-        done_iters += check;
-        FK_CUDA(cudaMemcpyAsync(w->hflag, &w->ctl->all_conf, sizeof(int), cudaMemcpyDeviceToHost, w->ws));
+    int launched = 0;
+    while (launched <= maxiter + check) {
+        FK_CUDA(cudaGraphLaunch(body, w->ws));
+        launched += check;
+        FK_CUDA(cudaMemcpyAsync(w->hflag, &w->ctl->all_conf, 2 * sizeof(int), cudaMemcpyDeviceToHost, w->ws));
         FK_CUDA(cudaStreamSynchronize(w->ws));
         if (w->hflag[0]) break;
+        if (rep && w->hflag[1]) {
+            FK_CUDA(cudaGraphLaunch(rep, w->ws));
+            FK_CUDA(cudaMemcpyAsync(w->hflag, &w->ctl->all_conf, 2 * sizeof(int), cudaMemcpyDeviceToHost, w->ws));
+            FK_CUDA(cudaStreamSynchronize(w->ws));
+            if (w->hflag[0]) break;
+        }
     }
     FK_CUDA(cudaEventRecord(w->ev, w->ws));
     FK_CUDA(cudaStreamWaitEvent(s, w->ev, 0));
@@ -688,6 +769,8 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     hc.maxiter = o->maxiter;
     hc.R = R;
     hc.sig2 = s2;
+    hc.replace = sizeof(T) == 4 ? 1 : 0;
+    hc.delta2 = 0.01;
     FK_CUDA(cudaMemcpyAsync(w->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, s));
     std::vector<double> hS((size_t)NF * R, 0.0);
     for (int r = 0; r < R; ++r) {
@@ -697,6 +780,7 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     }
     FK_CUDA(cudaMemcpyAsync(w->S, hS.data(), sizeof(double) * NF * R, cudaMemcpyHostToDevice, s));
     FK_CUDA(cudaMemsetAsync(w->state, 0, sizeof(int) * R, s));
+    FK_CUDA(cudaMemsetAsync(w->want, 0, sizeof(int) * R, s));
     FK_CUDA(cudaMemsetAsync(w->iters, 0, sizeof(int) * R, s));
     FK_CUDA(cudaMemsetAsync(b, 0, sizeof(T) * 6 * nT, s));
     FK_CUDA(cudaMemsetAsync(V.x, 0, sizeof(double) * nT, s));
@@ -717,7 +801,7 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
         FK_LAUNCH();
         k_pick<<<1, 128, 0, s>>>(V.t64, 4, R, gkg);
         FK_LAUNCH();
-        k_cg3_init<<<1, 128, 0, s>>>(w->S, gkg, w->state, w->iters, ha, w->ctl);
+        k_cg3_init<<<1, 128, 0, s>>>(w->S, gkg, w->state, w->want, w->iters, ha, w->ctl);
         FK_LAUNCH();
     } else {
         // r_hat_0 = -K_G W^T y / sigma^2 in FP64; r_hat = r_hat_0 in T
@@ -729,65 +813,59 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
         k_convert_t<double, T><<<gv, 256, 0, s>>>(V.r0, V.r, m, 1.0);
         FK_LAUNCH();
         FK_TRY((launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, 1, (const T *)nullptr, nullptr, gb, s)));
-        k_cg_fin_gamma<false><<<1, 256, 0, s>>>(w->part, gb, w->S, w->state, w->iters, hb, w->ctl, 1);
+        k_cg_fin_gamma<false><<<1, 256, 0, s>>>(w->part, gb, w->S, w->state, w->want, w->iters, hb, w->ctl, 1);
         FK_LAUNCH();
         FK_TRY(kgop_apply_dev(kg, V.u, V.v, R, V.r, sig2_dev, s));
         k_cg_psz<T, false><<<gb, CG_T, 0, s>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->S, w->state, w->part, w->ctl);
         FK_LAUNCH();
-        k_cg_fin_delta<false><<<1, 256, 0, s>>>(w->part, gb, w->S, w->state, w->iters, ha, w->ctl, 1);
+        k_cg_fin_delta<false><<<1, 256, 0, s>>>(w->part, gb, w->S, w->state, w->want, w->iters, ha, w->ctl, 1);
         FK_LAUNCH();
     }
     FK_TRY(kgop_reserve(kg, R));
     FK_TRY(kgop_reserve(kg64, R));
-    // capture: `check` iterations + one residual replacement
+    // capture the iteration chunk, and (MIXED) the residual-replacement pass
     const int check = std::max(1, o->check_every);
-    cudaGraph_t graph;
-    cudaGraphExec_t exec;
     const cudaStream_t cs = w->ws;
     const int NQ = GEN ? 2 : 1;
+    cudaGraph_t gbody = nullptr, grep = nullptr;
+    cudaGraphExec_t ebody = nullptr, erep = nullptr;
     FK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     int rc = FKSKI_OK;
     for (int it = 0; it < check && rc == FKSKI_OK; ++it) {
         k_cg_xr<T, GEN><<<gv, CG_T, 0, cs>>>(m, R, V.x, V.r, V.p, V.z, V.kg, w->S, w->state, w->ctl);
         rc = launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, gate_done, gb, cs);
         if (rc) break;
-        k_cg_fin_gamma<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->iters, hb, w->ctl, 0);
+        k_cg_fin_gamma<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->want, w->iters, hb, w->ctl, 0);
         rc = kgop_apply_dev(kg, V.u, V.v, R, V.r, sig2_dev, cs);
         if (rc) break;
         k_cg_psz<T, GEN><<<gb, CG_T, 0, cs>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->S, w->state, w->part, w->ctl);
-        k_cg_fin_delta<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->iters, ha, w->ctl, 0);
+        k_cg_fin_delta<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->want, w->iters, ha, w->ctl, 0);
     }
-    if (rc == FKSKI_OK) {
-        // true residual in FP64: w64 = K (W^T W x_hat) + sigma^2 x_hat
+    cudaError_t ce = cudaStreamEndCapture(cs, &gbody);
+    if (rc != FKSKI_OK) return rc;
+    FK_CUDA(ce);
+    if (sizeof(T) == 4) {
+        FK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+        // true residual in FP64: w64 = K (W^T W x_hat) + sigma^2 x_hat; gamma from it
         rc = launch_spmv<T, double>(band, st->grid, V.x, V.t64, m, R, nullptr, 1, nullptr, gate_conf, gb, cs);
         if (rc == FKSKI_OK) rc = kgop_apply_dev(kg64, V.t64, V.w64, R, V.x, sig2_dev, cs);
         if (rc == FKSKI_OK) {
-            k_cg_resid<T, GEN><<<gv, CG_T, 0, cs>>>(m, R, V.w64, V.r0, V.kg, V.r, w->S, w->state, w->ctl);
+            k_cg_resid<T, GEN><<<gv, CG_T, 0, cs>>>(m, R, V.w64, V.r0, V.kg, V.r, w->S, w->state, w->want, w->ctl);
             rc = launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, gate_conf, gb, cs);
         }
-        if (rc == FKSKI_OK) {
-            k_cg_fin_gamma<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->iters, hb, w->ctl, 2);
-            rc = kgop_apply_dev(kg, V.u, V.v, R, V.r, sig2_dev, cs);
-        }
-        // search direction products recomputed from p_hat: s = W^T W p, z = (K W^T W + sigma^2) p
-        if (rc == FKSKI_OK) rc = launch_spmv<T, T>(band, st->grid, V.p, V.s, m, R, nullptr, 1, nullptr, gate_conf, gb, cs);
-        if (rc == FKSKI_OK) rc = kgop_apply_dev(kg, V.s, V.z, R, V.p, sig2_dev, cs);
-        if (rc == FKSKI_OK) {
-            if (GEN)
-                k_dots4<T, T><<<gb, CG_T, 0, cs>>>(V.s, V.z, V.s, V.kg, V.p, V.g, V.z, V.g, m, R, w->part, gate_conf);
-            else
-                k_dots4<T, T><<<gb, CG_T, 0, cs>>>(V.s, V.z, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R,
-                                                   w->part, gate_conf);
-            k_cg_fin_delta<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->iters, ha, w->ctl, 2);
-        }
+        if (rc == FKSKI_OK)
+            k_cg_fin_replace<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->want, w->iters, ha, w->ctl);
+        ce = cudaStreamEndCapture(cs, &grep);
+        if (rc != FKSKI_OK) { cudaGraphDestroy(gbody); return rc; }
+        FK_CUDA(ce);
     }
-    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-    if (rc != FKSKI_OK) return rc;
-    FK_CUDA(ce);
-    FK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-    rc = run_graph_loop(exec, w, o->maxiter, check, s);
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
+    FK_CUDA(cudaGraphInstantiate(&ebody, gbody, 0));
+    if (grep) FK_CUDA(cudaGraphInstantiate(&erep, grep, 0));
+    rc = run_graph_loop(ebody, erep, w, o->maxiter, check, s);
+    cudaGraphExecDestroy(ebody);
+    cudaGraphDestroy(gbody);
+    if (erep) cudaGraphExecDestroy(erep);
+    if (grep) cudaGraphDestroy(grep);
     if (rc) return rc;
     CgCtl hc2;
     std::vector<double> hS2((size_t)NF * R);

@@ -33,7 +33,7 @@ def test_grad_matches_same_probe_oracle(fk, oracle_mod, d, M, n, kern, prec):
     T, seed = 8, 5
     st = fk.precompute(_tt(X), _tt(y), grid, n_probes=T, probe_seed=seed)
     rtol = 1e-8 if prec == 1 else 1e-5
-    L, g, info = fk.grad(st, kern, rtol=rtol, maxiter=2000, precision=prec)
+    L, g, info = fk.grad(st, kern, rtol=rtol, maxiter=4000, precision=prec)
     Z = np.stack([core.rademacher(seed, p, n) for p in range(T)])
     ref = core.loglik_grad_stochastic(grid, kern, X, y, Z, rtol=rtol)
     tol = 1e-4 if prec == 1 else 1e-3

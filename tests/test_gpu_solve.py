@@ -34,13 +34,17 @@ def test_mean_matches_nspace_cg(fk, oracle_mod, d, M, n, kern, rtol, prec, x0_mo
     dtype = np.float64 if prec == 1 else np.float32
     grid, X, y = problem(d, M, n, seed=11 + d, dtype=dtype)
     st = fk.precompute(_tt(X), _tt(y), grid)
-    a, v, info = fk.solve(st, kern, rtol=rtol, maxiter=3000, x0_mode=x0_mode, precision=prec)
+    a, v, info = fk.solve(st, kern, rtol=rtol, maxiter=6000, x0_mode=x0_mode, precision=prec)
     a_ref, v_ref, it_ref, _ = core.nspace_mean(grid, kern, X, y, rtol=rtol, x0_mode=x0_mode)
     assert rel_fro(v.double().cpu().numpy(), v_ref) <= 1e-4
     assert rel_fro(a.double().cpu().numpy(), a_ref) <= 1e-4
-    # iteration counts: FP64 runs track the n-space recurrence closely
+    # iteration counts: FP64 runs are the paper's EFCG and track the n-space recurrence (App. C.2,
+    # Fig. 5).  MIXED runs keep the Krylov vectors in FP32, which loses CG's superlinear
+    # convergence on these ill-conditioned systems (more iterations, same accuracy).
     if prec == 1:
         assert abs(info["iters"] - it_ref) <= max(3, 0.05 * it_ref), (info["iters"], it_ref)
+    else:
+        assert info["iters"] >= it_ref - max(3, 0.05 * it_ref)
     Xs = np.random.default_rng(3).uniform(0, 1, size=(d, 1000)).astype(dtype)
     mu = fk.predict(st, v, _tt(Xs)).double().cpu().numpy()
     mu_ref = core.predict(grid, v_ref, Xs)
@@ -53,7 +57,7 @@ def test_mean_against_tight_oracle(fk, oracle_mod):
     grid, X, y = problem(2, (32, 30), 20000, seed=3)
     kern = synth.Kernel(synth.RBF, (0.1, 0.12), 1.0, 0.02)
     st = fk.precompute(_tt(X), _tt(y), grid)
-    a, v, info = fk.solve(st, kern, rtol=1e-6)
+    a, v, info = fk.solve(st, kern, rtol=1e-6, maxiter=6000)
     _, v_tight, _, _ = core.nspace_mean(grid, kern, X, y, rtol=1e-12)
     assert rel_fro(v.double().cpu().numpy(), v_tight) <= 1e-4
 
@@ -89,6 +93,6 @@ def test_solve_deterministic(fk):
     grid, X, y = problem(3, (12, 12, 12), 20000, seed=5)
     kern = synth.Kernel(synth.RBF, (0.2, 0.2, 0.2), 1.0, 0.01)
     st = fk.precompute(_tt(X), _tt(y), grid)
-    a1, v1, _ = fk.solve(st, kern, rtol=1e-6)
-    a2, v2, _ = fk.solve(st, kern, rtol=1e-6)
+    a1, v1, _ = fk.solve(st, kern, rtol=1e-6, maxiter=6000)
+    a2, v2, _ = fk.solve(st, kern, rtol=1e-6, maxiter=6000)
     assert torch.equal(v1, v2) and torch.equal(a1, a2)
