@@ -33,7 +33,11 @@ constexpr int CG_T = 256;
 
 // per-rhs scalar fields (double S[F * R + r])
 enum {
-    F_GAMMA = 0, F_GNEW, F_ALPHA, F_BETA, F_CR, F_CP, F_CX, F_RHO0, F_EPS, F_GKG, F_DELTA, F_RES, F_GLAST, NF
+    F_GAMMA = 0, F_GNEW, F_ALPHA, F_BETA, F_CR, F_CP, F_CX, F_RHO0, F_EPS, F_GKG, F_DELTA, F_RES, F_GLAST,
+    F_RHOP,  // ||b'||^2 of the compressed base vector b' (GEN)
+    F_C0,    // x0 = c0 b (1/sigma^2 for the y / sigma^2 start, else 0)
+    F_BG,    // b_hat . W^T b' (GEN, for b^T x)
+    NF
 };
 
 // per-rhs state: 0 active, 1 converged on the recursive residual (to confirm), 2 finished
@@ -248,7 +252,13 @@ __global__ void k_fin_sums(const double *__restrict__ part, int nparts, int R, i
 }
 
 // ------------------------------------------------------------------ factorized CG kernels
-// GEN = true: Alg. 3 (compressed coefficients, g = W^T r0, kg = K_G g); false: Alg. 5.
+// GEN = false: Alg. 5 (r = W r_hat).  GEN = true: Alg. 3's compressed form r = W r_hat + c^r b'
+// with per-rhs base vector b', g = W^T b', kg = K_G g, rho' = ||b'||^2 (fields F_RHOP, F_GKG).
+// The paper's Alg. 3 takes b' = r0 = b, r_hat_0 = 0.  Here b is first split as b = W b_hat + b'
+// with b_hat a few CG steps on (W^T W) b_hat = W^T b, so b' is nearly orthogonal to range(W):
+// its part outside range(W) is an exact eigenvector of A (eigenvalue sigma^2) and no longer
+// cancels against in-span terms in the Claim 4 inner products (r_hat_0 = b_hat, c^r_0 = 1).
+// A rhs with b' = 0 (g = 0, rho' = 0) runs Alg. 5's recurrence inside the same kernels.
 
 // x_hat (FP64) += alpha p_hat;  r_hat -= alpha (z_hat + c^p kg)
 template <typename T, bool GEN>
@@ -339,7 +349,7 @@ __global__ void k_cg_fin_gamma(const double *__restrict__ part, int nparts, doub
             }
             S[F_CR * R + r] = cr;
         }
-        const double g = ur + (GEN ? 2.0 * cr * rg + cr * cr * S[F_RHO0 * R + r] : 0.0);
+        const double g = ur + (GEN ? 2.0 * cr * rg + cr * cr * S[F_RHOP * R + r] : 0.0);
         S[F_RES * R + r] = g;
         S[F_GNEW * R + r] = g;
         if (mode == 1) S[F_GLAST * R + r] = g;
@@ -396,7 +406,7 @@ __global__ void k_cg_fin_delta(const double *__restrict__ part, int nparts, doub
         if (GEN) {
             const double cp = S[F_CR * R + r] + S[F_BETA * R + r] * S[F_CP * R + r];
             const double cq = s2 * cp;
-            den += cp * skg + cq * pg + cp * zg + cp * cp * S[F_GKG * R + r] + cp * cq * S[F_RHO0 * R + r];
+            den += cp * skg + cq * pg + cp * zg + cp * cp * S[F_GKG * R + r] + cp * cq * S[F_RHOP * R + r];
             S[F_CP * R + r] = cp;
         }
         S[F_DELTA * R + r] = den;
@@ -461,7 +471,7 @@ __global__ void k_cg_fin_replace(const double *__restrict__ part, int nparts, do
             cr = 1.0 - s2 * S[F_CX * R + r];
             S[F_CR * R + r] = cr;
         }
-        const double g = ur + (GEN ? 2.0 * cr * rg + cr * cr * S[F_RHO0 * R + r] : 0.0);
+        const double g = ur + (GEN ? 2.0 * cr * rg + cr * cr * S[F_RHOP * R + r] : 0.0);
         S[F_RES * R + r] = g;
         S[F_GLAST * R + r] = g;
         S[F_GAMMA * R + r] = g;
@@ -503,52 +513,8 @@ __global__ void k_cg_fin_replace(const double *__restrict__ part, int nparts, do
     }
 }
 
-// Alg. 3 start (x0 = 0, r0 = b): c^r = c^p = 1, c^x = 0, gamma = rho0,
-// alpha_0 = rho0 / (g.K_G g + sigma^2 rho0).
-__global__ void k_cg3_init(double *__restrict__ S, const double *__restrict__ gkg, int *__restrict__ state,
-                           int *__restrict__ want, int *__restrict__ iters, double *__restrict__ hist_alpha,
-                           CgCtl *__restrict__ ctl) {
-    const int R = ctl->R;
-    const double s2 = ctl->sig2;
-    for (int r = threadIdx.x; r < R; r += blockDim.x) {
-        const double rho0 = S[F_RHO0 * R + r];
-        const double den = gkg[r] + s2 * rho0;
-        S[F_GKG * R + r] = gkg[r];
-        S[F_GAMMA * R + r] = rho0;
-        S[F_GNEW * R + r] = rho0;
-        S[F_RES * R + r] = rho0;
-        S[F_GLAST * R + r] = rho0;
-        S[F_CP * R + r] = 1.0;
-        S[F_CR * R + r] = 1.0;
-        S[F_CX * R + r] = 0.0;
-        state[r] = RS_ACTIVE;
-        want[r] = 0;
-        iters[r] = 0;
-        if (rho0 <= S[F_EPS * R + r]) {
-            state[r] = RS_FINAL;
-            continue;
-        }
-        if (!(den > 0.0) || !isfinite(den)) {
-            state[r] = RS_FINAL;
-            atomicOr(&ctl->status, ST_BREAKDOWN);
-            continue;
-        }
-        const double a = rho0 / den;
-        S[F_ALPHA * R + r] = a;
-        hist_alpha[r] = a;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int all = 1;
-        for (int r = 0; r < R; ++r) all &= state[r] == RS_FINAL;
-        ctl->all_done = all;
-        ctl->all_conf = all;
-        ctl->any_rep = 0;
-    }
-}
-
 // True residual from w64 = (K W^T W + sigma^2 I) x_hat (FP64):
-//   Alg. 5: r_hat = r_hat_0 - w64;   Alg. 3: r_hat = -(w64 + c^x kg)
+//   r_hat = r_hat_0 - w64 (- c^x kg for GEN), with c^r = 1 - sigma^2 c^x
 template <typename T, bool GEN>
 __global__ void k_cg_resid(int64_t m, int R, const double *__restrict__ w64, const double *__restrict__ r0,
                            const T *__restrict__ kg, T *__restrict__ r, const double *__restrict__ S,
@@ -557,9 +523,8 @@ __global__ void k_cg_resid(int64_t m, int R, const double *__restrict__ w64, con
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
         const int rr = (int)(e / m);
         if (state[rr] == RS_FINAL || !(want[rr] || state[rr] == RS_TENTATIVE)) continue;
-        double v;
-        if (GEN) v = -fma(S[F_CX * R + rr], (double)kg[e], w64[e]);
-        else v = r0[e] - w64[e];
+        double v = r0[e] - w64[e];
+        if (GEN) v -= S[F_CX * R + rr] * (double)kg[e];
         r[e] = (T)v;
     }
 }
@@ -733,16 +698,89 @@ static int run_graph_loop(cudaGraphExec_t body, cudaGraphExec_t rep, SolveWork *
 
 template <typename T>
 struct CgVecs {
-    T *r, *p, *u, *v, *s, *z, *g, *kg;     // solve precision
-    double *x, *r0, *t64, *w64;             // FP64: solution, Alg. 5 r_hat_0, temporaries
+    T *r, *p, *u, *v, *s, *z, *g, *kg, *g0;  // solve precision (g = W^T b', g0 = W^T b)
+    double *x, *r0, *t64, *w64;              // FP64: solution, r_hat_0, temporaries
 };
 
-// One factorized-CG solve (R right-hand sides).  GEN: Alg. 3 on b = [y, z_1..] with
-// g = [W^T y, W^T z_1..], rho0 = [y^T y, z_p^T z_p]; else Alg. 5 on y (R = 1).
-// On return V.x holds x_hat (FP64) and the scalars / histories stay in the workspace.
+// ---- setup kernels for the compressed base vectors (GEN)
+// few fixed CG steps on (W^T W) b_hat = W^T b (any b_hat gives an exact splitting b = W b_hat + b')
+template <typename T>
+__global__ void k_bcg_xr(int64_t m, int R, T *__restrict__ X, T *__restrict__ Rr, const T *__restrict__ P,
+                         const T *__restrict__ Q, const double *__restrict__ sums, const double *__restrict__ rr,
+                         const int *__restrict__ mask) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / m);
+        const double pq = sums[r * 4];
+        if (!mask[r] || !(pq > 0.0) || !(rr[r] > 0.0)) continue;
+        const T a = (T)(rr[r] / pq);
+        X[e] = fma(a, P[e], X[e]);
+        Rr[e] = fma(-a, Q[e], Rr[e]);
+    }
+}
+
+template <typename T>
+__global__ void k_bcg_p(int64_t m, int R, T *__restrict__ P, const T *__restrict__ Rr, const double *__restrict__ sums,
+                        const double *__restrict__ rr, const int *__restrict__ mask) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / m);
+        if (!mask[r] || !(rr[r] > 0.0)) continue;
+        const T be = (T)(sums[r * 4] / rr[r]);
+        P[e] = fma(be, P[e], Rr[e]);
+    }
+}
+
+// r0: rebased rows b_hat (from X), Alg. 5 rows -K_G W^T y / sigma^2 (from w64, already K applied)
+template <typename T>
+__global__ void k_r0_init(int64_t m, int R, const T *__restrict__ X, const double *__restrict__ kgy, double s2,
+                          double *__restrict__ r0, T *__restrict__ r, const int *__restrict__ mask) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int rr = (int)(e / m);
+        const double v = mask[rr] ? (double)X[e] : -kgy[e] / s2;
+        r0[e] = v;
+        r[e] = (T)v;
+    }
+}
+
+// g' = W^T b' = W^T b - W^T W b_hat (rebased rows), 0 for Alg. 5 rows
+template <typename T>
+__global__ void k_gprime(int64_t m, int R, const T *__restrict__ g0, const double *__restrict__ Bb, T *__restrict__ gp,
+                         const int *__restrict__ mask) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / m);
+        gp[e] = mask[r] ? (T)((double)g0[e] - Bb[e]) : T(0);
+    }
+}
+
+// sums[r*4+0] = b_hat . W^T b, sums[r*4+1] = b_hat . W^T W b_hat  (FP64)
+__global__ void k_rebase_scalars(const double *__restrict__ sums, double *__restrict__ S, int R, double s2,
+                                 const int *__restrict__ mask) {
+    const int r = threadIdx.x;
+    if (r >= R) return;
+    if (mask[r]) {
+        const double bg = sums[r * 4], bbb = sums[r * 4 + 1];
+        S[F_RHOP * R + r] = fmax(S[F_RHO0 * R + r] - 2.0 * bg + bbb, 0.0);
+        S[F_BG * R + r] = bg - bbb;
+        S[F_C0 * R + r] = 0.0;
+    } else {
+        S[F_RHOP * R + r] = 0.0;
+        S[F_BG * R + r] = 0.0;
+        S[F_C0 * R + r] = 1.0 / s2;
+    }
+    S[F_CR * R + r] = 1.0;
+    S[F_CP * R + r] = 1.0;
+    S[F_CX * R + r] = 0.0;
+}
+
+constexpr int BCG_STEPS = 8;
+
+// One factorized-CG solve of A x = b for R right-hand sides (b_0 = y, b_p = z_p).
+// GEN = false: Alg. 5 on y (R = 1).  GEN = true: compressed form with per-rhs base vectors;
+// rebase[r] = 1 splits b_r = W b_hat + b' (x0 = 0, the Lanczos start for SLQ), rebase[r] = 0 uses
+// Alg. 5's start x0 = b / sigma^2 for that rhs.  On return V.x holds x_hat (FP64); the scalars and
+// coefficient histories stay in the workspace.
 template <typename T, bool GEN>
-static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, CgVecs<T> &V,
-                     int *iters_host, double *res_host, int *status_out, cudaStream_t s) {
+static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, const int *rebase,
+                     CgVecs<T> &V, int *iters_host, double *res_host, int *status_out, cudaStream_t s) {
     SolveWork *w;
     FK_TRY(work_get(st, &w));
     const int dt = sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64;
@@ -755,11 +793,11 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     FK_TRY(stats_as<T>(st, &band, &wty, &wtz, s));
     const int64_t m = st->m;
     const size_t nT = (size_t)R * m;
-    FK_TRY(work_buf(w, sizeof(T) * 8 * nT + sizeof(double) * 4 * nT + 256));
+    FK_TRY(work_buf(w, sizeof(T) * 9 * nT + sizeof(double) * 4 * nT + 256));
     T *b = (T *)w->buf;
     V.r = b; V.p = b + nT; V.u = b + 2 * nT; V.v = b + 3 * nT; V.s = b + 4 * nT; V.z = b + 5 * nT;
-    V.g = b + 6 * nT; V.kg = b + 7 * nT;
-    double *d64 = (double *)((char *)w->buf + ((sizeof(T) * 8 * nT + 255) / 256) * 256);
+    V.g = b + 6 * nT; V.kg = b + 7 * nT; V.g0 = b + 8 * nT;
+    double *d64 = (double *)((char *)w->buf + ((sizeof(T) * 9 * nT + 255) / 256) * 256);
     V.x = d64; V.r0 = d64 + nT; V.t64 = d64 + 2 * nT; V.w64 = d64 + 3 * nT;
     FK_TRY(work_hist(w, R, o->maxiter));
     double *ha = w->hist, *hb = w->hist + w->hist_cap;
@@ -777,56 +815,92 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
         const double rho = r == 0 ? st->yty : st->ztz[r - 1];
         hS[F_RHO0 * R + r] = rho;
         hS[F_EPS * R + r] = o->rtol * o->rtol * rho;
+        hS[F_C0 * R + r] = 1.0 / s2;
     }
     FK_CUDA(cudaMemcpyAsync(w->S, hS.data(), sizeof(double) * NF * R, cudaMemcpyHostToDevice, s));
     FK_CUDA(cudaMemsetAsync(w->state, 0, sizeof(int) * R, s));
     FK_CUDA(cudaMemsetAsync(w->want, 0, sizeof(int) * R, s));
     FK_CUDA(cudaMemsetAsync(w->iters, 0, sizeof(int) * R, s));
-    FK_CUDA(cudaMemsetAsync(b, 0, sizeof(T) * 6 * nT, s));
+    FK_CUDA(cudaMemsetAsync(b, 0, sizeof(T) * 8 * nT, s));
     FK_CUDA(cudaMemsetAsync(V.x, 0, sizeof(double) * nT, s));
     const unsigned gb = (unsigned)grid_blocks(m);
     const unsigned gv = (unsigned)std::min<int64_t>(cdiv((int64_t)nT, 256), 152 * 8);
     const double *sig2_dev = &w->ctl->sig2;
     const int *gate_done = &w->ctl->all_done;
     const int *gate_conf = &w->ctl->all_conf;
+    const int NQ = GEN ? 2 : 1;
+    // W^T b for every rhs
+    FK_CUDA(cudaMemcpyAsync(V.g0, wty, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
+    if (R > 1) FK_CUDA(cudaMemcpyAsync(V.g0 + m, wtz, sizeof(T) * (R - 1) * m, cudaMemcpyDeviceToDevice, s));
+    // K_G W^T b in FP64 (for the Alg. 5 starts)
+    k_convert_t<T, double><<<gv, 256, 0, s>>>(V.g0, V.t64, (int64_t)nT, 1.0);
+    FK_LAUNCH();
+    FK_TRY(kgop_apply(kg64, V.t64, V.w64, R, nullptr, 0.0, s));
+    int *mask = w->want;  // reused below as the replacement flags (reset after setup)
     if (GEN) {
-        FK_CUDA(cudaMemcpyAsync(V.g, wty, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
-        if (R > 1) FK_CUDA(cudaMemcpyAsync(V.g + m, wtz, sizeof(T) * (R - 1) * m, cudaMemcpyDeviceToDevice, s));
+        std::vector<int> hm(R);
+        for (int r = 0; r < R; ++r) hm[r] = rebase ? rebase[r] : 1;
+        FK_CUDA(cudaMemcpyAsync(mask, hm.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
+        // b_hat: BCG_STEPS CG steps on (W^T W) b_hat = W^T b; X = V.u, Rr = V.v, P = V.p, Q = V.s
+        double *sums = V.r0;   // scratch (4 R doubles) until r0 is written
+        double *rr = V.r0 + 4 * R;
+        FK_CUDA(cudaMemcpyAsync(V.v, V.g0, sizeof(T) * nT, cudaMemcpyDeviceToDevice, s));
+        FK_CUDA(cudaMemcpyAsync(V.p, V.g0, sizeof(T) * nT, cudaMemcpyDeviceToDevice, s));
+        k_dots4<T, T><<<gb, CG_T, 0, s>>>(V.v, V.v, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R, w->part, nullptr);
+        k_fin_sums<<<(unsigned)cdiv(R * 4 * 32, 256), 256, 0, s>>>(w->part, gb, R, 4, sums);
+        k_pick<<<1, 128, 0, s>>>(sums, 4, R, rr);
+        FK_LAUNCH();
+        for (int it = 0; it < BCG_STEPS; ++it) {
+            FK_TRY((launch_spmv<T, T>(band, st->grid, V.p, V.s, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
+            k_dots4<T, T><<<gb, CG_T, 0, s>>>(V.p, V.s, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R, w->part, nullptr);
+            k_fin_sums<<<(unsigned)cdiv(R * 4 * 32, 256), 256, 0, s>>>(w->part, gb, R, 4, sums);
+            k_bcg_xr<T><<<gv, 256, 0, s>>>(m, R, V.u, V.v, V.p, V.s, sums, rr, mask);
+            k_dots4<T, T><<<gb, CG_T, 0, s>>>(V.v, V.v, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R, w->part, nullptr);
+            k_fin_sums<<<(unsigned)cdiv(R * 4 * 32, 256), 256, 0, s>>>(w->part, gb, R, 4, sums);
+            k_bcg_p<T><<<gv, 256, 0, s>>>(m, R, V.p, V.v, sums, rr, mask);
+            k_pick<<<1, 128, 0, s>>>(sums, 4, R, rr);
+            FK_LAUNCH();
+        }
+        // r_hat_0 (FP64 and T); W^T W b_hat in FP64; g' and the scalars of b'
+        k_r0_init<T><<<gv, 256, 0, s>>>(m, R, V.u, V.w64, s2, V.r0, V.r, mask);
+        FK_LAUNCH();
+        FK_TRY((launch_spmv<T, double>(band, st->grid, V.r0, V.t64, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
+        k_gprime<T><<<gv, 256, 0, s>>>(m, R, V.g0, V.t64, V.g, mask);
+        k_convert_t<T, double><<<gv, 256, 0, s>>>(V.g0, V.w64, (int64_t)nT, 1.0);
+        k_dots4<double, double><<<gb, CG_T, 0, s>>>(V.r0, V.w64, V.r0, V.t64, nullptr, nullptr, nullptr, nullptr, m, R,
+                                                    w->part, nullptr);
+        k_fin_sums<<<(unsigned)cdiv(R * 4 * 32, 256), 256, 0, s>>>(w->part, gb, R, 4, V.w64);
+        k_rebase_scalars<<<1, 128, 0, s>>>(V.w64, w->S, R, s2, mask);
+        FK_LAUNCH();
         FK_TRY(kgop_apply(kg, V.g, V.kg, R, nullptr, 0.0, s));
-        double *gkg = w->S + NF * MAX_R;
-        k_dots4<T, T><<<gb, CG_T, 0, s>>>(V.g, V.kg, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R, w->part,
-                                          nullptr);
+        k_dots4<T, T><<<gb, CG_T, 0, s>>>(V.g, V.kg, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R, w->part, nullptr);
+        k_fin_sums<<<(unsigned)cdiv(R * 4 * 32, 256), 256, 0, s>>>(w->part, gb, R, 4, V.w64);
+        k_pick<<<1, 128, 0, s>>>(V.w64, 4, R, w->S + F_GKG * R);
         FK_LAUNCH();
-        k_fin_sums<<<(unsigned)cdiv(R * 4 * 32, 256), 256, 0, s>>>(w->part, gb, R, 4, V.t64);
-        FK_LAUNCH();
-        k_pick<<<1, 128, 0, s>>>(V.t64, 4, R, gkg);
-        FK_LAUNCH();
-        k_cg3_init<<<1, 128, 0, s>>>(w->S, gkg, w->state, w->want, w->iters, ha, w->ctl);
-        FK_LAUNCH();
+        FK_CUDA(cudaMemsetAsync(mask, 0, sizeof(int) * R, s));
+        FK_CUDA(cudaMemsetAsync(V.u, 0, sizeof(T) * 3 * nT, s));  // u, v, p back to zero (s below)
+        FK_CUDA(cudaMemsetAsync(V.s, 0, sizeof(T) * nT, s));
     } else {
         // r_hat_0 = -K_G W^T y / sigma^2 in FP64; r_hat = r_hat_0 in T
-        k_convert_t<T, double><<<gv, 256, 0, s>>>(wty, V.t64, m, 1.0);
-        FK_LAUNCH();
-        FK_TRY(kgop_apply(kg64, V.t64, V.w64, 1, nullptr, 0.0, s));
         k_convert_t<double, double><<<gv, 256, 0, s>>>(V.w64, V.r0, m, -1.0 / s2);
         FK_LAUNCH();
         k_convert_t<double, T><<<gv, 256, 0, s>>>(V.r0, V.r, m, 1.0);
         FK_LAUNCH();
-        FK_TRY((launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, 1, (const T *)nullptr, nullptr, gb, s)));
-        k_cg_fin_gamma<false><<<1, 256, 0, s>>>(w->part, gb, w->S, w->state, w->want, w->iters, hb, w->ctl, 1);
-        FK_LAUNCH();
-        FK_TRY(kgop_apply_dev(kg, V.u, V.v, R, V.r, sig2_dev, s));
-        k_cg_psz<T, false><<<gb, CG_T, 0, s>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->S, w->state, w->part, w->ctl);
-        FK_LAUNCH();
-        k_cg_fin_delta<false><<<1, 256, 0, s>>>(w->part, gb, w->S, w->state, w->want, w->iters, ha, w->ctl, 1);
-        FK_LAUNCH();
     }
+    // init pass: gamma_0, s_0 = u_0, z_0 = v_0, p_0 = r_0, alpha_0
+    FK_TRY((launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, nullptr, gb, s)));
+    k_cg_fin_gamma<GEN><<<1, 256, 0, s>>>(w->part, gb, w->S, w->state, w->want, w->iters, hb, w->ctl, 1);
+    FK_LAUNCH();
+    FK_TRY(kgop_apply_dev(kg, V.u, V.v, R, V.r, sig2_dev, s));
+    k_cg_psz<T, GEN><<<gb, CG_T, 0, s>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->S, w->state, w->part, w->ctl);
+    FK_LAUNCH();
+    k_cg_fin_delta<GEN><<<1, 256, 0, s>>>(w->part, gb, w->S, w->state, w->want, w->iters, ha, w->ctl, 1);
+    FK_LAUNCH();
     FK_TRY(kgop_reserve(kg, R));
     FK_TRY(kgop_reserve(kg64, R));
     // capture the iteration chunk, and (MIXED) the residual-replacement pass
     const int check = std::max(1, o->check_every);
     const cudaStream_t cs = w->ws;
-    const int NQ = GEN ? 2 : 1;
     cudaGraph_t gbody = nullptr, grep = nullptr;
     cudaGraphExec_t ebody = nullptr, erep = nullptr;
     FK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
@@ -883,9 +957,18 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     return FKSKI_OK;
 }
 
-// W^T x for each rhs in FP64: W^T W x_hat (+ c^x g for Alg. 3, + W^T y / sigma^2 for Alg. 5)
-template <typename T, bool GEN>
-static int fcg_wtx64(fkski_stats *st, CgVecs<T> &V, int R, double s2, double *out64, cudaStream_t s) {
+// W^T x for each rhs in FP64: x = c0 b + W x_hat + c^x b'  ->  c0 W^T b + W^T W x_hat + c^x g
+template <typename T>
+__global__ void k_wtx64(const double *__restrict__ Bx, const T *__restrict__ g0, const T *__restrict__ gp,
+                        double *__restrict__ out, int64_t m, int R, const double *__restrict__ S) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / m);
+        out[e] = Bx[e] + S[F_C0 * R + r] * (double)g0[e] + S[F_CX * R + r] * (double)gp[e];
+    }
+}
+
+template <typename T>
+static int fcg_wtx64(fkski_stats *st, CgVecs<T> &V, int R, double *out64, cudaStream_t s) {
     SolveWork *w = st->work;
     const T *band, *wty, *wtz;
     FK_TRY(stats_as<T>(st, &band, &wty, &wtz, s));
@@ -893,10 +976,7 @@ static int fcg_wtx64(fkski_stats *st, CgVecs<T> &V, int R, double s2, double *ou
     const unsigned gb = (unsigned)grid_blocks(m);
     const unsigned gv = (unsigned)std::min<int64_t>(cdiv((int64_t)R * m, 256), 152 * 8);
     FK_TRY((launch_spmv<T, double>(band, st->grid, V.x, V.t64, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
-    if (GEN)
-        k_axpy64<T><<<gv, 256, 0, s>>>(V.t64, V.g, out64, m, R, w->S, F_CX, 0.0);
-    else
-        k_axpy64<T><<<gv, 256, 0, s>>>(V.t64, wty, out64, m, 1, nullptr, 0, 1.0 / s2);
+    k_wtx64<T><<<gv, 256, 0, s>>>(V.t64, V.g0, V.g, out64, m, R, w->S);
     FK_LAUNCH();
     return FKSKI_OK;
 }
@@ -907,13 +987,13 @@ static int solve_mean(fkski_stats *st, const fkski_kernel *kern, const fkski_opt
     CgVecs<T> V;
     int it = 0, status = 0;
     double res = 0.0;
-    if (gen) FK_TRY((fcg_solve<T, true>(st, kern, o, 1, V, &it, &res, &status, s)));
-    else FK_TRY((fcg_solve<T, false>(st, kern, o, 1, V, &it, &res, &status, s)));
+    const int rebase = 1;
+    if (gen) FK_TRY((fcg_solve<T, true>(st, kern, o, 1, &rebase, V, &it, &res, &status, s)));
+    else FK_TRY((fcg_solve<T, false>(st, kern, o, 1, nullptr, V, &it, &res, &status, s)));
     SolveWork *w = st->work;
     const int64_t m = st->m;
     // a = W^T z (FP64) -> w64; v = K_G a (FP64) -> r0 slot
-    if (gen) FK_TRY((fcg_wtx64<T, true>(st, V, 1, kern->noise_var, V.w64, s)));
-    else FK_TRY((fcg_wtx64<T, false>(st, V, 1, kern->noise_var, V.w64, s)));
+    FK_TRY(fcg_wtx64<T>(st, V, 1, V.w64, s));
     KgOp *kg64 = w->kg[1];
     FK_TRY(kgop_apply(kg64, V.w64, V.r0, 1, nullptr, 0.0, s));
     const unsigned gv = (unsigned)std::min<int64_t>(cdiv(m, 256), 152 * 8);
@@ -966,13 +1046,16 @@ int band_mvm_impl(const fkski_stats *stc, const void *x, void *u, int nrhs, int 
 }
 
 // ------------------------------------------------------------------ log-likelihood solves
-// Batched Alg. 3 on [y, z_1..z_T]; outputs for the gradient:
+// One batched solve of [y, z_1..z_T]: y starts from x0 = y / sigma^2 (Alg. 5's start, no
+// rebasing needed), each probe from x0 = 0 with the rebased compressed form (its CG coefficients
+// are those of the Krylov space of z_p, as SLQ needs).  Outputs for the gradient:
 //   sol[r] = W^T x_r (solve precision, R x m), a64 = W^T x_0 (FP64, m),
-//   zx[r] = b_r^T x_r = g_r . x_hat_r + c^x_r rho0_r (FP64, device, R).
-template <typename T>
+//   zx[r] = b_r^T x_r = c0 rho0 + (W^T b).x_hat + c^x (b_hat . W^T b' + ||b'||^2)  (FP64, device).
 __global__ void k_zx(const double *__restrict__ sums, const double *__restrict__ S, int R, double *__restrict__ zx) {
     const int r = threadIdx.x;
-    if (r < R) zx[r] = sums[r * 4] + S[F_CX * R + r] * S[F_RHO0 * R + r];
+    if (r < R)
+        zx[r] = S[F_C0 * R + r] * S[F_RHO0 * R + r] + sums[r * 4] +
+                S[F_CX * R + r] * (S[F_BG * R + r] + S[F_RHOP * R + r]);
 }
 
 template <typename T>
@@ -980,21 +1063,23 @@ static int grad_solve_t(fkski_stats *st, const fkski_kernel *kern, const fkski_o
                         int *iters, double *res, int *status, cudaStream_t s) {
     const int R = 1 + st->nprobes;
     CgVecs<T> V;
-    FK_TRY((fcg_solve<T, true>(st, kern, o, R, V, iters, res, status, s)));
+    std::vector<int> rebase(R, 1);
+    rebase[0] = 0;
+    FK_TRY((fcg_solve<T, true>(st, kern, o, R, rebase.data(), V, iters, res, status, s)));
     SolveWork *w = st->work;
     const int64_t m = st->m;
-    FK_TRY((fcg_wtx64<T, true>(st, V, R, kern->noise_var, V.w64, s)));
+    FK_TRY(fcg_wtx64<T>(st, V, R, V.w64, s));
     const unsigned gv = (unsigned)std::min<int64_t>(cdiv((int64_t)R * m, 256), 152 * 8);
     k_convert_t<double, T><<<gv, 256, 0, s>>>(V.w64, sol, (int64_t)R * m, 1.0);
     FK_LAUNCH();
     FK_CUDA(cudaMemcpyAsync(a64, V.w64, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
     const unsigned gb = (unsigned)grid_blocks(m);
-    k_dots4<T, double><<<gb, CG_T, 0, s>>>(V.g, V.x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R, w->part,
+    k_dots4<T, double><<<gb, CG_T, 0, s>>>(V.g0, V.x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R, w->part,
                                            nullptr);
     FK_LAUNCH();
     k_fin_sums<<<(unsigned)cdiv(R * 4 * 32, 256), 256, 0, s>>>(w->part, gb, R, 4, V.t64);
     FK_LAUNCH();
-    k_zx<T><<<1, 128, 0, s>>>(V.t64, w->S, R, zx);
+    k_zx<<<1, 128, 0, s>>>(V.t64, w->S, R, zx);
     FK_LAUNCH();
     return FKSKI_OK;
 }
