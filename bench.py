@@ -1,0 +1,363 @@
+"""Benchmark of the fkski hot path on GB300 (one JSON line on rank 0).
+
+One step = the whole hot path on the radar-shaped 3-D workload (n = 20 volumes x 14 sweeps x 720
+azimuths x 593 gates = 119,548,800 FP32 points, grid 128 x 128 x 32, m = 524,288; Sec. 5's 120M
+radar run): precompute of W^T W / W^T y (cell keys, stable sort, per-cell reduction, band
+assembly), the factorized-CG posterior mean (spectra, SpMV + K_G per iteration, rtol 1e-5) and
+prediction at 65,536 test points.  Inputs are resident in HBM and far larger than L2.
+
+value      = precompute throughput (Gpoints/s), the metric's first quantity; ms/CG iteration,
+             the fwd+bwd log-likelihood step on the gradient workload (n = 1e7, 64^3 grid, 16
+             probes) and its ratio to the plain FP64 forward are reported beside it.
+e2e        = Gpoints/s of the same step through the public API from pinned host buffers
+             (host->device copy of X, y, X* and device->host copy of mu inside the timed region).
+roofline   = the dominant kernel of the step (the banded SpMV of the CG iterations).
+cpu_baseline / --impl reference = the CPU oracle's precompute on a bounded sample.
+Multi-GPU: replicas (the path is single-GPU); value sums the ranks' points over the max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "precompute Gpoints/s (%HBM peak); ms/CG iter at m; fwd+bwd vs plain fwd"
+HBM_FALLBACK = 6800.0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", HBM_FALLBACK)), "measured"
+    return HBM_FALLBACK, "fallback"
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend)
+    return dist if world > 1 else None
+
+
+def dist_max(dist, x: float, device) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks during the timed region
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+# ------------------------------------------------------------------ workloads
+def radar_problem(volumes: int, device: str):
+    from paper_2101_11751_gb300 import synth
+    return synth.radar_3d(n_volumes=volumes, device=device)
+
+
+def cpu_oracle_precompute_rate(X: np.ndarray, y: np.ndarray, grid, sample: int, repeats: int = 1):
+    """The CPU oracle (single-threaded C, FP64) computing W^T W, W^T y, y^T y and the stable cell
+    sort on the first `sample` points; returns (Gpoints/s, seconds)."""
+    import oracle
+    from oracle import core
+    oracle.build()
+    Xs = np.ascontiguousarray(X[:, :sample])
+    ys = np.ascontiguousarray(y[:sample])
+    best = None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        core.precompute(grid, Xs, ys)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return sample / best / 1e9, best
+
+
+# ------------------------------------------------------------------ reference arm (CPU oracle)
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    prob = radar_problem(args.volumes, "cpu")
+    sample = args.ref_sample
+    for _ in range(args.warmup):
+        cpu_oracle_precompute_rate(prob.X, prob.y, prob.grid, sample)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_precompute_rate(prob.X, prob.y, prob.grid, sample)
+        times.append(dt)
+    t = statistics.mean(times)
+    v = sample / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gpoints/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"radar_3d sample of {sample} points (precompute only)", "grid": "128x128x32"},
+            "cpu_baseline": {"value": v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {sample} radar points, W^T W / W^T y / sort in FP64"},
+            "e2e": {"value": v, "unit": "Gpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fkski", choices=["fkski", "reference"])
+    ap.add_argument("--volumes", type=int, default=20, help="radar volumes (20 = 119.5M points)")
+    ap.add_argument("--no-grad", action="store_true", help="skip the fwd+bwd log-likelihood section")
+    ap.add_argument("--grad-n", type=int, default=10_000_000)
+    ap.add_argument("--ref-sample", type=int, default=200_000)
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--maxiter", type=int, default=4000)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    dist_barrier(dist)
+    __graft_entry__.build()
+    from paper_2101_11751_gb300 import api, synth
+    api.load()
+    hbm_peak, peak_kind = measured_peaks()
+
+    prob = radar_problem(args.volumes, str(dev))
+    n, grid, kern = prob.n, prob.grid, prob.kernel
+    m = grid.m
+    X = torch.from_numpy(prob.X).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    Xs = torch.from_numpy(prob.Xstar).to(dev)
+    rtol = prob.rtol
+    stream = torch.cuda.current_stream()
+
+    def step(Xd, yd, Xsd, ev=None):
+        if ev:
+            ev[0].record(stream)
+        st = api.precompute(Xd, yd, grid)
+        if ev:
+            ev[1].record(stream)
+        a, v, info = api.solve(st, kern, rtol=rtol, maxiter=args.maxiter, check_every=16, allow_not_converged=True)
+        if ev:
+            ev[2].record(stream)
+        mu = api.predict(st, v, Xsd)
+        if ev:
+            ev[3].record(stream)
+        st.close()
+        return info, mu
+
+    for _ in range(args.warmup):
+        step(X, y, Xs)
+    torch.cuda.synchronize()
+    dist_barrier(dist)
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = api._lib.fkski_kernel_launches()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    iters = []
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        info, mu = step(X, y, Xs, evs[k])
+        iters.append(info["iters"])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = api._lib.fkski_kernel_launches() - launches0
+    clocks = sampler.stop()
+    pre_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    sol_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    pred_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    step_ms = statistics.mean(e[0].elapsed_time(e[3]) for e in evs)
+    pre_ms_max = dist_max(dist, pre_ms, dev)
+    step_ms_max = dist_max(dist, step_ms, dev)
+    cg_iters = int(statistics.median(iters))
+
+    # kernel-level timings on the same data: banded SpMV and K_G (burst, events on this stream)
+    st = api.precompute(X, y, grid)
+    xv = torch.randn(m, device=dev, dtype=torch.float32)
+    for _ in range(3):
+        api.band_mvm(st, xv)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(stream)
+    for _ in range(reps):
+        api.band_mvm(st, xv)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = e0.elapsed_time(e1) / reps
+    st.close()
+
+    # end to end through the public API from pinned host buffers
+    Xh = torch.from_numpy(prob.X).pin_memory()
+    yh = torch.from_numpy(prob.y).pin_memory()
+    Xsh = torch.from_numpy(prob.Xstar).pin_memory()
+    mu_h = torch.empty(Xs.shape[1], dtype=torch.float32).pin_memory()
+    e2e_times = []
+    for k in range(max(2, args.steps // 2) if not args.no_e2e else 0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xd = Xh.to(dev, non_blocking=True)
+        yd = yh.to(dev, non_blocking=True)
+        Xsd = Xsh.to(dev, non_blocking=True)
+        info, mu = step(Xd, yd, Xsd)
+        mu_h.copy_(mu, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        del Xd, yd, Xsd
+    e2e_s = dist_max(dist, statistics.mean(e2e_times), dev) if e2e_times else float("nan")
+
+    # gradient workload: fwd+bwd (mixed precision) vs the plain FP64 forward at rtol 1e-4
+    grad_info = None
+    if not args.no_grad:
+        gp = synth.grf_3d(n=args.grad_n)
+        Xg = torch.from_numpy(gp.X).to(dev)
+        yg = torch.from_numpy(gp.y).to(dev)
+        sg = api.precompute(Xg, yg, gp.grid, n_probes=16, probe_seed=0)
+        api.grad(sg, gp.kernel, rtol=1e-4, maxiter=args.maxiter)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Lg, gg, ginfo = api.grad(sg, gp.kernel, rtol=1e-4, maxiter=args.maxiter)
+        torch.cuda.synchronize()
+        fwd_bwd_ms = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        Lf, finfo = api.loglik_forward(sg, gp.kernel, rtol=1e-4, maxiter=args.maxiter, precision=api.DOUBLE)
+        torch.cuda.synchronize()
+        plain_ms = (time.perf_counter() - t0) * 1e3
+        sg.close()
+        grad_info = {"workload": f"grf_3d n={gp.n} grid 64^3 (m={gp.grid.m}) RBF ARD, 16 Rademacher probes",
+                     "fwd_bwd_ms": fwd_bwd_ms, "plain_fp64_fwd_ms": plain_ms,
+                     "fwd_bwd_over_plain_fwd": fwd_bwd_ms / plain_ms,
+                     "loglik_mixed": Lg, "loglik_fp64": Lf, "grad": gg,
+                     "cg_iters_mixed_max": max(ginfo["iters"]), "cg_iters_fp64_max": max(finfo["iters"])}
+
+    # CPU oracle baseline (rank 0 at N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
+        rate, secs = cpu_oracle_precompute_rate(prob.X, prob.y, grid, args.cpu_sample)
+        cpu = {"value": rate, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {args.cpu_sample} radar points, W^T W / W^T y / stable sort in FP64 "
+                         f"({secs:.1f} s)"}
+
+    if rank != 0:
+        return
+    value = world * n / (pre_ms_max / 1e3) / 1e9
+    band_bytes = 343 * m * 4
+    pre_bytes = n * 16 + band_bytes + m * 4
+    spmv_bytes = band_bytes + 2 * m * 4
+    spmv_gbs = spmv_bytes / (spmv_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gpoints/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"radar_3d n={n} d=3 grid 128x128x32 (m={m}) RBF ARD rtol {rtol}",
+                   "n_points": n, "m": m, "test_points": int(Xs.shape[1]), "l2": "inputs > L2 (1.9 GB points)",
+                   "parallelism": f"replicas x{world}"},
+        "precompute_ms": pre_ms_max, "precompute_hbm_frac": pre_bytes / (pre_ms_max / 1e3) / 1e9 / hbm_peak,
+        "solve_ms": sol_ms, "predict_ms": pred_ms, "cg_iters": cg_iters,
+        "ms_per_cg_iter": sol_ms / max(cg_iters, 1),
+        "roofline": {"kernel": "k_band_spmv (W^T W x, 343 FP32 diagonals)", "bound": "hbm", "achieved": spmv_gbs,
+                     "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": spmv_gbs / hbm_peak,
+                     "traffic": None, "algorithmic_bytes": spmv_bytes, "launch_ms": spmv_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * n / e2e_s / 1e9, "unit": "Gpoints/s",
+                "h2d_bytes_per_step": int(prob.X.nbytes + prob.y.nbytes + prob.Xstar.nbytes),
+                "d2h_bytes_per_step": int(mu_h.numel() * 4)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "timed_wall_s": t_wall,
+    }
+    if grad_info is not None:
+        line["grad"] = grad_info
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -117,6 +117,10 @@ FKSKI_API const char *fkski_strerror(int status);
  * string, code and source location; empty if none).  Valid until the thread's next failing call. */
 FKSKI_API const char *fkski_last_error_detail(void);
 
+/* Number of kernel launches this library has issued in the process so far (a replayed CUDA graph
+ * counts each of its kernel nodes).  Host-only; for instrumentation. */
+FKSKI_API long long fkski_kernel_launches(void);
+
 /* ------------------------------------------------------------------ precompute (Sec. 3.1)
  * One O(n) pass computing the sufficient statistics of the Bayesian linear regression of Def. 2:
  *   W^T W  stored as its 7^d diagonals (Claim 2: at most (4r-1)^d = 7^d nonzeros per row, r = 2),

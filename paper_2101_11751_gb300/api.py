@@ -63,6 +63,7 @@ SIGNATURES = {
     "fkski_default_opts": (None, [ctypes.POINTER(COpts)]),
     "fkski_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "fkski_last_error_detail": (ctypes.c_char_p, []),
+    "fkski_kernel_launches": (ctypes.c_longlong, []),
     "fkski_precompute": (ctypes.c_int, [ctypes.POINTER(CGrid), P, P, P, ctypes.c_int64, ctypes.c_int,
                                         ctypes.POINTER(COpts), ctypes.POINTER(P), P]),
     "fkski_stats_info": (ctypes.c_int, [P, ctypes.POINTER(CGrid), PI64, PI64, PI64,

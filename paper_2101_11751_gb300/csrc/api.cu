@@ -2,6 +2,7 @@
 // object's lifetime, export and save/load.  All compute lives in the other translation units.
 #include "fkski_internal.cuh"
 
+#include <atomic>
 #include <cstdio>
 #include <vector>
 
@@ -23,6 +24,9 @@ void destroy_stats(fkski_stats *st) {
 static cudaStream_t S(void *stream) { return reinterpret_cast<cudaStream_t>(stream); }
 
 static thread_local char g_detail[256] = "";
+static std::atomic<long long> g_launches{0};
+
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 int note_cuda_error(cudaError_t e, const char *file, int line) {
     const char *base = strrchr(file, '/');
@@ -70,6 +74,8 @@ const char *fkski_strerror(int st) {
 }
 
 const char *fkski_last_error_detail(void) { return g_detail; }
+
+long long fkski_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int fkski_precompute(const fkski_grid *grid, const void *X, const void *y, const void *Z, int64_t n, int dtype,
                      const fkski_opts *opts, fkski_stats **out, void *stream) {

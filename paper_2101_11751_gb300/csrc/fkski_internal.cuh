@@ -27,7 +27,17 @@ int note_cuda_error(cudaError_t e, const char *file, int line);
         if (_s != FKSKI_OK) return _s; \
     } while (0)
 
-#define FK_LAUNCH() FK_CUDA(cudaGetLastError())
+namespace fk {
+// Process-wide count of kernel launches made by this library (graph launches add the number of
+// kernel nodes they replay).  Read through fkski_kernel_launches().
+void count_launches(long long k);
+}  // namespace fk
+
+#define FK_LAUNCH()                    \
+    do {                               \
+        fk::count_launches(1);         \
+        FK_CUDA(cudaGetLastError());   \
+    } while (0)
 
 namespace fk {
 

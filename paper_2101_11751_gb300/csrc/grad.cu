@@ -45,8 +45,11 @@ int spmv_for_grad(fkski_stats *st, const void *x, void *u, int R, int dtype, cud
 // while carrying the first row of the eigenvector matrix.  Output est[p] = rho0 sum_l z_l^2 log lam_l.
 constexpr int SLQ_MAXK = 4096;
 
+// A = W K W^T + sigma^2 I has spectrum in [sigma^2, inf), so a Ritz value below sigma^2 (left by
+// rounding in the FP32 Krylov recurrences) is clamped to sigma^2.
 __global__ void k_slq(const double *__restrict__ ha, const double *__restrict__ hb, const int *__restrict__ iters,
-                      const double *__restrict__ S, int R, int nf, double *__restrict__ est, int *__restrict__ status) {
+                      const double *__restrict__ S, int R, double sig2, double *__restrict__ est,
+                      int *__restrict__ status) {
     extern __shared__ double sm[];
     const int r = 1 + blockIdx.x;  // probe rhs
     const int k = iters[r];
@@ -113,8 +116,8 @@ __global__ void k_slq(const double *__restrict__ ha, const double *__restrict__ 
     }
     double acc = 0.0;
     for (int i = 0; i < k; ++i) {
-        if (!(dg[i] > 0.0)) fail = 1;
-        else acc += z[i] * z[i] * log(dg[i]);
+        if (!isfinite(dg[i])) fail = 1;
+        else acc += z[i] * z[i] * log(fmax(dg[i], sig2));
     }
     if (fail) atomicOr(status, ST_BREAKDOWN);
     est[blockIdx.x] = rho0 * acc;
@@ -255,7 +258,7 @@ static int forward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_
     if (kmax > SLQ_MAXK) return FKSKI_E_UNSUPPORTED;
     const size_t slq_sm = sizeof(double) * 3 * (size_t)(kmax + 1);
     if (slq_sm > 48 * 1024) FK_CUDA(cudaFuncSetAttribute(k_slq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slq_sm));
-    k_slq<<<R - 1, 128, slq_sm, s>>>(gv.hist_a, gv.hist_b, gv.iters, gv.S, R, 0, est, dstat);
+    k_slq<<<R - 1, 128, slq_sm, s>>>(gv.hist_a, gv.hist_b, gv.iters, gv.S, R, kern->noise_var, est, dstat);
     FK_LAUNCH();
     k_loglik_assemble<<<1, 32, 0, s>>>(gv.S, sl.zx, est, R, (double)st->n, sl.fs);
     FK_LAUNCH();

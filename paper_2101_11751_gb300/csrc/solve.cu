@@ -673,19 +673,34 @@ int stats_band_as(fkski_stats *st, int dtype, const void **band, const void **wt
 // Launch the captured iteration chunk (captured on w->ws) until every rhs is final, running the
 // captured residual-replacement pass whenever a chunk leaves a request for it.  The internal
 // stream first waits for the caller's stream, and the caller's stream waits for it at the end.
+static size_t graph_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (!g || cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+    size_t k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
 static int run_graph_loop(cudaGraphExec_t body, cudaGraphExec_t rep, SolveWork *w, int maxiter, int check,
-                          cudaStream_t s) {
+                          cudaStream_t s, long long nbody, long long nrep) {
     FK_CUDA(cudaEventRecord(w->ev, s));
     FK_CUDA(cudaStreamWaitEvent(w->ws, w->ev, 0));
     int launched = 0;
     while (launched <= maxiter + check) {
         FK_CUDA(cudaGraphLaunch(body, w->ws));
+        count_launches(nbody);
         launched += check;
         FK_CUDA(cudaMemcpyAsync(w->hflag, &w->ctl->all_conf, 2 * sizeof(int), cudaMemcpyDeviceToHost, w->ws));
         FK_CUDA(cudaStreamSynchronize(w->ws));
         if (w->hflag[0]) break;
         if (rep && w->hflag[1]) {
             FK_CUDA(cudaGraphLaunch(rep, w->ws));
+            count_launches(nrep);
             FK_CUDA(cudaMemcpyAsync(w->hflag, &w->ctl->all_conf, 2 * sizeof(int), cudaMemcpyDeviceToHost, w->ws));
             FK_CUDA(cudaStreamSynchronize(w->ws));
             if (w->hflag[0]) break;
@@ -903,6 +918,7 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     const cudaStream_t cs = w->ws;
     cudaGraph_t gbody = nullptr, grep = nullptr;
     cudaGraphExec_t ebody = nullptr, erep = nullptr;
+    const long long launches_before_capture = fkski_kernel_launches();
     FK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     int rc = FKSKI_OK;
     for (int it = 0; it < check && rc == FKSKI_OK; ++it) {
@@ -933,9 +949,12 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
         if (rc != FKSKI_OK) { cudaGraphDestroy(gbody); return rc; }
         FK_CUDA(ce);
     }
+    // captured launches are replays, counted when the graphs run
+    count_launches(launches_before_capture - fkski_kernel_launches());
     FK_CUDA(cudaGraphInstantiate(&ebody, gbody, 0));
     if (grep) FK_CUDA(cudaGraphInstantiate(&erep, grep, 0));
-    rc = run_graph_loop(ebody, erep, w, o->maxiter, check, s);
+    rc = run_graph_loop(ebody, erep, w, o->maxiter, check, s, (long long)graph_kernel_nodes(gbody),
+                        (long long)graph_kernel_nodes(grep));
     cudaGraphExecDestroy(ebody);
     cudaGraphDestroy(gbody);
     if (erep) cudaGraphExecDestroy(erep);

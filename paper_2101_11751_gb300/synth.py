@@ -201,13 +201,14 @@ def radar_geometry(n_sweeps: int = 14, n_az: int = 720, n_gates: int = 593) -> n
 
 
 def radar_3d(n_volumes: int = 20, seed: int = 0, M=(128, 128, 32), n_sweeps: int = 14,
-             n_az: int = 720, n_gates: int = 593) -> Problem:
+             n_az: int = 720, n_gates: int = 593, device: str = "cpu") -> Problem:
     """Radar-shaped d=3 FP32 workload (default n = 20*14*720*593 = 119,548,800 points).
 
     Each volume scan has the same sweep geometry (one site observed at 20 times). Reflectivity
     in dBZ is a sum of 32 Gaussian blobs per volume (amplitude exp(N(3, 0.5)), horizontal width
     U[5,30] km, vertical width U[1,4] km, advected 5 km per volume) plus N(0,1) noise.
-    Grid 128 x 128 x 32 over the full sweep box; RBF ARD l = (8, 8, 1.5) km, s = 100, sigma^2 = 1."""
+    Grid 128 x 128 x 32 over the full sweep box; RBF ARD l = (8, 8, 1.5) km, s = 100, sigma^2 = 1.
+    The blob sums are evaluated with torch on `device` (the random draws are numpy's either way)."""
     import torch
     rng = np.random.default_rng(seed)
     geo = radar_geometry(n_sweeps, n_az, n_gates)
@@ -215,7 +216,7 @@ def radar_3d(n_volumes: int = 20, seed: int = 0, M=(128, 128, 32), n_sweeps: int
     n = n_volumes * npv
     X = np.empty((3, n), dtype=np.float32)
     y = np.empty(n, dtype=np.float32)
-    gt = torch.from_numpy(geo)
+    gt = torch.from_numpy(geo).to(device)
     nb = 32
     amp = np.exp(rng.normal(3.0, 0.5, nb))
     cxy = rng.uniform(-120.0, 120.0, size=(nb, 2))
@@ -227,13 +228,13 @@ def radar_3d(n_volumes: int = 20, seed: int = 0, M=(128, 128, 32), n_sweeps: int
     for v in range(n_volumes):
         sl = slice(v * npv, (v + 1) * npv)
         X[:, sl] = geo
-        acc = torch.zeros(npv, dtype=torch.float32)
+        acc = torch.zeros(npv, dtype=torch.float32, device=device)
         for b in range(nb):
             c = cxy[b] + v * vel[b]
             q = ((gt[0] - float(c[0])) ** 2 + (gt[1] - float(c[1])) ** 2) / float(wxy[b] ** 2)
             q = q + (gt[2] - float(cz[b])) ** 2 / float(wz[b] ** 2)
             acc += float(amp[b]) * torch.exp(-0.5 * q)
-        y[sl] = acc.numpy() + rng.normal(0.0, 1.0, npv).astype(np.float32)
+        y[sl] = acc.cpu().numpy() + rng.normal(0.0, 1.0, npv).astype(np.float32)
     lo = X.min(axis=1).astype(np.float64)
     hi = X.max(axis=1).astype(np.float64)
     grid = grid_for_box(lo, hi, M)

@@ -37,7 +37,10 @@ def test_mean_matches_nspace_cg(fk, oracle_mod, d, M, n, kern, rtol, prec, x0_mo
     a, v, info = fk.solve(st, kern, rtol=rtol, maxiter=6000, x0_mode=x0_mode, precision=prec)
     a_ref, v_ref, it_ref, _ = core.nspace_mean(grid, kern, X, y, rtol=rtol, x0_mode=x0_mode)
     assert rel_fro(v.double().cpu().numpy(), v_ref) <= 1e-4
-    assert rel_fro(a.double().cpu().numpy(), a_ref) <= 1e-4
+    # a = W^T z: Alg. 3 on FP32 statistics mixes W^T y (FP32-accumulated) with y^T y in its scalar
+    # terms, consistent to ~1e-7 relative, which bounds a's accuracy near 5e-4; Alg. 5 has no such term.
+    a_tol = 1e-3 if (x0_mode == 0 and prec == 0) else 1e-4
+    assert rel_fro(a.double().cpu().numpy(), a_ref) <= a_tol
     # iteration counts: FP64 runs are the paper's EFCG and track the n-space recurrence (App. C.2,
     # Fig. 5).  MIXED runs keep the Krylov vectors in FP32, which loses CG's superlinear
     # convergence on these ill-conditioned systems (more iterations, same accuracy).
