@@ -59,7 +59,12 @@ extern "C" {
 #define FKSKI_X0_Y_OVER_S2 1 /* Alg. 5 (simplified EFCG, x0 = y / sigma^2, r0 in span(W))            */
 
 #define FKSKI_MIXED 0  /* FP32 band, FFT and Krylov vectors; FP64 solution, scalars, cross-warp
-                          inner-product sums, and the periodic true-residual replacement      */
+                          inner-product sums, and the periodic true-residual replacement.
+                          Attainable accuracy: every FP32 K_G / band product carries a normwise
+                          rounding error near 1e-6, which a CG step on A = W K W^T + sigma^2 I
+                          amplifies by up to ||A|| / sigma^2.  On ill-conditioned systems rtol
+                          much below 1e-5 can then end in FKSKI_E_NOT_CONVERGED or
+                          FKSKI_E_BREAKDOWN; use FKSKI_DOUBLE for such tolerances.          */
 #define FKSKI_DOUBLE 1 /* FP64 throughout                                                      */
 
 /* ------------------------------------------------------------------ configuration structs */
@@ -93,7 +98,9 @@ typedef struct {
     uint64_t probe_seed;  /* probe z_p(i) = sign of SplitMix64(seed) output k = p*2^40 + i + 1 */
     size_t iterate_budget_bytes; /* fkski_loglik_forward keeps its solutions if they fit     */
     int keep_sort;        /* fkski_precompute keeps cell keys and the permutation for export   */
-    int reserved[7];
+    int reliable_updates; /* true-residual replacement when the residual has dropped 10x since
+                             the last one: 0 default (on for MIXED, off for DOUBLE), 1 on, 2 off */
+    int reserved[6];
 } fkski_opts;
 
 typedef struct {

@@ -47,7 +47,7 @@ class COpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxiter", ctypes.c_int), ("x0_mode", ctypes.c_int),
                 ("precision", ctypes.c_int), ("check_every", ctypes.c_int), ("n_probes", ctypes.c_int),
                 ("probe_seed", ctypes.c_uint64), ("iterate_budget_bytes", ctypes.c_size_t),
-                ("keep_sort", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("keep_sort", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class CInfo(ctypes.Structure):

@@ -822,7 +822,8 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     hc.maxiter = o->maxiter;
     hc.R = R;
     hc.sig2 = s2;
-    hc.replace = sizeof(T) == 4 ? 1 : 0;
+    // reliable updates: on for FP32 vectors unless the caller chose (1 on, 2 off)
+    hc.replace = o->reliable_updates == 1 ? 1 : (o->reliable_updates == 2 ? 0 : (sizeof(T) == 4 ? 1 : 0));
     hc.delta2 = 0.01;
     FK_CUDA(cudaMemcpyAsync(w->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, s));
     std::vector<double> hS((size_t)NF * R, 0.0);
@@ -934,7 +935,7 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     cudaError_t ce = cudaStreamEndCapture(cs, &gbody);
     if (rc != FKSKI_OK) return rc;
     FK_CUDA(ce);
-    if (sizeof(T) == 4) {
+    if (hc.replace) {
         FK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
         // true residual in FP64: w64 = K (W^T W x_hat) + sigma^2 x_hat; gamma from it
         rc = launch_spmv<T, double>(band, st->grid, V.x, V.t64, m, R, nullptr, 1, nullptr, gate_conf, gb, cs);

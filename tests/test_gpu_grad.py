@@ -56,18 +56,19 @@ def test_grad_exact_traces_vs_fd(fk, oracle_mod):
 
 
 def test_autograd_function_and_budget_recompute(fk, oracle_mod):
+    # MIXED precision at the paper's accuracy regime; tighter tolerances need FKSKI_DOUBLE
     grid, X, y = problem(2, (16, 15), 3000, seed=4)
     st = fk.precompute(_tt(X), _tt(y), grid, n_probes=4, probe_seed=1)
     theta = torch.tensor([0.2, 0.25, 1.0, 0.02], dtype=torch.float64, requires_grad=True)
-    L1 = fk.log_marginal_likelihood(theta, st, rtol=1e-6)
+    L1 = fk.log_marginal_likelihood(theta, st, rtol=1e-4)
     L1.backward()
     g1 = theta.grad.clone()
     theta.grad = None
-    L2 = fk.log_marginal_likelihood(theta, st, rtol=1e-6, budget=0)  # solutions not kept
+    L2 = fk.log_marginal_likelihood(theta, st, rtol=1e-4, budget=0)  # solutions not kept
     L2.backward()
     assert L1.item() == L2.item()
     torch.testing.assert_close(theta.grad, g1, rtol=0, atol=0)
     kern = synth.Kernel(synth.RBF, (0.2, 0.25), 1.0, 0.02)
-    Lg, gg, _ = fk.grad(st, kern, rtol=1e-6)
+    Lg, gg, _ = fk.grad(st, kern, rtol=1e-4)
     assert Lg == L1.item()
     np.testing.assert_array_equal(np.array(gg), g1.numpy())
