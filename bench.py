@@ -69,6 +69,11 @@ def dist_max(dist, x: float, device) -> float:
     return float(t.item())
 
 
+def replica_value(world: int, n_per_rank: int, max_ms: float) -> float:
+    """Whole-job Gpoints/s of N independent replicas: all ranks' points over the slowest rank."""
+    return world * n_per_rank / (max_ms / 1e3) / 1e9
+
+
 def dist_barrier(dist):
     if dist is not None:
         dist.barrier()
@@ -328,7 +333,7 @@ def main():
 
     if rank != 0:
         return
-    value = world * n / (pre_ms_max / 1e3) / 1e9
+    value = replica_value(world, n, pre_ms_max)
     band_bytes = 343 * m * 4
     pre_bytes = n * 16 + band_bytes + m * 4
     spmv_bytes = band_bytes + 2 * m * 4
