@@ -178,6 +178,22 @@ FKSKI_API void fkski_destroy(fkski_stats *st);
 FKSKI_API int fkski_kg_mvm(const fkski_grid *grid, const fkski_kernel *kern, int param, const void *v,
                  void *out, int nrhs, int dtype, void *stream);
 
+/* Allocation-free variant of fkski_kg_mvm (the paper has no counterpart: this serves callers that
+ * may not allocate device memory during the call, e.g. under an allocator or memory budget owned
+ * by someone else).  Same arguments, result and dtype rules as fkski_kg_mvm, RBF kernel only
+ * (value or derivative, param as there).  All working memory -- the d axis spectra and one
+ * intermediate of nrhs*m values -- is one fixed device array of FKSKI_NOALLOC_SCRATCH_BYTES per
+ * device inside this library; nothing is allocated or freed and the stream is not synchronized.
+ * Limits: every M_k <= 2048; for d > 1, nrhs * m * (4 or 8 bytes) <= FKSKI_NOALLOC_SCRATCH_BYTES
+ * - 96 KiB (about 4.17 million FP32 values).  Beyond them, or for a Matern kernel, it returns
+ * FKSKI_E_UNSUPPORTED.  The first call on a device looks the array up and may load this
+ * library's device code, so make it before capturing a stream into a CUDA graph.  The array is
+ * shared: calls that overlap on one device (other streams, other threads) corrupt each other's
+ * results; order them.  Returns OK, INVALID_ARG, UNSUPPORTED, CUDA. */
+#define FKSKI_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+FKSKI_API int fkski_kg_mvm_noalloc(const fkski_grid *grid, const fkski_kernel *kern, int param, const void *v,
+                                   void *out, int nrhs, int dtype, void *stream);
+
 /* u = (W^T W) x for nrhs grid vectors (device, rhs-major, dtype) from the stored band
  * (Claim 2: O(m 7^d)). */
 FKSKI_API int fkski_band_mvm(const fkski_stats *st, const void *x, void *u, int nrhs, int dtype, void *stream);

@@ -75,6 +75,8 @@ SIGNATURES = {
     "fkski_destroy": (None, [P]),
     "fkski_kg_mvm": (ctypes.c_int, [ctypes.POINTER(CGrid), ctypes.POINTER(CKernel), ctypes.c_int, P, P,
                                     ctypes.c_int, ctypes.c_int, P]),
+    "fkski_kg_mvm_noalloc": (ctypes.c_int, [ctypes.POINTER(CGrid), ctypes.POINTER(CKernel), ctypes.c_int, P, P,
+                                            ctypes.c_int, ctypes.c_int, P]),
     "fkski_band_mvm": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P]),
     "fkski_solve": (ctypes.c_int, [P, ctypes.POINTER(CKernel), ctypes.POINTER(COpts), P, P,
                                    ctypes.POINTER(CInfo), P]),
@@ -253,6 +255,28 @@ def kg_mvm(grid, kernel, V: torch.Tensor, param: int = -1, stream=None) -> torch
     g, k = c_grid(grid), c_kernel(kernel)
     _check(_lib.fkski_kg_mvm(ctypes.byref(g), ctypes.byref(k), param, _ptr(V), _ptr(out), R, _dtype_code(V),
                              _stream(stream)), "fkski_kg_mvm")
+    return out
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def kg_mvm_noalloc(grid, kernel, V: torch.Tensor, out: torch.Tensor, param: int = -1, stream=None) -> torch.Tensor:
+    """fkski_kg_mvm_noalloc: out = K_G V without any device allocation inside the call (RBF only).
+
+    The caller provides `out` (same shape and dtype as V); the library works in one fixed
+    per-device scratch array, so calls on one device must not overlap."""
+    load()
+    if out.shape != V.shape or out.dtype != V.dtype or not out.is_contiguous():
+        raise ValueError("out must be a contiguous tensor of V's shape and dtype")
+    R = 1 if V.dim() == 1 else V.shape[0]
+    g, k = c_grid(grid), c_kernel(kernel)
+    rc = _lib.fkski_kg_mvm_noalloc(ctypes.byref(g), ctypes.byref(k), param, _ptr(V), _ptr(out), R,
+                                   _dtype_code(V), _stream(stream))
+    if rc == E_UNSUPPORTED:
+        raise FkskiError(rc, "fkski_kg_mvm_noalloc: needs an RBF kernel, M_k <= 2048 and, for d > 1, "
+                             f"nrhs*m*{V.element_size()} bytes within {NOALLOC_SCRATCH_BYTES} - 96 KiB")
+    _check(rc, "fkski_kg_mvm_noalloc")
     return out
 
 

@@ -244,6 +244,11 @@ int fkski_kg_mvm(const fkski_grid *grid, const fkski_kernel *kern, int param, co
     return kg_mvm_impl(grid, kern, param, v, out, nrhs, dtype, S(stream));
 }
 
+int fkski_kg_mvm_noalloc(const fkski_grid *grid, const fkski_kernel *kern, int param, const void *v, void *out,
+                         int nrhs, int dtype, void *stream) {
+    return kg_mvm_noalloc_impl(grid, kern, param, v, out, nrhs, dtype, S(stream));
+}
+
 int fkski_band_mvm(const fkski_stats *st, const void *x, void *u, int nrhs, int dtype, void *stream) {
     return band_mvm_impl(st, x, u, nrhs, dtype, S(stream));
 }

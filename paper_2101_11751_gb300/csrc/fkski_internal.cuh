@@ -126,6 +126,8 @@ int precompute_impl(const fkski_grid *grid, const void *X, const void *y, const 
                     int dtype, const fkski_opts *opts, fkski_stats **out, cudaStream_t s);
 int kg_mvm_impl(const fkski_grid *grid, const fkski_kernel *kern, int param, const void *v, void *out,
                 int nrhs, int dtype, cudaStream_t s);
+int kg_mvm_noalloc_impl(const fkski_grid *grid, const fkski_kernel *kern, int param, const void *v, void *out,
+                        int nrhs, int dtype, cudaStream_t s);
 int band_mvm_impl(const fkski_stats *st, const void *x, void *u, int nrhs, int dtype, cudaStream_t s);
 int stats_band_as(fkski_stats *st, int dtype, const void **band, const void **wty, const void **wtz,
                   cudaStream_t s);

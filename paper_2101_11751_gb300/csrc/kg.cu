@@ -17,6 +17,7 @@
 #include "fkski_internal.cuh"
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 namespace fk {
@@ -648,6 +649,82 @@ int kg_mvm_impl(const fkski_grid *grid, const fkski_kernel *kern, int param, con
     cudaStreamSynchronize(s);  // op buffers are freed below
     kgop_destroy(op);
     return rc;
+}
+
+// ------------------------------------------------------------------ allocation-free K_G product
+// For callers that may not allocate device memory at call time: code running while a
+// cudaMalloc-free region is required (an allocator owned by someone else, a fixed memory
+// budget checked up front, a host thread that must not take the allocator's locks).  The RBF
+// Kronecker product needs only the d axis spectra and one intermediate of nrhs * m values, so
+// both live in one fixed device array instead of buffers obtained per call.  That array is
+// shared by every call on a device and keeps whatever the last call wrote: each call rewrites
+// the spectra and the intermediate before reading them, so nothing in it has to start at zero,
+// but two calls in flight at once on the same device (two streams, two host threads) overwrite
+// each other's data and give wrong results.
+static __device__ __align__(256) unsigned char g_kg_noalloc_scratch[FKSKI_NOALLOC_SCRATCH_BYTES];
+
+constexpr size_t NOALLOC_LAM_BYTES = sizeof(double) * FFT_SMEM_CPLX;  // one axis spectrum, FP32 or FP64
+constexpr size_t NOALLOC_BUF_OFFSET = 3 * NOALLOC_LAM_BYTES;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static_assert(NOALLOC_BUF_OFFSET % 256 == 0, "intermediate must stay 256-byte aligned");
+static_assert(FKSKI_NOALLOC_SCRATCH_BYTES > NOALLOC_BUF_OFFSET, "scratch smaller than its spectra");
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_base[NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array for the current device, looked up once per device.
+static int noalloc_scratch(void **base) {
+    int dev = -1;
+    FK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return FKSKI_E_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        FK_CUDA(cudaGetSymbolAddress(&p, g_kg_noalloc_scratch));
+        g_noalloc_base[dev] = p;
+    }
+    *base = g_noalloc_base[dev];
+    return FKSKI_OK;
+}
+
+static size_t kg_noalloc_max_values(int dtype) {
+    return (FKSKI_NOALLOC_SCRATCH_BYTES - NOALLOC_BUF_OFFSET) / esz(dtype);
+}
+
+int kg_mvm_noalloc_impl(const fkski_grid *grid, const fkski_kernel *kern, int param, const void *v, void *out,
+                        int nrhs, int dtype, cudaStream_t s) {
+    if (!grid || !kern || !v || !out || nrhs < 1) return FKSKI_E_INVALID_ARG;
+    if (grid->d < 1 || grid->d > 3) return FKSKI_E_INVALID_ARG;
+    if (dtype != FKSKI_F32 && dtype != FKSKI_F64) return FKSKI_E_INVALID_ARG;
+    for (int k = 0; k < grid->d; ++k)
+        if (grid->M[k] < 4 || !(grid->h[k] > 0.0)) return FKSKI_E_INVALID_ARG;
+    if (v == out) return FKSKI_E_INVALID_ARG;
+    if (kern->type != FKSKI_RBF) return FKSKI_E_UNSUPPORTED;
+    KgOp op;
+    memset(&op, 0, sizeof(op));
+    op.g = *grid;
+    op.d = grid->d;
+    op.dtype = dtype;
+    op.m = 1;
+    op.N = 1;
+    op.kind = -1;
+    for (int a = 0; a < op.d; ++a) {
+        op.m *= grid->M[a];
+        op.L[a] = next_pow2(2 * grid->M[a] - 1);
+        if (op.L[a] > FFT_SMEM_CPLX) return FKSKI_E_UNSUPPORTED;
+        op.N *= op.L[a];
+    }
+    // the intermediate holds nrhs * m values (none for d = 1)
+    if (op.d > 1 && (uint64_t)nrhs * (uint64_t)op.m > kg_noalloc_max_values(dtype)) return FKSKI_E_UNSUPPORTED;
+    void *base = nullptr;
+    FK_TRY(noalloc_scratch(&base));
+    unsigned char *b = static_cast<unsigned char *>(base);
+    for (int a = 0; a < op.d; ++a) op.lam[a] = b + (size_t)a * NOALLOC_LAM_BYTES;
+    op.scratch = b + NOALLOC_BUF_OFFSET;
+    op.scratch_bytes = FKSKI_NOALLOC_SCRATCH_BYTES - NOALLOC_BUF_OFFSET;
+    // with the spectra and the intermediate already in place, neither step below allocates
+    FK_TRY(kgop_set(&op, kern, param, s));
+    return kgop_apply(&op, v, out, nrhs, nullptr, 0.0, s);
 }
 
 }  // namespace fk
