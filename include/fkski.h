@@ -124,6 +124,14 @@ FKSKI_API const char *fkski_strerror(int status);
  * string, code and source location; empty if none).  Valid until the thread's next failing call. */
 FKSKI_API const char *fkski_last_error_detail(void);
 
+/* The launch configurations the K_G autotuner has chosen so far in this process, one line per
+ * pass shape ("f32 L=256 M=128 S=32 lines=4096 -> radix 4, 4 lines/CTA, 256 threads, 0.0123 ms").
+ * The paper has no counterpart: the tuner picks, per Kronecker pass shape, the FFT stage radix
+ * (2 or 4), the lines per CTA and the threads per CTA by timing each candidate once (before the
+ * solver captures its graphs); the choices give bit-identical results.  Writes at most len bytes
+ * (NUL-terminated) to buf (may be NULL) and returns the size needed. */
+FKSKI_API size_t fkski_tuning_table(char *buf, size_t len);
+
 /* Number of kernel launches this library has issued in the process so far (a replayed CUDA graph
  * counts each of its kernel nodes).  Host-only; for instrumentation. */
 FKSKI_API long long fkski_kernel_launches(void);
@@ -208,8 +216,10 @@ FKSKI_API int fkski_band_mvm(const fkski_stats *st, const void *x, void *u, int 
  * Both are exact; the split keeps y's out-of-range(W) part (an eigenvector of A) from cancelling
  * against in-range terms in the inner products of Claim 4, which otherwise costs ~30% more
  * iterations in FP64 and breaks down in FP32.
- * MIXED: every opts->check_every iterations the residual is replaced by the true residual of the
- * FP64 solution (computed with an FP64 SpMV and FP64 K_G); convergence is declared only on it.
+ * MIXED: at the end of a chunk of opts->check_every iterations, a right-hand side whose residual
+ * fell 10x since its last replacement (or below the tolerance) gets the true residual of its FP64
+ * solution (FP64 SpMV and FP64 K_G) in place of the recursive one; convergence is declared only
+ * on that true residual.
  * Stops when ||r_k|| <= rtol ||y||.  info (host, may be NULL) receives iterations and residual.
  * Returns OK, NOT_CONVERGED (outputs written), BREAKDOWN, INVALID_ARG, OOM, CUDA.
  * Synchronizes the stream every opts->check_every iterations to test convergence. */
@@ -221,6 +231,38 @@ FKSKI_API int fkski_solve(fkski_stats *st, const fkski_kernel *kern, const fkski
  * Errors: OUT_OF_GRID / NONFINITE for a test point (mu for other points still written). */
 FKSKI_API int fkski_predict(const fkski_stats *st, const void *v, int vdtype, const void *Xstar, int xdtype,
                   int64_t nstar, void *mu_out, void *stream);
+
+/* ------------------------------------------------------------------ batches of independent problems
+ * Many unrelated GP problems of uneven sizes (serving-style batch), each with its own grid, data,
+ * kernel and noise; the arrays below have nprob entries, one per problem.  Per problem the
+ * results equal those of the single-problem call.
+ *
+ * fkski_precompute_batched: fkski_precompute for every problem in turn on `stream` (grids[p],
+ * X[p] (d_p x n[p] SoA), y[p], all in `dtype`; opts as for fkski_precompute, shared).  out[p]
+ * receives each statistics object; on an error every object already made is destroyed, out[]
+ * is set to NULL and the first error is returned.
+ *
+ * fkski_solve_batched: the posterior mean of every problem (Sec. 4, Alg. 5 or Alg. 3 per
+ * opts->x0_mode, shared opts).  st[] must be distinct objects.  All problems are set up, then
+ * their captured iteration chunks run as independent child graphs of one CUDA graph, launched
+ * once per check_every iterations until every problem has finished; finished problems skip
+ * their kernels.  a_out[p], v_out[p] as for fkski_solve (m_p entries); info (host, nprob
+ * entries, may be NULL) per problem.  Returns OK, or the first error / NOT_CONVERGED /
+ * BREAKDOWN met (BREAKDOWN first); outputs of every problem are written.
+ *
+ * fkski_predict_batched: mu_p(x*) = w_{x*}^T v_p for every problem in one kernel launch per
+ * distinct d (Def. 1, Fact 2).  v[p] device m_p (vdtype), Xstar[p] device d_p x nstar[p]
+ * (xdtype), mu_out[p] device nstar[p] (vdtype); status (host, nprob entries, may be NULL)
+ * receives each problem's OUT_OF_GRID / NONFINITE / OK.  Returns OK or the first error. */
+FKSKI_API int fkski_precompute_batched(int nprob, const fkski_grid *grids, const void *const *X, const void *const *y,
+                                       const int64_t *n, int dtype, const fkski_opts *opts, fkski_stats **out,
+                                       void *stream);
+FKSKI_API int fkski_solve_batched(int nprob, fkski_stats *const *st, const fkski_kernel *kernels,
+                                  const fkski_opts *opts, void *const *a_out, void *const *v_out, fkski_info *info,
+                                  void *stream);
+FKSKI_API int fkski_predict_batched(int nprob, const fkski_stats *const *st, const void *const *v, int vdtype,
+                                    const void *const *Xstar, int xdtype, const int64_t *nstar, void *const *mu_out,
+                                    int *status, void *stream);
 
 /* ------------------------------------------------------------------ log-likelihood and gradient
  * Log marginal likelihood of Def. 1, L = -1/2 [logdet(A) + y^T A^{-1} y + n log 2pi] with

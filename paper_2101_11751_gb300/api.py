@@ -75,12 +75,20 @@ SIGNATURES = {
     "fkski_destroy": (None, [P]),
     "fkski_kg_mvm": (ctypes.c_int, [ctypes.POINTER(CGrid), ctypes.POINTER(CKernel), ctypes.c_int, P, P,
                                     ctypes.c_int, ctypes.c_int, P]),
+    "fkski_tuning_table": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     "fkski_kg_mvm_noalloc": (ctypes.c_int, [ctypes.POINTER(CGrid), ctypes.POINTER(CKernel), ctypes.c_int, P, P,
                                             ctypes.c_int, ctypes.c_int, P]),
     "fkski_band_mvm": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P]),
     "fkski_solve": (ctypes.c_int, [P, ctypes.POINTER(CKernel), ctypes.POINTER(COpts), P, P,
                                    ctypes.POINTER(CInfo), P]),
     "fkski_predict": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int64, P, P]),
+    "fkski_precompute_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(CGrid), P, P,
+                                                ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(COpts),
+                                                P, P]),
+    "fkski_solve_batched": (ctypes.c_int, [ctypes.c_int, P, ctypes.POINTER(CKernel), ctypes.POINTER(COpts), P, P,
+                                           ctypes.POINTER(CInfo), P]),
+    "fkski_predict_batched": (ctypes.c_int, [ctypes.c_int, P, P, ctypes.c_int, P, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_int64), P, ctypes.POINTER(ctypes.c_int), P]),
     "fkski_loglik_forward": (ctypes.c_int, [P, ctypes.POINTER(CKernel), ctypes.POINTER(COpts), PD,
                                             ctypes.POINTER(CInfo), P]),
     "fkski_loglik_backward": (ctypes.c_int, [P, ctypes.POINTER(CKernel), ctypes.POINTER(COpts), PD,
@@ -280,6 +288,15 @@ def kg_mvm_noalloc(grid, kernel, V: torch.Tensor, out: torch.Tensor, param: int 
     return out
 
 
+def tuning_table() -> str:
+    """The K_G pass configurations chosen by the autotuner so far (fkski_tuning_table)."""
+    load()
+    n = _lib.fkski_tuning_table(None, 0)
+    buf = ctypes.create_string_buffer(n)
+    _lib.fkski_tuning_table(buf, n)
+    return buf.value.decode()
+
+
 def band_mvm(st: Stats, X: torch.Tensor, stream=None) -> torch.Tensor:
     load()
     out = torch.empty_like(X)
@@ -313,6 +330,60 @@ def predict(st: Stats, v: torch.Tensor, Xstar: torch.Tensor, stream=None) -> tor
     _check(_lib.fkski_predict(st.handle, _ptr(v), _dtype_code(v), _ptr(Xstar), _dtype_code(Xstar),
                               Xstar.shape[1], _ptr(mu), _stream(stream)), "fkski_predict")
     return mu
+
+
+def precompute_batched(Xs: Sequence[torch.Tensor], ys: Sequence[torch.Tensor], grids, stream=None):
+    """fkski_precompute_batched: one statistics object per problem (X_p (d_p, n_p), y_p (n_p))."""
+    load()
+    P = len(Xs)
+    G = (CGrid * P)(*[c_grid(g) for g in grids])
+    Xp = (ctypes.c_void_p * P)(*[X.data_ptr() for X in Xs])
+    yp = (ctypes.c_void_p * P)(*[y.data_ptr() for y in ys])
+    n = (ctypes.c_int64 * P)(*[X.shape[1] for X in Xs])
+    out = (ctypes.c_void_p * P)()
+    o = opts()
+    _check(_lib.fkski_precompute_batched(P, G, Xp, yp, n, _dtype_code(Xs[0]), ctypes.byref(o), out, _stream(stream)),
+           "fkski_precompute_batched")
+    return [Stats(ctypes.c_void_p(out[p]), grids[p], Xs[p].shape[1]) for p in range(P)]
+
+
+def solve_batched(sts: Sequence[Stats], kernels, rtol: float = 1e-6, maxiter: int = 1000,
+                  x0_mode: int = X0_Y_OVER_S2, precision: int = MIXED, check_every: int = 16, stream=None,
+                  allow_not_converged: bool = False):
+    """fkski_solve_batched: returns lists a_p, v_p and per-problem info dicts."""
+    load()
+    P = len(sts)
+    dt = torch.float32 if precision == MIXED else torch.float64
+    ms = [st.info()["m"] for st in sts]
+    a = [torch.empty(m, dtype=dt, device="cuda") for m in ms]
+    v = [torch.empty(m, dtype=dt, device="cuda") for m in ms]
+    H = (ctypes.c_void_p * P)(*[st.handle.value for st in sts])
+    K = (CKernel * P)(*[c_kernel(k) for k in kernels])
+    A = (ctypes.c_void_p * P)(*[t.data_ptr() for t in a])
+    V = (ctypes.c_void_p * P)(*[t.data_ptr() for t in v])
+    inf = (CInfo * P)()
+    o = opts(rtol=rtol, maxiter=maxiter, x0_mode=x0_mode, precision=precision, check_every=check_every)
+    code = _lib.fkski_solve_batched(P, H, K, ctypes.byref(o), A, V, inf, _stream(stream))
+    if not (allow_not_converged and code == E_NOT_CONVERGED):
+        _check(code, "fkski_solve_batched")
+    infos = [dict(iters=inf[p].iters, rel_residual=inf[p].rel_residual, status=inf[p].status) for p in range(P)]
+    return a, v, infos
+
+
+def predict_batched(sts: Sequence[Stats], vs: Sequence[torch.Tensor], Xstars: Sequence[torch.Tensor], stream=None):
+    """fkski_predict_batched: mu_p = w_{x*}^T v_p for every problem (one launch per distinct d)."""
+    load()
+    P = len(sts)
+    mus = [torch.empty(X.shape[1], dtype=vs[0].dtype, device="cuda") for X in Xstars]
+    H = (ctypes.c_void_p * P)(*[st.handle.value for st in sts])
+    Vp = (ctypes.c_void_p * P)(*[t.data_ptr() for t in vs])
+    Xp = (ctypes.c_void_p * P)(*[t.data_ptr() for t in Xstars])
+    n = (ctypes.c_int64 * P)(*[X.shape[1] for X in Xstars])
+    M = (ctypes.c_void_p * P)(*[t.data_ptr() for t in mus])
+    status = (ctypes.c_int * P)()
+    _check(_lib.fkski_predict_batched(P, H, Vp, _dtype_code(vs[0]), Xp, _dtype_code(Xstars[0]), n, M, status,
+                                      _stream(stream)), "fkski_predict_batched")
+    return mus
 
 
 def _grad_opts(rtol, maxiter, precision, budget, check_every):

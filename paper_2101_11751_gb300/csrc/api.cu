@@ -75,6 +75,8 @@ const char *fkski_strerror(int st) {
 
 const char *fkski_last_error_detail(void) { return g_detail; }
 
+size_t fkski_tuning_table(char *buf, size_t len) { return kg_tuning_table(buf, len); }
+
 long long fkski_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int fkski_precompute(const fkski_grid *grid, const void *X, const void *y, const void *Z, int64_t n, int dtype,
@@ -256,6 +258,35 @@ int fkski_band_mvm(const fkski_stats *st, const void *x, void *u, int nrhs, int 
 int fkski_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, void *a_out, void *v_out,
                 fkski_info *info, void *stream) {
     return solve_impl(st, kern, opts, a_out, v_out, info, S(stream));
+}
+
+int fkski_precompute_batched(int nprob, const fkski_grid *grids, const void *const *X, const void *const *y,
+                             const int64_t *n, int dtype, const fkski_opts *opts, fkski_stats **out, void *stream) {
+    if (nprob < 1 || !grids || !X || !y || !n || !out) return FKSKI_E_INVALID_ARG;
+    for (int p = 0; p < nprob; ++p) out[p] = nullptr;
+    for (int p = 0; p < nprob; ++p) {
+        const int rc = fkski_precompute(&grids[p], X[p], y[p], nullptr, n[p], dtype, opts, &out[p], stream);
+        if (rc != FKSKI_OK) {
+            for (int q = 0; q < p; ++q) {
+                fkski_destroy(out[q]);
+                out[q] = nullptr;
+            }
+            out[p] = nullptr;
+            return rc;
+        }
+    }
+    return FKSKI_OK;
+}
+
+int fkski_solve_batched(int nprob, fkski_stats *const *st, const fkski_kernel *kernels, const fkski_opts *opts,
+                        void *const *a_out, void *const *v_out, fkski_info *info, void *stream) {
+    return solve_batched_impl(nprob, st, kernels, opts, a_out, v_out, info, S(stream));
+}
+
+int fkski_predict_batched(int nprob, const fkski_stats *const *st, const void *const *v, int vdtype,
+                          const void *const *Xstar, int xdtype, const int64_t *nstar, void *const *mu_out, int *status,
+                          void *stream) {
+    return predict_batched_impl(nprob, st, v, vdtype, Xstar, xdtype, nstar, mu_out, status, S(stream));
 }
 
 int fkski_predict(const fkski_stats *st, const void *v, int vdtype, const void *Xstar, int xdtype, int64_t nstar,

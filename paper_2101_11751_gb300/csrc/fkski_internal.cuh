@@ -135,6 +135,10 @@ int solve_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts
                void *v_out, fkski_info *info, cudaStream_t s);
 int predict_impl(const fkski_stats *st, const void *v, int vdtype, const void *Xs, int xdtype,
                  int64_t ns, void *mu, cudaStream_t s);
+int solve_batched_impl(int P, fkski_stats *const *sts, const fkski_kernel *kernels, const fkski_opts *opts,
+                       void *const *a_out, void *const *v_out, fkski_info *info, cudaStream_t s);
+int predict_batched_impl(int P, const fkski_stats *const *st, const void *const *v, int vdtype, const void *const *Xs,
+                         int xdtype, const int64_t *ns, void *const *mu, int *status, cudaStream_t s);
 int loglik_forward_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts,
                         double *L, fkski_info *info, cudaStream_t s);
 int loglik_backward_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts,
@@ -153,7 +157,14 @@ int kgop_apply(KgOp *op, const void *v, void *out, int nrhs, const void *addv, d
                cudaStream_t s);
 // Pre-allocate the scratch for nrhs vectors (call before capturing applications in a graph).
 int kgop_reserve(KgOp *op, int nrhs);
+// Time the launch configurations of this operator's passes for nrhs vectors (RBF) and keep the
+// fastest per pass shape; needs the spectra (kgop_set).  Not inside a stream capture.
+int kgop_tune(KgOp *op, int nrhs, cudaStream_t s);
+// Text table of the tuned pass shapes (returns the size needed including the terminator).
+size_t kg_tuning_table(char *buf, size_t len);
 // Same, with alpha read from device memory (a double) so graphs can be reused.
+// Device flag that makes every kernel of later products return at once while it is set (null: none).
+void kgop_set_gate(KgOp *op, const int *gate);
 int kgop_apply_dev(KgOp *op, const void *v, void *out, int nrhs, const void *addv,
                    const double *alpha_dev, cudaStream_t s);
 }  // namespace fk

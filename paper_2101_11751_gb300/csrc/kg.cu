@@ -17,7 +17,9 @@
 #include "fkski_internal.cuh"
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 namespace fk {
@@ -50,52 +52,131 @@ __device__ __forceinline__ void make_twiddles(typename Cx<T>::t *tw, int L) {
     }
 }
 
-// In-place radix-2 DIF over `nl` lines of length L stored contiguously (line stride L).
-template <typename T>
+// Butterfly arithmetic with every rounding spelled out (no contraction left to the compiler), so
+// that the radix-2 and radix-4 stage groupings below give bit-identical results: the tuner's
+// choice changes speed only.
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// DIF butterfly: (u, v) -> (u + v, (u - v) w)
+template <typename C>
+__device__ __forceinline__ void bf_dif(C &u, C &v, const C w) {
+    const auto dx = r_sub(u.x, v.x), dy = r_sub(u.y, v.y);
+    u.x = r_add(u.x, v.x);
+    u.y = r_add(u.y, v.y);
+    v.x = r_fma(dx, w.x, -r_mul(dy, w.y));
+    v.y = r_fma(dx, w.y, r_mul(dy, w.x));
+}
+
+// DIT inverse butterfly: t = v conj(w); (u, v) -> (u + t, u - t)
+template <typename C>
+__device__ __forceinline__ void bf_dit(C &u, C &v, const C w) {
+    const auto tx = r_fma(v.x, w.x, r_mul(v.y, w.y));
+    const auto ty = r_fma(v.y, w.x, -r_mul(v.x, w.y));
+    v.x = r_sub(u.x, tx);
+    v.y = r_sub(u.y, ty);
+    u.x = r_add(u.x, tx);
+    u.y = r_add(u.y, ty);
+}
+
+// In-place DIF over `nl` lines of length L stored contiguously (line stride L), natural order in,
+// bit-reversed out.  RADIX 4 runs two radix-2 stages (spans h, h/2) per pass over shared memory:
+// each thread keeps 4 values in registers, halving the passes and barriers.
+template <typename T, int RADIX>
 __device__ __forceinline__ void fft_dif(typename Cx<T>::t *x, int nl, int L, const typename Cx<T>::t *tw) {
     using C = typename Cx<T>::t;
+    int h = L >> 1;
+    if (RADIX == 4) {
+        const int ng = nl * (L >> 2);
+        const int lq = __ffs(L) - 3;  // log2(L/4)
+        for (; h >= 2; h >>= 2) {
+            const int q = h >> 1, lqq = __ffs(q) - 1;
+            const int tA = L / (2 * h), tB = L / h;
+            for (int b = threadIdx.x; b < ng; b += blockDim.x) {
+                const int line = b >> lq, k = b & ((L >> 2) - 1);
+                const int j = k & (q - 1), blk = k >> lqq;
+                C *xl = x + line * L + blk * 2 * h;
+                C a0 = xl[j], a1 = xl[j + q], a2 = xl[j + h], a3 = xl[j + h + q];
+                bf_dif(a0, a2, tw[j * tA]);
+                bf_dif(a1, a3, tw[(j + q) * tA]);
+                const C wb = tw[j * tB];
+                bf_dif(a0, a1, wb);
+                bf_dif(a2, a3, wb);
+                xl[j] = a0;
+                xl[j + q] = a1;
+                xl[j + h] = a2;
+                xl[j + h + q] = a3;
+            }
+            __syncthreads();
+        }
+    }
     const int nbf = nl * (L >> 1);
     const int lhalf = __ffs(L) - 2;  // log2(L/2)
-    for (int h = L >> 1; h >= 1; h >>= 1) {
+    for (; h >= 1; h >>= 1) {
         const int tstep = L / (2 * h);
         const int lh = __ffs(h) - 1;
         for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
             const int line = b >> lhalf, k = b & ((L >> 1) - 1);
             const int j = k & (h - 1), blk = k >> lh;
             C *xl = x + line * L + blk * 2 * h;
-            const C u = xl[j], v = xl[j + h];
-            const C w = tw[j * tstep];
-            const T dx = u.x - v.x, dy = u.y - v.y;
-            xl[j].x = u.x + v.x;
-            xl[j].y = u.y + v.y;
-            xl[j + h].x = dx * w.x - dy * w.y;
-            xl[j + h].y = dx * w.y + dy * w.x;
+            C u = xl[j], v = xl[j + h];
+            bf_dif(u, v, tw[j * tstep]);
+            xl[j] = u;
+            xl[j + h] = v;
         }
         __syncthreads();
     }
 }
 
-// In-place radix-2 DIT inverse (conjugate twiddles, no 1/L: folded into the spectrum).
-template <typename T>
+// In-place DIT inverse (conjugate twiddles, no 1/L: folded into the spectrum), bit-reversed in,
+// natural out.  RADIX 4 groups the spans (h, 2h) from h = 1 upwards.
+template <typename T, int RADIX>
 __device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L, const typename Cx<T>::t *tw) {
     using C = typename Cx<T>::t;
+    int h = 1;
+    if (RADIX == 4) {
+        const int ng = nl * (L >> 2);
+        const int lq = __ffs(L) - 3;  // log2(L/4)
+        for (; 4 * h <= L; h <<= 2) {
+            const int lh = __ffs(h) - 1;
+            const int tA = L / (2 * h), tB = L / (4 * h);
+            for (int b = threadIdx.x; b < ng; b += blockDim.x) {
+                const int line = b >> lq, k = b & ((L >> 2) - 1);
+                const int j = k & (h - 1), blk = k >> lh;
+                C *xl = x + line * L + blk * 4 * h;
+                C a0 = xl[j], a1 = xl[j + h], a2 = xl[j + 2 * h], a3 = xl[j + 3 * h];
+                const C wa = tw[j * tA];
+                bf_dit(a0, a1, wa);
+                bf_dit(a2, a3, wa);
+                bf_dit(a0, a2, tw[j * tB]);
+                bf_dit(a1, a3, tw[(j + h) * tB]);
+                xl[j] = a0;
+                xl[j + h] = a1;
+                xl[j + 2 * h] = a2;
+                xl[j + 3 * h] = a3;
+            }
+            __syncthreads();
+        }
+    }
     const int nbf = nl * (L >> 1);
     const int lhalf = __ffs(L) - 2;  // log2(L/2)
-    for (int h = 1; h < L; h <<= 1) {
+    for (; h < L; h <<= 1) {
         const int tstep = L / (2 * h);
         const int lh = __ffs(h) - 1;
         for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
             const int line = b >> lhalf, k = b & ((L >> 1) - 1);
             const int j = k & (h - 1), blk = k >> lh;
             C *xl = x + line * L + blk * 2 * h;
-            const C u = xl[j], v = xl[j + h];
-            const C w = tw[j * tstep];
-            // v * conj(w)
-            const T tx = v.x * w.x + v.y * w.y, ty = v.y * w.x - v.x * w.y;
-            xl[j].x = u.x + tx;
-            xl[j].y = u.y + ty;
-            xl[j + h].x = u.x - tx;
-            xl[j + h].y = u.y - ty;
+            C u = xl[j], v = xl[j + h];
+            bf_dit(u, v, tw[j * tstep]);
+            xl[j] = u;
+            xl[j + h] = v;
         }
         __syncthreads();
     }
@@ -104,17 +185,27 @@ __device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L,
 // ------------------------------------------------------------------ Kronecker (real) axis pass
 // Vector layout per rhs: [O][M][S] (axis of length M, S = product of later axes).
 // Real lines l = (r*O + o)*S + s; two consecutive lines form one complex line.
+// Lines of different right-hand sides never share a complex transform: FP32 rounding in the
+// shared transform is relative to the larger of the two lines, which would put errors of one
+// vector's size into the other.  When a rhs has an odd number of lines, its last line is paired
+// with an empty padding line (index space per rhs rounded up to even).
 struct RealPass {
-    int64_t nlines;  // R * O * S
+    int64_t nlines;  // R * lpr2 (padded line slots)
+    int64_t lpr;     // real lines per rhs = O * S
+    int64_t lpr2;    // lpr rounded up to even
     int64_t S;       // inner stride
     int M, L;
     int Q;           // real lines per CTA (even)
 };
 
-template <typename T, bool EPI>
-__global__ void __launch_bounds__(FFT_T) k_kron_pass(const T *__restrict__ in, T *__restrict__ out, RealPass p,
+constexpr int FFT_TMAX = 512;
+
+template <typename T, bool EPI, int RADIX>
+__global__ void __launch_bounds__(FFT_TMAX) k_kron_pass(const T *__restrict__ in, T *__restrict__ out, RealPass p,
                                                       const T *__restrict__ lam_br, const T *__restrict__ addv,
-                                                      const double *__restrict__ alpha_dev, double alpha_host) {
+                                                      const double *__restrict__ alpha_dev, double alpha_host,
+                                                      const int *__restrict__ gate) {
+    if (gate && *gate) return;
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *tw = reinterpret_cast<C *>(smraw);
@@ -130,30 +221,34 @@ __global__ void __launch_bounds__(FFT_T) k_kron_pass(const T *__restrict__ in, T
         x[e].y = T(0);
     }
     __syncthreads();
-    // load: element (q, i), address base(l0+q) + i*S
+    // load: element (q, i), address base(line) + i*S (padding slots stay zero)
     const int64_t S = p.S;
     for (int e = threadIdx.x; e < nq * M; e += blockDim.x) {
         int q, i;
         if (S == 1) { q = e / M; i = e % M; } else { q = e % nq; i = e / nq; }
-        const int64_t l = l0 + q;
+        const int64_t slot = l0 + q, lr = slot % p.lpr2;
+        if (lr >= p.lpr) continue;
+        const int64_t l = (slot / p.lpr2) * p.lpr + lr;
         const int64_t base = (l / S) * (int64_t)M * S + (l % S);
         const T v = in[base + (int64_t)i * S];
         if (q & 1) x[(q >> 1) * L + i].y = v; else x[(q >> 1) * L + i].x = v;
     }
     __syncthreads();
-    fft_dif<T>(x, nc, L, tw);
+    fft_dif<T, RADIX>(x, nc, L, tw);
     for (int e = threadIdx.x; e < nc * L; e += blockDim.x) {
         const T lm = lam_br[e % L];
         x[e].x *= lm;
         x[e].y *= lm;
     }
     __syncthreads();
-    fft_dit_inv<T>(x, nc, L, tw);
+    fft_dit_inv<T, RADIX>(x, nc, L, tw);
     const T alpha = EPI ? (alpha_dev ? (T)(*alpha_dev) : (T)alpha_host) : T(0);
     for (int e = threadIdx.x; e < nq * M; e += blockDim.x) {
         int q, i;
         if (S == 1) { q = e / M; i = e % M; } else { q = e % nq; i = e / nq; }
-        const int64_t l = l0 + q;
+        const int64_t slot = l0 + q, lr = slot % p.lpr2;
+        if (lr >= p.lpr) continue;
+        const int64_t l = (slot / p.lpr2) * p.lpr + lr;
         const int64_t a = (l / S) * (int64_t)M * S + (l % S) + (int64_t)i * S;
         T v = (q & 1) ? x[(q >> 1) * L + i].y : x[(q >> 1) * L + i].x;
         if (EPI) v = fma(alpha, addv[a], v);
@@ -172,7 +267,8 @@ struct CplxPass {
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(FFT_T) k_cplx_pass(const typename Cx<T>::t *__restrict__ in, typename Cx<T>::t *__restrict__ out,
-                                                      CplxPass p, const T *__restrict__ lam) {
+                                                      CplxPass p, const T *__restrict__ lam, const int *__restrict__ gate) {
+    if (gate && *gate) return;
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *tw = reinterpret_cast<C *>(smraw);
@@ -194,7 +290,7 @@ __global__ void __launch_bounds__(FFT_T) k_cplx_pass(const typename Cx<T>::t *__
         x[q * L + i] = in[(l / S) * (int64_t)p.Min * S + (l % S) + (int64_t)i * S];
     }
     __syncthreads();
-    if (MODE == 0 || MODE == 2) fft_dif<T>(x, Q, L, tw);
+    if (MODE == 0 || MODE == 2) fft_dif<T, 4>(x, Q, L, tw);
     if (MODE == 2) {
         for (int e = threadIdx.x; e < nq * L; e += blockDim.x) {
             const int q = e / L, k = e % L;
@@ -205,7 +301,7 @@ __global__ void __launch_bounds__(FFT_T) k_cplx_pass(const typename Cx<T>::t *__
         }
         __syncthreads();
     }
-    if (MODE == 1 || MODE == 2) fft_dit_inv<T>(x, Q, L, tw);
+    if (MODE == 1 || MODE == 2) fft_dit_inv<T, 4>(x, Q, L, tw);
     for (int e = threadIdx.x; e < nq * p.Mout; e += blockDim.x) {
         int q, i;
         if (S == 1) { q = e / p.Mout; i = e % p.Mout; } else { q = e % nq; i = e / nq; }
@@ -214,29 +310,28 @@ __global__ void __launch_bounds__(FFT_T) k_cplx_pass(const typename Cx<T>::t *__
     }
 }
 
-// pack real rhs pairs into complex tensors of shape (M_1..M_d) and unpack (with epilogue)
+// real rhs into complex tensors of shape (M_1..M_d), one rhs each (imaginary part zero: rhs
+// never share a transform, for the reason given at RealPass), and back (with epilogue)
 template <typename T>
-__global__ void k_pack_pairs(const T *__restrict__ v, typename Cx<T>::t *__restrict__ z, int64_t m, int nrhs) {
-    const int npair = (nrhs + 1) / 2;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)npair * m; e += (int64_t)gridDim.x * blockDim.x) {
-        const int pr = (int)(e / m);
-        const int64_t i = e % m;
+__global__ void k_pack_pairs(const T *__restrict__ v, typename Cx<T>::t *__restrict__ z, int64_t m, int nrhs,
+                             const int *__restrict__ gate) {
+    if (gate && *gate) return;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nrhs * m; e += (int64_t)gridDim.x * blockDim.x) {
         typename Cx<T>::t c;
-        c.x = v[(int64_t)(2 * pr) * m + i];
-        c.y = (2 * pr + 1 < nrhs) ? v[(int64_t)(2 * pr + 1) * m + i] : T(0);
+        c.x = v[e];
+        c.y = T(0);
         z[e] = c;
     }
 }
 
 template <typename T>
 __global__ void k_unpack_pairs(const typename Cx<T>::t *__restrict__ z, T *__restrict__ out, int64_t m, int nrhs,
-                               const T *__restrict__ addv, const double *__restrict__ alpha_dev, double alpha_host) {
+                               const T *__restrict__ addv, const double *__restrict__ alpha_dev, double alpha_host,
+                               const int *__restrict__ gate) {
+    if (gate && *gate) return;
     const T alpha = addv ? (alpha_dev ? (T)(*alpha_dev) : (T)alpha_host) : T(0);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nrhs * m; e += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / m);
-        const int64_t i = e % m;
-        const typename Cx<T>::t c = z[(int64_t)(r / 2) * m + i];
-        T v = (r & 1) ? c.y : c.x;
+        T v = z[e].x;
         if (addv) v = fma(alpha, addv[e], v);
         out[e] = v;
     }
@@ -253,15 +348,18 @@ __device__ __forceinline__ int circ_delta(int i, int M, int L, bool &valid) {
 }
 
 // Kronecker factor spectrum (one CTA): lam_br[k] = scale / L * DFT(c)[bitrev(k)] for the RBF
-// factor exp(-1/2 (delta h / l)^2) (or its derivative in l when deriv).
+// factor exp(-1/2 (delta h / l)^2) (or its derivative in l when deriv).  Always computed in FP64
+// and rounded once to T: an FP32 transform would give the small eigenvalues absolute errors near
+// 2^-24 of the largest, i.e. a different operator from the FP64 one, and the FP32 solver's
+// true-residual checks (FP64 K_G) must see the same operator as its iterations.
 template <typename T>
 __global__ void __launch_bounds__(FFT_T) k_spectrum_1d(T *__restrict__ lam_br, int M, int L, double h, double ell,
                                                         int deriv, double scale) {
-    using C = typename Cx<T>::t;
+    using C = double2;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *tw = reinterpret_cast<C *>(smraw);
     C *x = tw + L / 2;
-    make_twiddles<T>(tw, L);
+    make_twiddles<double>(tw, L);
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         bool ok;
         const int dl = circ_delta(i, M, L, ok);
@@ -271,12 +369,12 @@ __global__ void __launch_bounds__(FFT_T) k_spectrum_1d(T *__restrict__ lam_br, i
             v = exp(-0.5 * r * r);
             if (deriv) v *= r * r / ell;
         }
-        x[i].x = (T)v;
-        x[i].y = T(0);
+        x[i].x = v;
+        x[i].y = 0.0;
     }
     __syncthreads();
-    fft_dif<T>(x, 1, L, tw);
-    for (int k = threadIdx.x; k < L; k += blockDim.x) lam_br[k] = (T)(scale / L) * x[k].x;
+    fft_dif<double, 4>(x, 1, L, tw);
+    for (int k = threadIdx.x; k < L; k += blockDim.x) lam_br[k] = (T)(scale / L * x[k].x);
 }
 
 // d-level embedding values for a (possibly derivative) stationary kernel, written as a complex
@@ -326,7 +424,7 @@ __global__ void k_embed_values(typename Cx<T>::t *__restrict__ z, EmbedParams ep
 }
 
 template <typename T>
-__global__ void k_take_real_scaled(const typename Cx<T>::t *__restrict__ z, T *__restrict__ lam, int64_t N, double scale) {
+__global__ void k_take_real_scaled(const double2 *__restrict__ z, T *__restrict__ lam, int64_t N, double scale) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
         lam[e] = (T)(scale * (double)z[e].x);
 }
@@ -344,6 +442,7 @@ struct KgOp {
     int64_t N;          // prod L_k
     void *scratch;      // work buffer
     size_t scratch_bytes;
+    const int *gate;    // device flag: when set, the product's kernels return at once (null: always run)
 };
 
 static int next_pow2(int64_t v) {
@@ -417,19 +516,19 @@ static CplxPass cplx_geom(const int64_t ext[3], int d, int a, int Min, int Mout,
 
 template <typename T>
 static int launch_cplx(const typename Cx<T>::t *in, typename Cx<T>::t *out, CplxPass p, int mode, const T *lam,
-                       cudaStream_t s) {
+                       cudaStream_t s, const int *gate = nullptr) {
     using C = typename Cx<T>::t;
     const size_t sm = sizeof(C) * ((size_t)p.L / 2 + (size_t)p.Q * p.L);
     const unsigned nb = (unsigned)cdiv(p.nlines, p.Q);
     if (mode == 0) {
         FK_CUDA(cudaFuncSetAttribute(k_cplx_pass<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_cplx_pass<T, 0><<<nb, FFT_T, sm, s>>>(in, out, p, lam);
+        k_cplx_pass<T, 0><<<nb, FFT_T, sm, s>>>(in, out, p, lam, gate);
     } else if (mode == 1) {
         FK_CUDA(cudaFuncSetAttribute(k_cplx_pass<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_cplx_pass<T, 1><<<nb, FFT_T, sm, s>>>(in, out, p, lam);
+        k_cplx_pass<T, 1><<<nb, FFT_T, sm, s>>>(in, out, p, lam, gate);
     } else {
         FK_CUDA(cudaFuncSetAttribute(k_cplx_pass<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_cplx_pass<T, 2><<<nb, FFT_T, sm, s>>>(in, out, p, lam);
+        k_cplx_pass<T, 2><<<nb, FFT_T, sm, s>>>(in, out, p, lam, gate);
     }
     FK_LAUNCH();
     return FKSKI_OK;
@@ -437,9 +536,10 @@ static int launch_cplx(const typename Cx<T>::t *in, typename Cx<T>::t *out, Cplx
 
 // BTTB spectrum: embed kernel values on the L-box, forward DIF along every axis (bit-reversed
 // order per axis), keep the real part scaled by 1/N.
+// Computed in FP64 for both operator precisions (see k_spectrum_1d), rounded once to T.
 template <typename T>
 static int bttb_spectrum(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s) {
-    using C = typename Cx<T>::t;
+    using C = double2;
     const int d = op->d;
     const int64_t N = op->N;
     size_t have = 0;
@@ -460,13 +560,13 @@ static int bttb_spectrum(KgOp *op, const fkski_kernel *kern, int param, cudaStre
     ep.kind = kern->type == FKSKI_MATERN52 ? 0 : 1;
     ep.deriv = param;
     const unsigned nb = (unsigned)std::min<int64_t>(cdiv(N, 256), 4096);
-    k_embed_values<T><<<nb, 256, 0, s>>>(z0, ep, N);
+    k_embed_values<double><<<nb, 256, 0, s>>>(z0, ep, N);
     FK_LAUNCH();
     int64_t ext[3] = {op->L[0], op->L[1], op->L[2]};
     C *cur = z0, *nxt = z1;
     for (int a = d - 1; a >= 0; --a) {
         CplxPass p = cplx_geom(ext, d, a, op->L[a], op->L[a], op->L[a], 1);
-        FK_TRY(launch_cplx<T>(cur, nxt, p, 0, (const T *)nullptr, s));
+        FK_TRY(launch_cplx<double>(cur, nxt, p, 0, (const double *)nullptr, s));
         std::swap(cur, nxt);
     }
     k_take_real_scaled<T><<<nb, 256, 0, s>>>(cur, (T *)op->lamN, N, 1.0 / (double)N);
@@ -492,7 +592,7 @@ int kgop_set(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s) {
             if (!op->lam[a]) FK_TRY(ensure(&op->lam[a], have, es * op->L[a]));
             const double scale = (a == 0) ? (param == op->d ? 1.0 : kern->outputscale) : 1.0;
             const int deriv = (param == a) ? 1 : 0;
-            const size_t sm = es * 2 * ((size_t)op->L[a] / 2 + (size_t)op->L[a]);
+            const size_t sm = sizeof(double2) * ((size_t)op->L[a] / 2 + (size_t)op->L[a]);
             if (op->dtype == FKSKI_F32) {
                 FK_CUDA(cudaFuncSetAttribute(k_spectrum_1d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
                 k_spectrum_1d<float><<<1, FFT_T, sm, s>>>((float *)op->lam[a], (int)op->g.M[a], op->L[a], op->g.h[a],
@@ -507,6 +607,173 @@ int kgop_set(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s) {
         return FKSKI_OK;
     }
     return op->dtype == FKSKI_F32 ? bttb_spectrum<float>(op, kern, param, s) : bttb_spectrum<double>(op, kern, param, s);
+}
+
+// ------------------------------------------------------------------ pass configuration and tuner
+// A Kronecker pass is launched with (RADIX, complex lines per CTA, threads per CTA).  The choice
+// changes speed only (the stage groupings are bit-identical, and lines are independent).  The
+// tuner times every candidate on the real pass shape (once per shape and process, outside any
+// graph capture: the solver calls kgop_tune before capturing) and keeps the fastest; untuned shapes get a default that
+// puts at least ~4 CTAs on every SM.
+struct PassCfg {
+    int radix, cl, threads;
+    float ms;  // tuned time per launch (0: default, not tuned)
+};
+
+struct PassKey {
+    int dtype, L, M;
+    int64_t S, nlines;
+    bool operator<(const PassKey &o) const {
+        if (dtype != o.dtype) return dtype < o.dtype;
+        if (L != o.L) return L < o.L;
+        if (M != o.M) return M < o.M;
+        if (S != o.S) return S < o.S;
+        return nlines < o.nlines;
+    }
+};
+
+static std::mutex g_tune_mu;
+static std::map<PassKey, PassCfg> g_tune;
+
+static int device_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 1;
+    }
+    return n;
+}
+
+static PassCfg default_cfg(const RealPass &p) {
+    const int64_t ncl = p.nlines / 2;  // complex lines
+    int cl = std::max(1, FFT_SMEM_CPLX / p.L);
+    while (cl > 1 && cdiv(ncl, cl) < 4 * device_sms()) cl >>= 1;
+    return PassCfg{4, cl, 256, 0.f};
+}
+
+static PassCfg pass_config(int dtype, const RealPass &p, int nrhs) {
+    (void)nrhs;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const auto it = g_tune.find(PassKey{dtype, p.L, p.M, p.S, p.nlines});
+    return it != g_tune.end() ? it->second : default_cfg(p);
+}
+
+template <typename T>
+static int launch_kron(const T *src, T *dst, RealPass p, const PassCfg &cfg, const T *lam, const T *addv,
+                       const double *alpha_dev, double alpha, const int *gate, cudaStream_t s) {
+    p.Q = 2 * cfg.cl;
+    const size_t sm = sizeof(typename Cx<T>::t) * ((size_t)p.L / 2 + (size_t)cfg.cl * p.L);
+    const unsigned nb = (unsigned)cdiv(p.nlines, p.Q);
+#define FK_KRON(EPIV, RADV)                                                                                      \
+    do {                                                                                                         \
+        FK_CUDA(cudaFuncSetAttribute(k_kron_pass<T, EPIV, RADV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+        k_kron_pass<T, EPIV, RADV><<<nb, cfg.threads, sm, s>>>(src, dst, p, lam, addv, alpha_dev, alpha, gate); \
+    } while (0)
+    if (addv) {
+        if (cfg.radix == 4) FK_KRON(true, 4); else FK_KRON(true, 2);
+    } else {
+        if (cfg.radix == 4) FK_KRON(false, 4); else FK_KRON(false, 2);
+    }
+#undef FK_KRON
+    FK_LAUNCH();
+    return FKSKI_OK;
+}
+
+// Time the candidates of one pass shape on scratch data and record the fastest.
+template <typename T>
+static int tune_pass(int dtype, RealPass p, const T *lam, T *buf_in, T *buf_out, cudaStream_t s) {
+    const PassKey key{dtype, p.L, p.M, p.S, p.nlines};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        if (g_tune.count(key)) return FKSKI_OK;
+    }
+    cudaEvent_t e0, e1;
+    FK_CUDA(cudaEventCreate(&e0));
+    FK_CUDA(cudaEventCreate(&e1));
+    PassCfg best = default_cfg(p);
+    best.ms = 1e30f;
+    const int clmax = std::max(1, FFT_SMEM_CPLX / p.L);
+    const int64_t ncl = std::max<int64_t>(1, p.nlines / 2);
+    int rc = FKSKI_OK;
+    for (int radix : {4, 2}) {
+        for (int threads : {128, 256, 512}) {
+            for (int cl = 1; cl <= clmax && rc == FKSKI_OK; cl <<= 1) {
+                if (cl > 1 && cl / 2 >= ncl) break;  // more lines per CTA than there are lines
+                const PassCfg c{radix, cl, threads, 0.f};
+                rc = launch_kron<T>(buf_in, buf_out, p, c, lam, nullptr, nullptr, 0.0, nullptr, s);  // warm-up
+                if (rc) break;
+                const int reps = 3;
+                cudaError_t e = cudaEventRecord(e0, s);
+                for (int r = 0; r < reps && rc == FKSKI_OK; ++r)
+                    rc = launch_kron<T>(buf_in, buf_out, p, c, lam, nullptr, nullptr, 0.0, nullptr, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) { rc = note_cuda_error(e, __FILE__, __LINE__); break; }
+                ms /= reps;
+                if (ms < best.ms) best = PassCfg{radix, cl, threads, ms};
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = best;
+    return FKSKI_OK;
+}
+
+template <typename T>
+static int kron_tune(KgOp *op, int nrhs, cudaStream_t s) {
+    const int64_t m = op->m;
+    T *buf = nullptr;
+    FK_CUDA(cudaMallocAsync((void **)&buf, sizeof(T) * 2 * (size_t)nrhs * m, s));
+    int rc = cudaMemsetAsync(buf, 0, sizeof(T) * 2 * (size_t)nrhs * m, s) == cudaSuccess ? FKSKI_OK : FKSKI_E_CUDA;
+    for (int a = 0; a < op->d && rc == FKSKI_OK; ++a) {
+        RealPass p;
+        int64_t S = 1;
+        for (int k = a + 1; k < op->d; ++k) S *= op->g.M[k];
+        p.S = S;
+        p.M = (int)op->g.M[a];
+        p.L = op->L[a];
+        p.lpr = m / p.M;
+        p.lpr2 = p.lpr + (p.lpr & 1);
+        p.nlines = (int64_t)nrhs * p.lpr2;
+        p.Q = 2;
+        rc = tune_pass<T>(op->dtype, p, (const T *)op->lam[a], buf, buf + (size_t)nrhs * m, s);
+    }
+    cudaFreeAsync(buf, s);
+    return rc;
+}
+
+int kgop_tune(KgOp *op, int nrhs, cudaStream_t s) {
+    if (op->kind != FKSKI_RBF || nrhs < 1) return FKSKI_OK;
+    for (int a = 0; a < op->d; ++a)
+        if (!op->lam[a]) return FKSKI_E_INVALID_ARG;  // spectra first (kgop_set)
+    return op->dtype == FKSKI_F32 ? kron_tune<float>(op, nrhs, s) : kron_tune<double>(op, nrhs, s);
+}
+
+// One line per tuned pass shape: "dtype L M S lines -> radix cl threads ms".
+size_t kg_tuning_table(char *buf, size_t len) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    std::string out;
+    char line[200];
+    for (const auto &kv : g_tune) {
+        snprintf(line, sizeof(line), "%s L=%d M=%d S=%lld lines=%lld -> radix %d, %d lines/CTA, %d threads, %.4f ms\n",
+                 kv.first.dtype == FKSKI_F32 ? "f32" : "f64", kv.first.L, kv.first.M, (long long)kv.first.S,
+                 (long long)kv.first.nlines, kv.second.radix, kv.second.cl, kv.second.threads, (double)kv.second.ms);
+        out += line;
+    }
+    if (buf && len > 0) {
+        const size_t n = std::min(len - 1, out.size());
+        memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return out.size() + 1;
 }
 
 template <typename T>
@@ -531,19 +798,14 @@ static int kron_apply(KgOp *op, const T *v, T *out, int nrhs, const T *addv, con
         p.S = S;
         p.M = (int)op->g.M[a];
         p.L = op->L[a];
-        p.nlines = (int64_t)nrhs * (m / p.M);
-        p.Q = std::max(2, 2 * (FFT_SMEM_CPLX / p.L));
-        const size_t sm = sizeof(typename Cx<T>::t) * ((size_t)p.L / 2 + (size_t)(p.Q / 2) * p.L);
-        const unsigned nb = (unsigned)cdiv(p.nlines, p.Q);
+        p.lpr = m / p.M;
+        p.lpr2 = p.lpr + (p.lpr & 1);
+        p.nlines = (int64_t)nrhs * p.lpr2;
+        const PassCfg cfg = pass_config(op->dtype, p, nrhs);
+        p.Q = 2 * cfg.cl;
         const bool last = step == d - 1;
-        if (last && addv) {
-            FK_CUDA(cudaFuncSetAttribute(k_kron_pass<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            k_kron_pass<T, true><<<nb, FFT_T, sm, s>>>(src, dst, p, (const T *)op->lam[a], addv, alpha_dev, alpha);
-        } else {
-            FK_CUDA(cudaFuncSetAttribute(k_kron_pass<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            k_kron_pass<T, false><<<nb, FFT_T, sm, s>>>(src, dst, p, (const T *)op->lam[a], nullptr, nullptr, 0.0);
-        }
-        FK_LAUNCH();
+        FK_TRY((launch_kron<T>(src, dst, p, cfg, (const T *)op->lam[a], last ? addv : nullptr, alpha_dev, alpha,
+                               op->gate, s)));
         src = dst;
     }
     return FKSKI_OK;
@@ -555,7 +817,7 @@ static int bttb_apply(KgOp *op, const T *v, T *out, int nrhs, const T *addv, con
     using C = typename Cx<T>::t;
     const int d = op->d;
     const int64_t m = op->m;
-    const int npair = (nrhs + 1) / 2;
+    const int npair = nrhs;  // complex tensors, one per rhs
     // largest intermediate: M_0 x L_1 x ... x L_{d-1} complex per pair (or m complex)
     int64_t big = op->g.M[0];
     for (int k = 1; k < d; ++k) big *= op->L[k];
@@ -564,14 +826,14 @@ static int bttb_apply(KgOp *op, const T *v, T *out, int nrhs, const T *addv, con
     C *z0 = (C *)op->scratch;
     C *z1 = z0 + (size_t)npair * big;
     const unsigned nb = (unsigned)std::min<int64_t>(cdiv((int64_t)npair * m, 256), 4096);
-    k_pack_pairs<T><<<nb, 256, 0, s>>>(v, z0, m, nrhs);
+    k_pack_pairs<T><<<nb, 256, 0, s>>>(v, z0, m, nrhs, op->gate);
     FK_LAUNCH();
     int64_t ext[3] = {op->g.M[0], op->g.M[1], op->g.M[2]};
     C *cur = z0, *nxt = z1;
     // forward along axes d-1..1 (extent M -> L)
     for (int a = d - 1; a >= 1; --a) {
         CplxPass p = cplx_geom(ext, d, a, (int)op->g.M[a], op->L[a], op->L[a], npair);
-        FK_TRY(launch_cplx<T>(cur, nxt, p, 0, (const T *)nullptr, s));
+        FK_TRY(launch_cplx<T>(cur, nxt, p, 0, (const T *)nullptr, s, op->gate));
         ext[a] = op->L[a];
         std::swap(cur, nxt);
     }
@@ -579,17 +841,17 @@ static int bttb_apply(KgOp *op, const T *v, T *out, int nrhs, const T *addv, con
     {
         CplxPass p = cplx_geom(ext, d, 0, (int)op->g.M[0], (int)op->g.M[0], op->L[0], npair);
         // lam is indexed [k * S + s] with S = prod_{k>0} L_k = p.S (the pair index folds into O)
-        FK_TRY(launch_cplx<T>(cur, nxt, p, 2, (const T *)op->lamN, s));
+        FK_TRY(launch_cplx<T>(cur, nxt, p, 2, (const T *)op->lamN, s, op->gate));
         std::swap(cur, nxt);
     }
     for (int a = 1; a < d; ++a) {
         CplxPass p = cplx_geom(ext, d, a, op->L[a], (int)op->g.M[a], op->L[a], npair);
-        FK_TRY(launch_cplx<T>(cur, nxt, p, 1, (const T *)nullptr, s));
+        FK_TRY(launch_cplx<T>(cur, nxt, p, 1, (const T *)nullptr, s, op->gate));
         ext[a] = op->g.M[a];
         std::swap(cur, nxt);
     }
     const unsigned nb2 = (unsigned)std::min<int64_t>(cdiv((int64_t)nrhs * m, 256), 4096);
-    k_unpack_pairs<T><<<nb2, 256, 0, s>>>(cur, out, m, nrhs, addv, alpha_dev, alpha);
+    k_unpack_pairs<T><<<nb2, 256, 0, s>>>(cur, out, m, nrhs, addv, alpha_dev, alpha, op->gate);
     FK_LAUNCH();
     return FKSKI_OK;
 }
@@ -619,11 +881,13 @@ int kgop_reserve(KgOp *op, int nrhs) {
         int64_t big = op->g.M[0];
         for (int k = 1; k < d; ++k) big *= op->L[k];
         big = std::max(big, op->m);
-        want = 2 * 2 * es * (size_t)((nrhs + 1) / 2) * big;
+        want = 2 * 2 * es * (size_t)nrhs * big;
     }
     if (want == 0) return FKSKI_OK;
     return ensure(&op->scratch, op->scratch_bytes, want);
 }
+
+void kgop_set_gate(KgOp *op, const int *gate) { op->gate = gate; }
 
 int kgop_apply(KgOp *op, const void *v, void *out, int nrhs, const void *addv, double alpha, cudaStream_t s) {
     return kgop_apply_any(op, v, out, nrhs, addv, nullptr, alpha, s);

@@ -20,6 +20,7 @@
 #include "fkski_internal.cuh"
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 namespace fk {
@@ -307,6 +308,18 @@ constexpr int RS_ITEMS = 32;
 constexpr int RS_TILE = RS_T * RS_ITEMS;  // 8192; each warp owns 1024 contiguous keys
 constexpr int RS_MAXBITS = 10;
 
+// Lanes of the warp holding the same `bits`-bit digit, from one ballot per bit (lanes outside
+// `valid_mask` never match).
+__device__ __forceinline__ unsigned digit_peers(uint32_t dg, int bits, unsigned valid_mask) {
+    unsigned peers = valid_mask;
+    for (int b = 0; b < bits; ++b) {
+        const unsigned bit = (dg >> b) & 1u;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
 __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
                                                      int bits, uint32_t *__restrict__ ghist, int64_t ntiles) {
     __shared__ uint32_t h[1 << RS_MAXBITS];
@@ -318,9 +331,10 @@ __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint32_t *__restrict_
     const int lane = threadIdx.x & 31;
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int64_t i = base + (int64_t)k * RS_T + threadIdx.x;
-        const uint32_t dg = i < n ? (keys[i] >> shift) & mask : 0xFFFFFFFFu;
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
-        if (dg != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&h[dg], (uint32_t)__popc(peers));
+        const bool valid = i < n;
+        const uint32_t dg = valid ? (keys[i] >> shift) & mask : 0u;
+        const unsigned peers = digit_peers(dg, bits, __ballot_sync(0xFFFFFFFFu, valid));
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[dg], (uint32_t)__popc(peers));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += RS_T) ghist[(int64_t)i * ntiles + blockIdx.x] = h[i];
@@ -346,15 +360,22 @@ __global__ void __launch_bounds__(RS_T) k_radix_scatter(const uint32_t *__restri
     const int tile_n = (int)min((int64_t)RS_TILE, n - base);
     for (int i = threadIdx.x; i < 8 * nb; i += RS_T) wcnt[i] = 0;
     __syncthreads();
-    uint32_t kr[RS_ITEMS];
+    // rank of each key among the earlier keys of this warp with the same digit
+    // (ranks < 1024: two 16-bit ranks per register)
+    uint32_t kr[RS_ITEMS], rk[RS_ITEMS / 2];
+    const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int s = 0; s < RS_ITEMS; ++s) {
         const int pos = w * (RS_ITEMS * 32) + s * 32 + lane;
         const bool valid = pos < tile_n;
         kr[s] = valid ? kin[base + pos] : 0u;
-        const uint32_t dg = valid ? (kr[s] >> shift) & mask : 0xFFFFFFFFu;
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
-        if (valid && lane == __ffs(peers) - 1) wcnt[w * nb + dg] += (uint32_t)__popc(peers);
+        const uint32_t dg = (kr[s] >> shift) & mask;
+        const unsigned peers = digit_peers(dg, bits, __ballot_sync(0xFFFFFFFFu, valid));
+        const uint32_t before = valid ? wcnt[w * nb + dg] : 0u;
+        const uint32_t rank = before + (uint32_t)__popc(peers & lt);
+        if (s & 1) rk[s >> 1] |= rank << 16; else rk[s >> 1] = rank;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wcnt[w * nb + dg] = before + (uint32_t)__popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -391,18 +412,12 @@ __global__ void __launch_bounds__(RS_T) k_radix_scatter(const uint32_t *__restri
 #pragma unroll
     for (int s = 0; s < RS_ITEMS; ++s) {
         const int pos = w * (RS_ITEMS * 32) + s * 32 + lane;
-        const bool valid = pos < tile_n;
-        const uint32_t dg = valid ? (kr[s] >> shift) & mask : 0xFFFFFFFFu;
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
-        if (valid) {
-            const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-            const uint32_t lp = tstart[dg] + wcnt[w * nb + dg] + rank;
+        if (pos < tile_n) {
+            const uint32_t dg = (kr[s] >> shift) & mask;
+            const uint32_t lp = tstart[dg] + wcnt[w * nb + dg] + ((s & 1) ? (rk[s >> 1] >> 16) : (rk[s >> 1] & 0xFFFFu));
             skey[lp] = kr[s];
             sval[lp] = FIRST ? (uint32_t)(base + pos) : vin[base + pos];
         }
-        __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) wcnt[w * nb + dg] += (uint32_t)__popc(peers);
-        __syncwarp();
     }
     __syncthreads();
     for (int i = threadIdx.x; i < tile_n; i += RS_T) {
@@ -805,6 +820,240 @@ __global__ void __launch_bounds__(MOM_WARPS * 32) k_moments(const uint32_t *__re
     }
 }
 
+// ------------------------------------------------------------------ FP32 3-D moments, point-balanced
+// The same per-cell sums as k_moments<float, 3>, with the work of a column tile split evenly by
+// points instead of by cells: warp w takes the w-th eighth of the tile's sorted point range,
+// walks it cell by cell in chunks of at most 32 points of one cell, and keeps 49 + 8 FP32 sums
+// per lane (4 sub-groups x 8 roles, as in cell_moments_d3).  Every M3_FLUSH chunks and at the
+// end of its part of a cell it folds the sub-groups together and adds the sums to shared
+// memory: straight into the cell's slot when the warp owns the whole cell, else into one of its
+// two edge buffers (first / last cell, shared with the neighbouring warps).  The edge buffers
+// are added to the slots in warp order afterwards, so the result does not depend on timing.
+// Records of the next chunk are loaded before the current one is computed.
+constexpr int M3_WARPS = 8;
+constexpr int M3_PS = 36;     // staged floats per point: B1[7], y | B2[7], 0 | B3[7], 0 | w1[4] | w2[4] | w3[4]
+constexpr int M3_SLOT = 408;  // 343 moments + 64 y-moments + 1 pad
+constexpr int M3_FLUSH = 8;   // chunks between folds of the register sums
+constexpr int M3_NCT = 64;    // cells per tile
+
+static size_t moments3f_smem(int nct) {
+    return sizeof(float) * ((size_t)M3_WARPS * 32 * M3_PS + (size_t)nct * M3_SLOT + (size_t)M3_WARPS * 2 * M3_SLOT) +
+           sizeof(uint32_t) * (size_t)(nct + 1) + sizeof(int) * 2 * M3_WARPS;
+}
+
+__device__ __forceinline__ int m3_find_cell(const uint32_t *coff, int nct, uint32_t p) {
+    int lo = 0, hi = nct - 1;  // largest i with coff[i] <= p
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (coff[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__restrict__ perm, const Rec4<float> *__restrict__ rec,
+                                                              const uint32_t *__restrict__ offsets, ColTiling tl, ETab<float> E,
+                                                              float *__restrict__ outM, float *__restrict__ outY) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sg = lane >> 3, r = lane & 7;
+    const int64_t col = blockIdx.x / tl.ntile;
+    const int tile = (int)(blockIdx.x % tl.ntile);
+    const int js = tile * tl.NT;
+    const int je = min(js + tl.NT, tl.Ml);
+    const int cfirst = max(js - 3, 0);
+    const int cend = min(je, tl.C);
+    const int nct = cend - cfirst;
+    float *stage = reinterpret_cast<float *>(smraw);
+    float *slots = stage + M3_WARPS * 32 * M3_PS;
+    float *edge = slots + nct * M3_SLOT;
+    uint32_t *coff = reinterpret_cast<uint32_t *>(edge + M3_WARPS * 2 * M3_SLOT);
+    int *ecell = reinterpret_cast<int *>(coff + nct + 1);
+    const int64_t key0 = col * tl.C + cfirst;
+    for (int i = threadIdx.x; i <= nct; i += blockDim.x) coff[i] = offsets[key0 + i];
+    for (int i = threadIdx.x; i < nct * M3_SLOT + M3_WARPS * 2 * M3_SLOT; i += blockDim.x) slots[i] = 0.f;
+    __syncthreads();
+    const uint32_t P0 = coff[0], len = coff[nct] - P0;
+    const uint32_t ws = P0 + (uint32_t)(((uint64_t)len * warp) / M3_WARPS);
+    const uint32_t we = P0 + (uint32_t)(((uint64_t)len * (warp + 1)) / M3_WARPS);
+    int e0 = -1, e1 = -1;
+    if (ws < we) {
+        const int cw = m3_find_cell(coff, nct, ws);
+        const int cl = m3_find_cell(coff, nct, we - 1);
+        if (coff[cw] < ws || coff[cw + 1] > we) e0 = cw;
+        if (cl != cw && coff[cl + 1] > we) e1 = cl;
+    }
+    if (lane == 0) {
+        ecell[2 * warp] = e0;
+        ecell[2 * warp + 1] = e1;
+    }
+    float *pb = stage + warp * 32 * M3_PS;
+    float m[49], yacc[8];
+#pragma unroll
+    for (int i = 0; i < 49; ++i) m[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) yacc[i] = 0.f;
+    uint32_t p = ws;
+    int c = ws < we ? m3_find_cell(coff, nct, ws) : 0;
+    int nh = ws < we ? (int)min(32u, min(coff[c + 1], we) - p) : 0;
+    Rec4<float> my;
+    my.t[0] = my.t[1] = my.t[2] = my.y = 0.f;
+    if (lane < nh) my = rec[perm[p + lane]];
+    int nacc = 0;
+    while (p < we) {
+        // stage this chunk (one point per lane)
+        if (lane < nh) {
+            float b[7], w[4], q[M3_PS];
+            bern6<float>(my.t[0], b);
+#pragma unroll
+            for (int i = 0; i < 7; ++i) q[i] = b[i];
+            q[7] = my.y;
+            bern6<float>(my.t[1], b);
+#pragma unroll
+            for (int i = 0; i < 7; ++i) q[8 + i] = b[i];
+            q[15] = 0.f;
+            bern6<float>(my.t[2], b);
+#pragma unroll
+            for (int i = 0; i < 7; ++i) q[16 + i] = b[i];
+            q[23] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                keys_weights<float>(my.t[k], w);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) q[24 + 4 * k + i] = w[i];
+            }
+            float4 *dst = reinterpret_cast<float4 *>(pb + lane * M3_PS);
+#pragma unroll
+            for (int v = 0; v < M3_PS / 4; ++v) dst[v] = make_float4(q[4 * v], q[4 * v + 1], q[4 * v + 2], q[4 * v + 3]);
+        }
+        // next chunk: skip to the cell holding p + nh, prefetch its records
+        const uint32_t pn = p + (uint32_t)nh;
+        const bool cell_done = pn == coff[c + 1] || pn >= we;
+        int cn = c;
+        int nhn = 0;
+        if (pn < we) {
+            while (coff[cn + 1] <= pn) ++cn;
+            nhn = (int)min(32u, min(coff[cn + 1], we) - pn);
+            if (lane < nhn) my = rec[perm[pn + lane]];
+        }
+        __syncwarp();
+        for (int k = sg; k < nh; k += 4) {
+            const float *q = pb + k * M3_PS;
+            const float alpha = r < 7 ? q[r] : 0.f;
+            const float yv = q[7];
+            const float4 b2a = *reinterpret_cast<const float4 *>(q + 8), b2b = *reinterpret_cast<const float4 *>(q + 12);
+            const float4 b3a = *reinterpret_cast<const float4 *>(q + 16), b3b = *reinterpret_cast<const float4 *>(q + 20);
+            const float b2[7] = {b2a.x, b2a.y, b2a.z, b2a.w, b2b.x, b2b.y, b2b.z};
+            const float b3[7] = {b3a.x, b3a.y, b3a.z, b3a.w, b3b.x, b3b.y, b3b.z};
+#pragma unroll
+            for (int p2 = 0; p2 < 7; ++p2) {
+                const float ab = alpha * b2[p2];
+#pragma unroll
+                for (int p3 = 0; p3 < 7; ++p3) m[p2 * 7 + p3] = fmaf(ab, b3[p3], m[p2 * 7 + p3]);
+            }
+            const float ywa = yv * q[24 + (r >> 1)];
+            const float2 w2 = *reinterpret_cast<const float2 *>(q + 28 + 2 * (r & 1));
+            const float4 w3 = *reinterpret_cast<const float4 *>(q + 32);
+            const float q0 = ywa * w2.x, q1 = ywa * w2.y;
+            yacc[0] = fmaf(q0, w3.x, yacc[0]);
+            yacc[1] = fmaf(q0, w3.y, yacc[1]);
+            yacc[2] = fmaf(q0, w3.z, yacc[2]);
+            yacc[3] = fmaf(q0, w3.w, yacc[3]);
+            yacc[4] = fmaf(q1, w3.x, yacc[4]);
+            yacc[5] = fmaf(q1, w3.y, yacc[5]);
+            yacc[6] = fmaf(q1, w3.z, yacc[6]);
+            yacc[7] = fmaf(q1, w3.w, yacc[7]);
+        }
+        __syncwarp();
+        if (cell_done || ++nacc == M3_FLUSH) {
+#pragma unroll
+            for (int i = 0; i < 49; ++i) {
+                m[i] += __shfl_xor_sync(0xFFFFFFFFu, m[i], 8);
+                m[i] += __shfl_xor_sync(0xFFFFFFFFu, m[i], 16);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                yacc[i] += __shfl_xor_sync(0xFFFFFFFFu, yacc[i], 8);
+                yacc[i] += __shfl_xor_sync(0xFFFFFFFFu, yacc[i], 16);
+            }
+            if (sg == 0) {
+                float *dst = c == e0 ? edge + (warp * 2) * M3_SLOT
+                                     : (c == e1 ? edge + (warp * 2 + 1) * M3_SLOT : slots + c * M3_SLOT);
+                if (r < 7) {
+#pragma unroll
+                    for (int i = 0; i < 49; ++i) dst[r * 49 + i] += m[i];
+                }
+                const int a1 = r >> 1, a2 = 2 * (r & 1);
+#pragma unroll
+                for (int a3 = 0; a3 < 4; ++a3) {
+                    dst[343 + a1 * 16 + a2 * 4 + a3] += yacc[a3];
+                    dst[343 + a1 * 16 + (a2 + 1) * 4 + a3] += yacc[4 + a3];
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 49; ++i) m[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) yacc[i] = 0.f;
+            nacc = 0;
+        }
+        p = pn;
+        c = cn;
+        nh = nhn;
+    }
+    __syncthreads();
+    // edge partials into their cells, in warp order
+    for (int i = threadIdx.x; i < M3_SLOT; i += blockDim.x) {
+        for (int w = 0; w < M3_WARPS; ++w) {
+            const int a = ecell[2 * w], b = ecell[2 * w + 1];
+            if (a >= 0) slots[a * M3_SLOT + i] += edge[(w * 2) * M3_SLOT + i];
+            if (b >= 0) slots[b * M3_SLOT + i] += edge[(w * 2 + 1) * M3_SLOT + i];
+        }
+    }
+    __syncthreads();
+    // last-axis contraction (as in k_moments)
+    const int nj = je - js;
+    const int64_t S1 = tl.ncol * tl.Ml;
+    for (int it = threadIdx.x; it < 49 * nj; it += blockDim.x) {
+        const int jj = it % nj, pp = it / nj;
+        const int j = js + jj;
+        float acc[7];
+#pragma unroll
+        for (int dl = 0; dl < 7; ++dl) acc[dl] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int cc = j - a;
+            if (cc >= cfirst && cc < cend) {
+                const float *sl = slots + (cc - cfirst) * M3_SLOT + pp * 7;
+                float v[7];
+#pragma unroll
+                for (int q = 0; q < 7; ++q) v[q] = sl[q];
+#pragma unroll
+                for (int dl = 0; dl < 7; ++dl) {
+                    const int b = a + dl - 3;
+                    if (b >= 0 && b < 4) {
+#pragma unroll
+                        for (int q = 0; q < 7; ++q) acc[dl] = fmaf(E.e[a][dl][q], v[q], acc[dl]);
+                    }
+                }
+            }
+        }
+        const int64_t sp = col * tl.Ml + j;
+#pragma unroll
+        for (int dl = 0; dl < 7; ++dl) outM[(int64_t)(pp * 7 + dl) * S1 + sp] = acc[dl];
+    }
+    for (int it = threadIdx.x; it < 16 * nj; it += blockDim.x) {
+        const int jj = it % nj, yy = it / nj;
+        const int j = js + jj;
+        float acc = 0.f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int cc = j - a;
+            if (cc >= cfirst && cc < cend) acc += slots[(cc - cfirst) * M3_SLOT + 343 + yy * 4 + a];
+        }
+        outY[(int64_t)yy * S1 + col * tl.Ml + j] = acc;
+    }
+}
+
 // ------------------------------------------------------------------ probe moments
 // For a group of up to 16 probes: per cell Yz[t][a] = sum_i z_t(i) prod_k w_{a_k}(t_ik).
 // Lane = (h, t): t = lane & 15 (probe in group), h = lane >> 4 picks a1 in {2h, 2h+1}.
@@ -1057,10 +1306,18 @@ static int reduce_and_assemble(fkski_stats *st, const uint32_t *perm, const Rec4
         FK_TRY(sc.get(&t1, sizeof(T) * (size_t)(L::NM * S1)));
         FK_TRY(sc.get(&t1y, sizeof(T) * (size_t)((L::NY / 4) * S1)));
     }
-    const size_t smem = sizeof(T) * ((size_t)(L::PSTRIDE > 0 ? MOM_WARPS * 32 * L::PSTRIDE : 0) +
-                                     (size_t)tl.nct * L::SLOT);
-    FK_CUDA(cudaFuncSetAttribute(k_moments<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_moments<T, D><<<(unsigned)(tl.ncol * tl.ntile), MOM_WARPS * 32, smem, s>>>(perm, rec, offsets, tl, E, t1, t1y);
+    if constexpr (std::is_same<T, float>::value && D == 3) {
+        ColTiling t3;
+        make_tiling<T, D>(g, M3_NCT, t3);
+        const size_t smem = moments3f_smem(t3.nct);
+        FK_CUDA(cudaFuncSetAttribute(k_moments3f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_moments3f<<<(unsigned)(t3.ncol * t3.ntile), M3_WARPS * 32, smem, s>>>(perm, rec, offsets, t3, E, t1, t1y);
+    } else {
+        const size_t smem = sizeof(T) * ((size_t)(L::PSTRIDE > 0 ? MOM_WARPS * 32 * L::PSTRIDE : 0) +
+                                         (size_t)tl.nct * L::SLOT);
+        FK_CUDA(cudaFuncSetAttribute(k_moments<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_moments<T, D><<<(unsigned)(tl.ncol * tl.ntile), MOM_WARPS * 32, smem, s>>>(perm, rec, offsets, tl, E, t1, t1y);
+    }
     FK_LAUNCH();
     const int64_t M0 = g.M[0];
     if (D == 3) {

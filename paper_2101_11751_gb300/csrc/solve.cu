@@ -143,6 +143,158 @@ __global__ void __launch_bounds__(CG_T) k_band_spmv(const TB *__restrict__ band,
     }
 }
 
+// Vectorised form for an FP32 band and FP32 vectors (the MIXED iterations).  Each thread owns 4
+// consecutive nodes i0..i0+3: every diagonal is one aligned float4 of the band, streamed past L1
+// (each band value is used once per launch), and the 7 neighbours along the last axis of all 4
+// nodes are one 12-wide window of x, three aligned float4 per grid row (dz, dy) and rhs.  The
+// row loop is not unrolled: its 7 independent float4 band loads are in flight together.  Needs
+// m and M_{d-1} to be multiples of 4 so that every row start stays 16-byte aligned.
+struct RowOffs {
+    int base[49];  // offset of row (dz, dy) = (row / 7 - 3, row % 7 - 3); diagonal o = row * 7 + dx + 3
+};
+
+// Only the first `nwork` blocks (as many as are resident at once) do work; the others write
+// zero partials so that the partial-sum layout stays one entry per launched block.
+template <int RB>
+struct Spmv4Occ {
+    static constexpr int blocks = RB <= 1 ? 4 : (RB <= 2 ? 3 : 2);
+};
+
+template <int NROW, int RB>
+__global__ void __launch_bounds__(CG_T, Spmv4Occ<RB>::blocks) k_band_spmv4(const float *__restrict__ band, const float *__restrict__ x,
+                                                      float *__restrict__ u, int64_t m, int R, RowOffs rows,
+                                                      double *__restrict__ part, int NQ, const float *__restrict__ g,
+                                                      const int *__restrict__ gate, int Rtot, int r0, int nwork) {
+    if (gate && *gate) return;
+    __shared__ double sh[CG_T / 32];
+    if ((int)blockIdx.x >= nwork) {
+        if (part && threadIdx.x == 0)
+            for (int k = 0; k < R && k < RB; ++k)
+                for (int q = 0; q < NQ && q < 2; ++q) part[(int64_t)blockIdx.x * NQ * Rtot + (r0 + k) * NQ + q] = 0.0;
+        return;
+    }
+    float dq0[RB], dq1[RB];
+#pragma unroll
+    for (int k = 0; k < RB; ++k) dq0[k] = dq1[k] = 0.f;
+    const int64_t nquad = m >> 2;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nquad; t += (int64_t)nwork * blockDim.x) {
+        const int64_t i0 = t << 2;
+        float acc[RB][4];
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[k][q] = 0.f;
+#pragma unroll 1
+        for (int row = 0; row < NROW; ++row) {
+            float4 b[7];
+#pragma unroll
+            for (int e = 0; e < 7; ++e) b[e] = __ldcs(reinterpret_cast<const float4 *>(band + (int64_t)(row * 7 + e) * m + i0));
+            const int64_t w0 = i0 + rows.base[row] - 4;  // window x[w0 .. w0 + 11]
+            const bool inside = w0 >= 0 && w0 + 12 <= m;
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                if (k < R) {
+                    const float *xk = x + (int64_t)k * m;
+                    float v[12];
+                    if (inside) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float4 f = __ldg(reinterpret_cast<const float4 *>(xk + w0) + c);
+                            v[4 * c] = f.x;
+                            v[4 * c + 1] = f.y;
+                            v[4 * c + 2] = f.z;
+                            v[4 * c + 3] = f.w;
+                        }
+                    } else {
+                        // grid ends: off-grid neighbours have zero band entries; read nothing there
+#pragma unroll
+                        for (int j = 0; j < 12; ++j) v[j] = (w0 + j >= 0 && w0 + j < m) ? __ldg(xk + w0 + j) : 0.f;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 7; ++e) {
+                        acc[k][0] = fmaf(b[e].x, v[e + 1], acc[k][0]);
+                        acc[k][1] = fmaf(b[e].y, v[e + 2], acc[k][1]);
+                        acc[k][2] = fmaf(b[e].z, v[e + 3], acc[k][2]);
+                        acc[k][3] = fmaf(b[e].w, v[e + 4], acc[k][3]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+            if (k < R) {
+                *reinterpret_cast<float4 *>(u + (int64_t)k * m + i0) = make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+                if (part) {
+                    const float4 xv = __ldg(reinterpret_cast<const float4 *>(x + (int64_t)k * m + i0));
+                    dq0[k] = fmaf(acc[k][0], xv.x, dq0[k]);
+                    dq0[k] = fmaf(acc[k][1], xv.y, dq0[k]);
+                    dq0[k] = fmaf(acc[k][2], xv.z, dq0[k]);
+                    dq0[k] = fmaf(acc[k][3], xv.w, dq0[k]);
+                    if (g) {
+                        const float4 gv = __ldg(reinterpret_cast<const float4 *>(g + (int64_t)k * m + i0));
+                        dq1[k] = fmaf(xv.x, gv.x, dq1[k]);
+                        dq1[k] = fmaf(xv.y, gv.y, dq1[k]);
+                        dq1[k] = fmaf(xv.z, gv.z, dq1[k]);
+                        dq1[k] = fmaf(xv.w, gv.w, dq1[k]);
+                    }
+                }
+            }
+    }
+    if (!part) return;
+    for (int k = 0; k < R && k < RB; ++k) {
+        const double s0 = block_sum<float>(dq0[k], sh);
+        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ * Rtot + (r0 + k) * NQ + 0] = s0;
+        if (NQ > 1) {
+            const double s1 = block_sum<float>(dq1[k], sh);
+            if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ * Rtot + (r0 + k) * NQ + 1] = s1;
+        }
+    }
+}
+
+static int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 1;
+    }
+    return n;
+}
+
+static bool spmv4_ok(const fkski_grid &g, int64_t m, const void *band, const void *x, const void *u, const void *gv) {
+    if ((m & 3) != 0 || (g.M[g.d - 1] & 3) != 0) return false;
+    const uintptr_t a = (uintptr_t)band | (uintptr_t)x | (uintptr_t)u | (uintptr_t)gv;
+    return (a & 15) == 0;
+}
+
+static RowOffs make_rows(const fkski_grid &g) {
+    RowOffs ro;
+    memset(&ro, 0, sizeof(ro));
+    if (g.d == 3) {
+        for (int row = 0; row < 49; ++row)
+            ro.base[row] = (int)((row / 7 - 3) * g.M[1] * g.M[2] + (row % 7 - 3) * g.M[2]);
+    } else if (g.d == 2) {
+        for (int row = 0; row < 7; ++row) ro.base[row] = (int)((row - 3) * g.M[1]);
+    }
+    return ro;
+}
+
+template <int NROW>
+static void launch_spmv4_rows(const float *band, const float *x, float *u, int64_t m, int R, const RowOffs &ro,
+                              double *part, int NQ, const float *gv, const int *gate, int nblocks, int Rtot, int r0,
+                              cudaStream_t s) {
+#define FK_SPMV4(RBV) \
+    k_band_spmv4<NROW, RBV><<<nblocks, CG_T, 0, s>>>(band, x, u, m, R, ro, part, NQ, gv, gate, Rtot, r0, \
+                                                      std::min(nblocks, num_sms() * Spmv4Occ<RBV>::blocks))
+    if (R <= 1) FK_SPMV4(1);
+    else if (R <= 2) FK_SPMV4(2);
+    else if (R <= 4) FK_SPMV4(4);
+    else FK_SPMV4(8);
+#undef FK_SPMV4
+}
+
 static BandOffs make_offs(const fkski_grid &g) {
     BandOffs bo;
     memset(&bo, 0, sizeof(bo));
@@ -167,6 +319,24 @@ static int grid_blocks(int64_t work) { return (int)std::max<int64_t>(1, std::min
 template <typename TB, typename TX>
 static int launch_spmv(const TB *band, const fkski_grid &g, const TX *x, TX *u, int64_t m, int R, double *part, int NQ,
                        const TX *gv, const int *gate, int nblocks, cudaStream_t s) {
+    if constexpr (std::is_same<TB, float>::value && std::is_same<TX, float>::value) {
+        if (spmv4_ok(g, m, band, x, u, gv)) {
+            const RowOffs ro = make_rows(g);
+            // rhs in even groups of at most 8: the band is read once per group
+            const int ng = (int)cdiv(R, 8), per = (int)cdiv(R, ng);
+            for (int r0 = 0; r0 < R; r0 += per) {
+                const int Rb = std::min(per, R - r0);
+                const float *xb = x + (int64_t)r0 * m;
+                float *ub = u + (int64_t)r0 * m;
+                const float *gb = gv ? gv + (int64_t)r0 * m : nullptr;
+                if (g.d == 3) launch_spmv4_rows<49>(band, xb, ub, m, Rb, ro, part, NQ, gb, gate, nblocks, R, r0, s);
+                else if (g.d == 2) launch_spmv4_rows<7>(band, xb, ub, m, Rb, ro, part, NQ, gb, gate, nblocks, R, r0, s);
+                else launch_spmv4_rows<1>(band, xb, ub, m, Rb, ro, part, NQ, gb, gate, nblocks, R, r0, s);
+                FK_LAUNCH();
+            }
+            return FKSKI_OK;
+        }
+    }
     const BandOffs bo = make_offs(g);
     const int nb = (int)ipow(7, g.d);
     for (int r0 = 0; r0 < R; r0 += 32) {
@@ -793,9 +963,23 @@ constexpr int BCG_STEPS = 8;
 // rebase[r] = 1 splits b_r = W b_hat + b' (x0 = 0, the Lanczos start for SLQ), rebase[r] = 0 uses
 // Alg. 5's start x0 = b / sigma^2 for that rhs.  On return V.x holds x_hat (FP64); the scalars and
 // coefficient histories stay in the workspace.
+// One factorized-CG solve split in phases, so that several independent problems can run their
+// iteration chunks from one graph launch: prepare (set-up launches on the caller's stream and
+// capture of the chunk graphs), the chunk loop, and collect (results to the host).
+struct FcgGraphs {
+    cudaGraph_t body = nullptr, rep = nullptr;
+    long long nbody = 0, nrep = 0;
+    int check = 1;
+    void release() {
+        if (body) cudaGraphDestroy(body);
+        if (rep) cudaGraphDestroy(rep);
+        body = rep = nullptr;
+    }
+};
+
 template <typename T, bool GEN>
-static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, const int *rebase,
-                     CgVecs<T> &V, int *iters_host, double *res_host, int *status_out, cudaStream_t s) {
+static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, const int *rebase,
+                       CgVecs<T> &V, FcgGraphs &G, cudaStream_t s) {
     SolveWork *w;
     FK_TRY(work_get(st, &w));
     const int dt = sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64;
@@ -914,14 +1098,16 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     FK_LAUNCH();
     FK_TRY(kgop_reserve(kg, R));
     FK_TRY(kgop_reserve(kg64, R));
+    FK_TRY(kgop_tune(kg, R, s));
+    if (hc.replace && kg64 != kg) FK_TRY(kgop_tune(kg64, R, s));
     // capture the iteration chunk, and (MIXED) the residual-replacement pass
     const int check = std::max(1, o->check_every);
     const cudaStream_t cs = w->ws;
     cudaGraph_t gbody = nullptr, grep = nullptr;
-    cudaGraphExec_t ebody = nullptr, erep = nullptr;
     const long long launches_before_capture = fkski_kernel_launches();
     FK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     int rc = FKSKI_OK;
+    kgop_set_gate(kg, gate_done);  // finished solves skip their K_G passes too
     for (int it = 0; it < check && rc == FKSKI_OK; ++it) {
         k_cg_xr<T, GEN><<<gv, CG_T, 0, cs>>>(m, R, V.x, V.r, V.p, V.z, V.kg, w->S, w->state, w->ctl);
         rc = launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, gate_done, gb, cs);
@@ -933,10 +1119,12 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
         k_cg_fin_delta<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->want, w->iters, ha, w->ctl, 0);
     }
     cudaError_t ce = cudaStreamEndCapture(cs, &gbody);
+    kgop_set_gate(kg, nullptr);
     if (rc != FKSKI_OK) return rc;
     FK_CUDA(ce);
     if (hc.replace) {
         FK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+        kgop_set_gate(kg64, gate_conf);
         // true residual in FP64: w64 = K (W^T W x_hat) + sigma^2 x_hat; gamma from it
         rc = launch_spmv<T, double>(band, st->grid, V.x, V.t64, m, R, nullptr, 1, nullptr, gate_conf, gb, cs);
         if (rc == FKSKI_OK) rc = kgop_apply_dev(kg64, V.t64, V.w64, R, V.x, sig2_dev, cs);
@@ -947,20 +1135,24 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
         if (rc == FKSKI_OK)
             k_cg_fin_replace<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->want, w->iters, ha, w->ctl);
         ce = cudaStreamEndCapture(cs, &grep);
+        kgop_set_gate(kg64, nullptr);
         if (rc != FKSKI_OK) { cudaGraphDestroy(gbody); return rc; }
         FK_CUDA(ce);
     }
     // captured launches are replays, counted when the graphs run
     count_launches(launches_before_capture - fkski_kernel_launches());
-    FK_CUDA(cudaGraphInstantiate(&ebody, gbody, 0));
-    if (grep) FK_CUDA(cudaGraphInstantiate(&erep, grep, 0));
-    rc = run_graph_loop(ebody, erep, w, o->maxiter, check, s, (long long)graph_kernel_nodes(gbody),
-                        (long long)graph_kernel_nodes(grep));
-    cudaGraphExecDestroy(ebody);
-    cudaGraphDestroy(gbody);
-    if (erep) cudaGraphExecDestroy(erep);
-    if (grep) cudaGraphDestroy(grep);
-    if (rc) return rc;
+    G.body = gbody;
+    G.rep = grep;
+    G.nbody = (long long)graph_kernel_nodes(gbody);
+    G.nrep = (long long)graph_kernel_nodes(grep);
+    G.check = check;
+    return FKSKI_OK;
+}
+
+// Iterations, residuals and status of a finished solve (synchronizes s).
+template <typename T>
+static int fcg_collect(fkski_stats *st, int R, int *iters_host, double *res_host, int *status_out, cudaStream_t s) {
+    SolveWork *w = st->work;
     CgCtl hc2;
     std::vector<double> hS2((size_t)NF * R);
     FK_CUDA(cudaMemcpyAsync(&hc2, w->ctl, sizeof(hc2), cudaMemcpyDeviceToHost, s));
@@ -975,6 +1167,23 @@ static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     if (hc2.status & ST_BREAKDOWN) status = FKSKI_E_BREAKDOWN;
     *status_out = status;
     return FKSKI_OK;
+}
+
+template <typename T, bool GEN>
+static int fcg_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, const int *rebase,
+                     CgVecs<T> &V, int *iters_host, double *res_host, int *status_out, cudaStream_t s) {
+    FcgGraphs G;
+    FK_TRY((fcg_prepare<T, GEN>(st, kern, o, R, rebase, V, G, s)));
+    cudaGraphExec_t ebody = nullptr, erep = nullptr;
+    cudaError_t ce = cudaGraphInstantiate(&ebody, G.body, 0);
+    if (ce == cudaSuccess && G.rep) ce = cudaGraphInstantiate(&erep, G.rep, 0);
+    int rc = ce == cudaSuccess ? FKSKI_OK : note_cuda_error(ce, __FILE__, __LINE__);
+    if (rc == FKSKI_OK) rc = run_graph_loop(ebody, erep, st->work, o->maxiter, G.check, s, G.nbody, G.nrep);
+    if (ebody) cudaGraphExecDestroy(ebody);
+    if (erep) cudaGraphExecDestroy(erep);
+    G.release();
+    if (rc) return rc;
+    return fcg_collect<T>(st, R, iters_host, res_host, status_out, s);
 }
 
 // W^T x for each rhs in FP64: x = c0 b + W x_hat + c^x b'  ->  c0 W^T b + W^T W x_hat + c^x g
@@ -1001,6 +1210,22 @@ static int fcg_wtx64(fkski_stats *st, CgVecs<T> &V, int R, double *out64, cudaSt
     return FKSKI_OK;
 }
 
+// a = W^T z (FP64 -> T) and v = K_G a (FP64 product -> T) of a finished single-rhs solve.
+template <typename T>
+static int mean_outputs(fkski_stats *st, CgVecs<T> &V, T *a_out, T *v_out, cudaStream_t s) {
+    SolveWork *w = st->work;
+    const int64_t m = st->m;
+    FK_TRY(fcg_wtx64<T>(st, V, 1, V.w64, s));
+    KgOp *kg64 = w->kg[1];
+    FK_TRY(kgop_apply(kg64, V.w64, V.r0, 1, nullptr, 0.0, s));
+    const unsigned gv = (unsigned)std::min<int64_t>(cdiv(m, 256), 152 * 8);
+    k_convert_t<double, T><<<gv, 256, 0, s>>>(V.w64, a_out, m, 1.0);
+    FK_LAUNCH();
+    k_convert_t<double, T><<<gv, 256, 0, s>>>(V.r0, v_out, m, 1.0);
+    FK_LAUNCH();
+    return FKSKI_OK;
+}
+
 template <typename T>
 static int solve_mean(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, bool gen, T *a_out, T *v_out,
                       fkski_info *info, cudaStream_t s) {
@@ -1010,17 +1235,7 @@ static int solve_mean(fkski_stats *st, const fkski_kernel *kern, const fkski_opt
     const int rebase = 1;
     if (gen) FK_TRY((fcg_solve<T, true>(st, kern, o, 1, &rebase, V, &it, &res, &status, s)));
     else FK_TRY((fcg_solve<T, false>(st, kern, o, 1, nullptr, V, &it, &res, &status, s)));
-    SolveWork *w = st->work;
-    const int64_t m = st->m;
-    // a = W^T z (FP64) -> w64; v = K_G a (FP64) -> r0 slot
-    FK_TRY(fcg_wtx64<T>(st, V, 1, V.w64, s));
-    KgOp *kg64 = w->kg[1];
-    FK_TRY(kgop_apply(kg64, V.w64, V.r0, 1, nullptr, 0.0, s));
-    const unsigned gv = (unsigned)std::min<int64_t>(cdiv(m, 256), 152 * 8);
-    k_convert_t<double, T><<<gv, 256, 0, s>>>(V.w64, a_out, m, 1.0);
-    FK_LAUNCH();
-    k_convert_t<double, T><<<gv, 256, 0, s>>>(V.r0, v_out, m, 1.0);
-    FK_LAUNCH();
+    FK_TRY(mean_outputs<T>(st, V, a_out, v_out, s));
     FK_CUDA(cudaStreamSynchronize(s));
     if (info) {
         info->iters = it;
@@ -1044,6 +1259,160 @@ int solve_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts
     if (o.precision == FKSKI_DOUBLE)
         return solve_mean<double>(st, kern, &o, gen, (double *)a_out, (double *)v_out, info, s);
     return solve_mean<float>(st, kern, &o, gen, (float *)a_out, (float *)v_out, info, s);
+}
+
+// ------------------------------------------------------------------ batch of independent problems
+// Every problem is prepared as for fkski_solve (set-up launches, captured chunk graphs), then one
+// parent graph holds all chunk graphs as independent child nodes (the GPU runs them
+// concurrently) followed by one small kernel that gathers every problem's flags; each replay
+// advances every unfinished problem by check_every iterations and costs one flag read.
+__global__ void k_gather_flags(CgCtl *const *__restrict__ ctls, int P, int *__restrict__ flags) {
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        flags[2 * p] = ctls[p]->all_conf;
+        flags[2 * p + 1] = ctls[p]->any_rep;
+    }
+}
+
+static int parent_graph(const std::vector<cudaGraph_t> &kids, CgCtl **dctls, int P, int *dflags, cudaGraphExec_t *exec) {
+    cudaGraph_t g = nullptr;
+    FK_CUDA(cudaGraphCreate(&g, 0));
+    std::vector<cudaGraphNode_t> nodes;
+    int rc = FKSKI_OK;
+    for (cudaGraph_t k : kids) {
+        if (!k) continue;
+        cudaGraphNode_t nd;
+        const cudaError_t e = cudaGraphAddChildGraphNode(&nd, g, nullptr, 0, k);
+        if (e != cudaSuccess) { rc = note_cuda_error(e, __FILE__, __LINE__); break; }
+        nodes.push_back(nd);
+    }
+    if (rc == FKSKI_OK) {
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        void *args[] = {(void *)&dctls, (void *)&P, (void *)&dflags};
+        kp.func = (void *)k_gather_flags;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(128);
+        kp.kernelParams = args;
+        cudaGraphNode_t nd;
+        cudaError_t e = cudaGraphAddKernelNode(&nd, g, nodes.data(), nodes.size(), &kp);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+        if (e != cudaSuccess) rc = note_cuda_error(e, __FILE__, __LINE__);
+    }
+    cudaGraphDestroy(g);
+    return rc;
+}
+
+template <typename T>
+static int solve_batched_typed(int P, fkski_stats *const *sts, const fkski_kernel *kernels, const fkski_opts *o,
+                               void *const *a_out, void *const *v_out, fkski_info *info, cudaStream_t s) {
+    const bool gen = o->x0_mode == FKSKI_X0_ZERO;
+    std::vector<CgVecs<T>> V(P);
+    std::vector<FcgGraphs> G(P);
+    const int rebase = 1;
+    int rc = FKSKI_OK;
+    for (int p = 0; p < P && rc == FKSKI_OK; ++p)
+        rc = gen ? fcg_prepare<T, true>(sts[p], &kernels[p], o, 1, &rebase, V[p], G[p], s)
+                 : fcg_prepare<T, false>(sts[p], &kernels[p], o, 1, nullptr, V[p], G[p], s);
+    CgCtl **dctls = nullptr;
+    int *dflags = nullptr, *hflags = nullptr;
+    cudaGraphExec_t eb = nullptr, er = nullptr;
+    long long nb = 1, nr = 1;
+    std::vector<cudaGraph_t> kb, kr;
+    for (int p = 0; p < P; ++p) {
+        kb.push_back(G[p].body);
+        kr.push_back(G[p].rep);
+        nb += G[p].nbody;
+        nr += G[p].nrep;
+    }
+    const bool any_rep_graph = std::any_of(kr.begin(), kr.end(), [](cudaGraph_t g) { return g != nullptr; });
+    if (rc == FKSKI_OK) {
+        std::vector<CgCtl *> hctls(P);
+        for (int p = 0; p < P; ++p) hctls[p] = sts[p]->work->ctl;
+        cudaError_t e = cudaMallocAsync((void **)&dctls, sizeof(CgCtl *) * P, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&dflags, sizeof(int) * 2 * P, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dctls, hctls.data(), sizeof(CgCtl *) * P, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&hflags, sizeof(int) * 2 * P);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // hctls is a host temporary
+        if (e != cudaSuccess) rc = note_cuda_error(e, __FILE__, __LINE__);
+    }
+    if (rc == FKSKI_OK) rc = parent_graph(kb, dctls, P, dflags, &eb);
+    if (rc == FKSKI_OK && any_rep_graph) rc = parent_graph(kr, dctls, P, dflags, &er);
+    for (auto &g : G) g.release();
+    if (rc == FKSKI_OK) {
+        SolveWork *w0 = sts[0]->work;
+        const cudaStream_t ws = w0->ws;
+        const int check = G[0].check;
+        cudaError_t e = cudaEventRecord(w0->ev, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ws, w0->ev, 0);
+        int launched = 0;
+        while (e == cudaSuccess && launched <= o->maxiter + check) {
+            e = cudaGraphLaunch(eb, ws);
+            count_launches(nb);
+            launched += check;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, dflags, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, ws);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ws);
+            if (e != cudaSuccess) break;
+            bool all = true, rep = false;
+            for (int p = 0; p < P; ++p) {
+                all = all && hflags[2 * p];
+                rep = rep || hflags[2 * p + 1];
+            }
+            if (all) break;
+            if (er && rep) {
+                e = cudaGraphLaunch(er, ws);
+                count_launches(nr);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, dflags, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, ws);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(ws);
+                if (e != cudaSuccess) break;
+                all = true;
+                for (int p = 0; p < P; ++p) all = all && hflags[2 * p];
+                if (all) break;
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(w0->ev, ws);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, w0->ev, 0);
+        if (e != cudaSuccess) rc = note_cuda_error(e, __FILE__, __LINE__);
+    }
+    if (eb) cudaGraphExecDestroy(eb);
+    if (er) cudaGraphExecDestroy(er);
+    int worst = FKSKI_OK;
+    for (int p = 0; p < P && rc == FKSKI_OK; ++p) {
+        int it = 0, status = FKSKI_OK;
+        double res = 0.0;
+        rc = fcg_collect<T>(sts[p], 1, &it, &res, &status, s);
+        if (rc == FKSKI_OK) rc = mean_outputs<T>(sts[p], V[p], (T *)a_out[p], (T *)v_out[p], s);
+        if (info) {
+            info[p].iters = it;
+            info[p].iters_rhs[0] = it;
+            info[p].rel_residual = res;
+            info[p].status = status;
+        }
+        if (status == FKSKI_E_BREAKDOWN || (status != FKSKI_OK && worst == FKSKI_OK)) worst = status;
+    }
+    if (dctls) cudaFreeAsync(dctls, s);
+    if (dflags) cudaFreeAsync(dflags, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (hflags) cudaFreeHost(hflags);
+    if (rc == FKSKI_OK && e != cudaSuccess) rc = note_cuda_error(e, __FILE__, __LINE__);
+    return rc != FKSKI_OK ? rc : worst;
+}
+
+int solve_batched_impl(int P, fkski_stats *const *sts, const fkski_kernel *kernels, const fkski_opts *opts,
+                       void *const *a_out, void *const *v_out, fkski_info *info, cudaStream_t s) {
+    if (P < 1 || !sts || !kernels || !a_out || !v_out) return FKSKI_E_INVALID_ARG;
+    fkski_opts o;
+    if (opts) o = *opts; else fkski_default_opts(&o);
+    if (o.maxiter < 1 || !(o.rtol >= 0.0)) return FKSKI_E_INVALID_ARG;
+    if (o.x0_mode != FKSKI_X0_ZERO && o.x0_mode != FKSKI_X0_Y_OVER_S2) return FKSKI_E_INVALID_ARG;
+    for (int p = 0; p < P; ++p) {
+        if (!sts[p] || !a_out[p] || !v_out[p]) return FKSKI_E_INVALID_ARG;
+        if (!(kernels[p].noise_var > 0.0) || !std::isfinite(kernels[p].noise_var)) return FKSKI_E_INVALID_ARG;
+        for (int q = 0; q < p; ++q)
+            if (sts[q] == sts[p]) return FKSKI_E_INVALID_ARG;  // one workspace per statistics object
+    }
+    if (info) memset(info, 0, sizeof(fkski_info) * P);
+    if (o.precision == FKSKI_DOUBLE) return solve_batched_typed<double>(P, sts, kernels, &o, a_out, v_out, info, s);
+    return solve_batched_typed<float>(P, sts, kernels, &o, a_out, v_out, info, s);
 }
 
 int band_mvm_impl(const fkski_stats *stc, const void *x, void *u, int nrhs, int dtype, cudaStream_t s) {
@@ -1113,59 +1482,90 @@ int grad_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, i
 // ------------------------------------------------------------------ predict
 // mu(x*) = sum over the 4^d stencil nodes of w(x*) v  (Def. 1 / Fact 2 mean)
 template <typename TX, typename TV, int D>
+__device__ __forceinline__ TV predict_point(const TX *__restrict__ Xs, int64_t ns, int64_t i, const KeyParams &kp,
+                                            const TV *__restrict__ v, int64_t s1, int64_t s2, int &bad) {
+    int c[3] = {1, 1, 1};
+    TX t[3] = {TX(0), TX(0), TX(0)};
+    int st = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) st |= axis_cell<TX>(Xs[(int64_t)k * ns + i], kp, k, c[k], t[k]);
+    if (st) {
+        bad |= (st & 2) ? ST_NONFINITE : ST_OUT_OF_GRID;
+        return TV(0);
+    }
+    TV w[3][4];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        TX wx[4];
+        keys_weights<TX>(t[k], wx);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) w[k][a] = (TV)wx[a];
+    }
+    TV acc = TV(0);
+    if (D == 1) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc = fma(w[0][a], v[c[0] - 1 + a], acc);
+    } else if (D == 2) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            TV rowacc = TV(0);
+            const int64_t base = (int64_t)(c[0] - 1 + a) * s1 + (c[1] - 1);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) rowacc = fma(w[1][b], v[base + b], rowacc);
+            acc = fma(w[0][a], rowacc, acc);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            TV pl = TV(0);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int64_t base = (int64_t)(c[0] - 1 + a) * s1 + (int64_t)(c[1] - 1 + b) * s2 + (c[2] - 1);
+                TV rowacc = TV(0);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) rowacc = fma(w[2][e], v[base + e], rowacc);
+                pl = fma(w[1][b], rowacc, pl);
+            }
+            acc = fma(w[0][a], pl, acc);
+        }
+    }
+    return acc;
+}
+
+template <typename TX, typename TV, int D>
 __global__ void k_predict(const TX *__restrict__ Xs, int64_t ns, KeyParams kp, const TV *__restrict__ v,
                           TV *__restrict__ mu, int *__restrict__ status, int64_t s1, int64_t s2) {
     int bad = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
-        int c[3] = {1, 1, 1};
-        TX t[3] = {TX(0), TX(0), TX(0)};
-        int st = 0;
-#pragma unroll
-        for (int k = 0; k < D; ++k) st |= axis_cell<TX>(Xs[(int64_t)k * ns + i], kp, k, c[k], t[k]);
-        if (st) {
-            bad |= (st & 2) ? ST_NONFINITE : ST_OUT_OF_GRID;
-            mu[i] = TV(0);
-            continue;
-        }
-        TV w[3][4];
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            TX wx[4];
-            keys_weights<TX>(t[k], wx);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) w[k][a] = (TV)wx[a];
-        }
-        TV acc = TV(0);
-        if (D == 1) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) acc = fma(w[0][a], v[c[0] - 1 + a], acc);
-        } else if (D == 2) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                TV rowacc = TV(0);
-                const int64_t base = (int64_t)(c[0] - 1 + a) * s1 + (c[1] - 1);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) rowacc = fma(w[1][b], v[base + b], rowacc);
-                acc = fma(w[0][a], rowacc, acc);
-            }
-        } else {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                TV pl = TV(0);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int64_t base = (int64_t)(c[0] - 1 + a) * s1 + (int64_t)(c[1] - 1 + b) * s2 + (c[2] - 1);
-                    TV rowacc = TV(0);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) rowacc = fma(w[2][e], v[base + e], rowacc);
-                    pl = fma(w[1][b], rowacc, pl);
-                }
-                acc = fma(w[0][a], pl, acc);
-            }
-        }
-        mu[i] = acc;
-    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x)
+        mu[i] = predict_point<TX, TV, D>(Xs, ns, i, kp, v, s1, s2, bad);
     if (bad) atomicOr(status, bad);
+}
+
+// Batch of independent problems with the same d: one launch over the concatenated test points;
+// a thread finds its problem by binary search over the jobs' first indices.
+template <typename TX, typename TV>
+struct PredJob {
+    KeyParams kp;
+    const TX *Xs;
+    const TV *v;
+    TV *mu;
+    int64_t ns, s1, s2, first;
+};
+
+template <typename TX, typename TV, int D>
+__global__ void k_predict_batched(const PredJob<TX, TV> *__restrict__ jobs, int nj, int64_t total, int *__restrict__ status) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nj - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].first <= g) lo = mid; else hi = mid - 1;
+        }
+        const PredJob<TX, TV> &J = jobs[lo];
+        int bad = 0;
+        const int64_t i = g - J.first;
+        J.mu[i] = predict_point<TX, TV, D>(J.Xs, J.ns, i, J.kp, J.v, J.s1, J.s2, bad);
+        if (bad) atomicOr(&status[lo], bad);
+    }
 }
 
 template <typename TX, typename TV>
@@ -1203,6 +1603,82 @@ int predict_impl(const fkski_stats *st, const void *v, int vdtype, const void *X
     return FKSKI_E_INVALID_ARG;
 }
 
+
+template <typename TX, typename TV>
+static int predict_batched_typed(int P, const fkski_stats *const *st, const void *const *v, const void *const *Xs,
+                                 const int64_t *ns, void *const *mu, int *status_out, cudaStream_t s) {
+    std::vector<PredJob<TX, TV>> jobs[3];
+    std::vector<int> owner[3];
+    int64_t total[3] = {0, 0, 0};
+    for (int p = 0; p < P; ++p) {
+        if (ns[p] == 0) continue;
+        const int d = st[p]->d;
+        PredJob<TX, TV> J;
+        memset(&J, 0, sizeof(J));
+        J.kp = make_key_params(st[p]->grid);
+        J.Xs = (const TX *)Xs[p];
+        J.v = (const TV *)v[p];
+        J.mu = (TV *)mu[p];
+        J.ns = ns[p];
+        const int64_t M1 = st[p]->grid.M[1], M2 = st[p]->grid.M[2];
+        J.s1 = d == 2 ? M1 : M1 * M2;
+        J.s2 = M2;
+        J.first = total[d - 1];
+        total[d - 1] += ns[p];
+        jobs[d - 1].push_back(J);
+        owner[d - 1].push_back(p);
+    }
+    size_t jb = 0;
+    for (int k = 0; k < 3; ++k) jb += jobs[k].size();
+    PredJob<TX, TV> *dj = nullptr;
+    int *dst = nullptr;
+    FK_CUDA(cudaMallocAsync((void **)&dj, sizeof(PredJob<TX, TV>) * std::max<size_t>(jb, 1), s));
+    FK_CUDA(cudaMallocAsync((void **)&dst, sizeof(int) * std::max<size_t>(jb, 1), s));
+    FK_CUDA(cudaMemsetAsync(dst, 0, sizeof(int) * std::max<size_t>(jb, 1), s));
+    std::vector<PredJob<TX, TV>> all;
+    for (int k = 0; k < 3; ++k) all.insert(all.end(), jobs[k].begin(), jobs[k].end());
+    if (jb) FK_CUDA(cudaMemcpyAsync(dj, all.data(), sizeof(PredJob<TX, TV>) * jb, cudaMemcpyHostToDevice, s));
+    size_t off = 0;
+    for (int k = 0; k < 3; ++k) {
+        const int nj = (int)jobs[k].size();
+        if (nj == 0) continue;
+        const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total[k], 256), 152 * 16));
+        if (k == 0) k_predict_batched<TX, TV, 1><<<gb, 256, 0, s>>>(dj + off, nj, total[k], dst + off);
+        else if (k == 1) k_predict_batched<TX, TV, 2><<<gb, 256, 0, s>>>(dj + off, nj, total[k], dst + off);
+        else k_predict_batched<TX, TV, 3><<<gb, 256, 0, s>>>(dj + off, nj, total[k], dst + off);
+        FK_LAUNCH();
+        off += nj;
+    }
+    std::vector<int> h(std::max<size_t>(jb, 1), 0);
+    FK_CUDA(cudaMemcpyAsync(h.data(), dst, sizeof(int) * std::max<size_t>(jb, 1), cudaMemcpyDeviceToHost, s));
+    FK_CUDA(cudaFreeAsync(dj, s));
+    FK_CUDA(cudaFreeAsync(dst, s));
+    FK_CUDA(cudaStreamSynchronize(s));
+    int worst = FKSKI_OK;
+    off = 0;
+    for (int p = 0; p < P; ++p) status_out[p] = FKSKI_OK;
+    for (int k = 0; k < 3; ++k)
+        for (size_t j = 0; j < jobs[k].size(); ++j, ++off) {
+            const int rc = status_from_bits(h[off]);
+            status_out[owner[k][j]] = rc;
+            if (rc != FKSKI_OK && worst == FKSKI_OK) worst = rc;
+        }
+    return worst;
+}
+
+int predict_batched_impl(int P, const fkski_stats *const *st, const void *const *v, int vdtype, const void *const *Xs,
+                         int xdtype, const int64_t *ns, void *const *mu, int *status, cudaStream_t s) {
+    if (P < 1 || !st || !v || !Xs || !ns || !mu) return FKSKI_E_INVALID_ARG;
+    for (int p = 0; p < P; ++p)
+        if (!st[p] || ns[p] < 0 || (ns[p] > 0 && (!v[p] || !Xs[p] || !mu[p]))) return FKSKI_E_INVALID_ARG;
+    std::vector<int> tmp(P);
+    int *so = status ? status : tmp.data();
+    if (vdtype == FKSKI_F32 && xdtype == FKSKI_F32) return predict_batched_typed<float, float>(P, st, v, Xs, ns, mu, so, s);
+    if (vdtype == FKSKI_F64 && xdtype == FKSKI_F32) return predict_batched_typed<float, double>(P, st, v, Xs, ns, mu, so, s);
+    if (vdtype == FKSKI_F32 && xdtype == FKSKI_F64) return predict_batched_typed<double, float>(P, st, v, Xs, ns, mu, so, s);
+    if (vdtype == FKSKI_F64 && xdtype == FKSKI_F64) return predict_batched_typed<double, double>(P, st, v, Xs, ns, mu, so, s);
+    return FKSKI_E_INVALID_ARG;
+}
 }  // namespace fk
 
 namespace fk {
