@@ -346,6 +346,27 @@ def nspace_mean(grid, kernel, X, y, rtol: float, x0_mode: int = 0, maxiter: int 
     return a, kg_matvec(grid, kernel, a), it, z
 
 
+def nspace_cov(grid, kernel, X, Xs, rtol: float, maxiter: int = 10000):
+    """SKI posterior covariance at test points Xs (Def. 1 / Theorem 1) by n-space CG (Alg. 1),
+    one solve per test point from x0 = 0:
+        cov[:, j] = W_s K w_j - W_s K W^T A^{-1} (W K w_j),  A = W K W^T + sigma^2 I,
+    each solve stopped at ||r|| <= rtol ||W K w_j||.  Returns (cov, max iterations)."""
+    W = w_csr(grid, X)
+    Ws = w_csr(grid, Xs)
+    mv = ski_operator(grid, kernel, W)
+    ns = Ws.shape[0]
+    cov = np.zeros((ns, ns))
+    itmax = 0
+    for j in range(ns):
+        kw = kg_matvec(grid, kernel, Ws[j].toarray().ravel())
+        b = W @ kw
+        z, it, _, _ = cg(mv, b, None, (rtol ** 2) * float(b @ b), maxiter)
+        itmax = max(itmax, it)
+        c = kw - kg_matvec(grid, kernel, W.T @ z)
+        cov[:, j] = Ws @ c
+    return cov, itmax
+
+
 def dense_system(grid, kernel, X):
     W = w_csr(grid, X).toarray()
     K = kg_dense(grid, kernel)

@@ -275,6 +275,24 @@ def test_theorem1_ski_equals_gsgp(oracle_mod, d, ktype):
     assert a["logdet"] == pytest.approx(b["logdetB"] + (n - m) * math.log(kern.noise_var), rel=1e-10)
 
 
+@pytest.mark.parametrize("d", [1, 2])
+def test_nspace_cov_matches_dense(oracle_mod, d):
+    """The CG covariance oracle equals the dense Def. 1 covariance (pinned to Fact 2 by Theorem 1
+    above) at a tight tolerance, is symmetric, and has a non-negative diagonal no larger than the
+    prior variance w^T K w."""
+    from oracle import core
+    grid, X, y = _tiny(d, n=80, seed=9)
+    kern = synth.Kernel(synth.RBF, (0.3, 0.25)[:d], 1.1, 0.04)
+    Xs = np.random.default_rng(10).uniform(0, 1, size=(d, 9))
+    cov, _ = core.nspace_cov(grid, kern, X, Xs, rtol=1e-13)
+    ref = core.ski_inference_dense(grid, kern, X, y, Xs)["cov"]
+    np.testing.assert_allclose(cov, ref, rtol=1e-7, atol=1e-9 * np.abs(ref).max())
+    np.testing.assert_allclose(cov, cov.T, rtol=1e-7, atol=1e-9 * np.abs(ref).max())
+    Ws = core.w_csr(grid, Xs).toarray()
+    prior = np.einsum("ij,ij->i", Ws, (core.kg_dense(grid, kern) @ Ws.T).T)
+    assert np.all(np.diag(cov) >= -1e-12) and np.all(np.diag(cov) <= prior + 1e-12)
+
+
 def test_nspace_cg_mean_matches_dense(oracle_mod):
     from oracle import core
     grid, X, y = _tiny(2, n=150, seed=9)
