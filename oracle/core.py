@@ -367,6 +367,54 @@ def nspace_cov(grid, kernel, X, Xs, rtol: float, maxiter: int = 10000):
     return cov, itmax
 
 
+def lanczos(mv, b: np.ndarray, k: int, breakdown: float = 1e-10):
+    """Lanczos tridiagonalisation with full reorthogonalisation (Alg. 6, with its garbled
+    updates read as q_{i+1} - alpha_i q_i and T_{i+1,i} = T_{i,i+1}), started at b / ||b||.
+    Stops early when beta_{i+1} <= breakdown * ||A q_i|| (invariant Krylov space).
+    Returns Q (n x k') and T (k' x k')."""
+    n = len(b)
+    Q = np.zeros((n, k))
+    T = np.zeros((k, k))
+    q = b / np.linalg.norm(b)
+    q_prev = np.zeros(n)
+    beta = 0.0
+    kk = k
+    for i in range(k):
+        Q[:, i] = q
+        w = mv(q)
+        aq = np.linalg.norm(w)
+        w = w - beta * q_prev
+        alpha = float(q @ w)
+        T[i, i] = alpha
+        if i == k - 1:
+            break
+        w = w - alpha * q
+        w = w - Q[:, :i + 1] @ (Q[:, :i + 1].T @ w)
+        beta = float(np.linalg.norm(w))
+        if beta <= breakdown * aq:
+            kk = i + 1
+            break
+        T[i, i + 1] = T[i + 1, i] = beta
+        q_prev, q = q, w / beta
+    return Q[:, :kk], T[:kk, :kk]
+
+
+def lowrank_cov(grid, kernel, X, y, Xs, k: int):
+    """Rank-k posterior covariance at test points from k Lanczos steps on A = W K W^T + sigma^2 I
+    started at y (the predictive-covariance approximation the paper uses, ref. [ConstantTimePD]):
+        A^{-1} ~ Q T^{-1} Q^T,   cov ~ W_s K W_s^T - (Q^T W K W_s^T)^T T^{-1} (Q^T W K W_s^T).
+    Returns (cov, T)."""
+    W = w_csr(grid, X)
+    Ws = w_csr(grid, Xs)
+    mv = ski_operator(grid, kernel, W)
+    Q, T = lanczos(mv, np.asarray(y, dtype=np.float64), k)
+    KWs = kg_matvec(grid, kernel, Ws.T.toarray())  # m x ns
+    Ks = W @ KWs                                     # n x ns
+    prior = Ws @ KWs
+    G = Q.T @ Ks
+    return prior - G.T @ np.linalg.solve(T, G), T
+
+
 def dense_system(grid, kernel, X):
     W = w_csr(grid, X).toarray()
     K = kg_dense(grid, kernel)

@@ -293,6 +293,31 @@ def test_nspace_cov_matches_dense(oracle_mod, d):
     assert np.all(np.diag(cov) >= -1e-12) and np.all(np.diag(cov) <= prior + 1e-12)
 
 
+def test_lanczos_lowrank_cov_exact_at_full_rank(oracle_mod):
+    """Lanczos with full reorthogonalisation: Q orthonormal, T symmetric tridiagonal and
+    Q^T A Q = T; run until the Krylov space of y is invariant (it then contains span(W), as A
+    acts as sigma^2 on the complement), the low-rank covariance equals the exact one."""
+    from oracle import core
+    grid, X, y = _tiny(2, n=70, seed=12)
+    kern = synth.Kernel(synth.RBF, (0.3, 0.35), 1.0, 0.05)
+    W = core.w_csr(grid, X)
+    mv = core.ski_operator(grid, kern, W)
+    Q, T = core.lanczos(mv, y.astype(np.float64), 12)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-10)
+    AQ = np.stack([mv(Q[:, i]) for i in range(Q.shape[1])], axis=1)
+    np.testing.assert_allclose(Q.T @ AQ, T, atol=1e-9 * np.abs(T).max())
+    assert np.all(np.abs(np.triu(T, 2)) == 0) and np.allclose(T, T.T)
+    Xs = np.random.default_rng(13).uniform(0, 1, size=(2, 11))
+    cov, Tf = core.lowrank_cov(grid, kern, X, y, Xs, k=X.shape[1])
+    assert Tf.shape[0] <= grid.m + 1  # invariant Krylov space reached
+    ref = core.ski_inference_dense(grid, kern, X, y, Xs)["cov"]
+    np.testing.assert_allclose(cov, ref, rtol=1e-6, atol=1e-8 * np.abs(ref).max())
+    # few steps: a partial correction, between the prior and the exact covariance on the diagonal
+    cov5, _ = core.lowrank_cov(grid, kern, X, y, Xs, k=5)
+    prior = np.diag(core.w_csr(grid, Xs).toarray() @ core.kg_dense(grid, kern) @ core.w_csr(grid, Xs).toarray().T)
+    assert np.all(np.diag(cov5) <= prior + 1e-12) and np.all(np.diag(cov5) >= np.diag(ref) - 1e-9)
+
+
 def test_nspace_cg_mean_matches_dense(oracle_mod):
     from oracle import core
     grid, X, y = _tiny(2, n=150, seed=9)
