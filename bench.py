@@ -173,6 +173,44 @@ def cpu_oracle_precompute_rate(X: np.ndarray, y: np.ndarray, grid, sample: int, 
     return sample / best / 1e9, best
 
 
+def per_iter_ms(run, k1: int = 32, k2: int = 96) -> float:
+    """Per-iteration time of a solver `run(maxiter)` that does exactly maxiter iterations
+    (rtol 0): (t(k2) - t(k1)) / (k2 - k1), so set-up and capture costs cancel."""
+    import torch
+    run(k1)  # warm-up (spectra, tuning, graph capture paths)
+    ts = {}
+    for k in (k1, k2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run(k)
+        torch.cuda.synchronize()
+        ts[k] = time.perf_counter() - t0
+    return (ts[k2] - ts[k1]) / (k2 - k1) * 1e3
+
+
+def ski_vs_gsgp(api, synth, dev, X=None, y=None, grid=None, kern=None, label=None):
+    """Per-iteration time of plain SKI (n-space CG, Alg. 1) and of the factorized solver on the
+    same problem (Sec. 5, Table 1 / Fig. 2), both FP32 vectors."""
+    import torch
+    st = api.precompute(X, y, grid, keep_points=True)
+    ski = per_iter_ms(lambda k: api.ski_solve(st, kern, rtol=0.0, maxiter=k, allow_not_converged=True))
+    gs = per_iter_ms(lambda k: api.solve(st, kern, rtol=0.0, maxiter=k, allow_not_converged=True))
+    st.close()
+    return {"workload": label, "n": int(X.shape[1]), "m": int(grid.m), "ski_ms_per_iter": ski,
+            "gsgp_ms_per_iter": gs, "gsgp_over_ski": gs / ski}
+
+
+def sine_sweep(api, synth, dev):
+    import torch
+    out = []
+    for n, m in [(2048, 2048), (32768, 2048), (1_000_000, 1000), (4_000_000, 2000), (16_000_000, 2000)]:
+        pr = synth.sine_sweep(n, m)
+        X = torch.from_numpy(pr.X).to(dev)
+        y = torch.from_numpy(pr.y).to(dev)
+        out.append(ski_vs_gsgp(api, synth, dev, X, y, pr.grid, pr.kernel, f"sine n={n} m={m}"))
+    return out
+
+
 # ------------------------------------------------------------------ reference arm (CPU oracle)
 def reference_arm(args):
     rank, world, _ = dist_env()
@@ -212,6 +250,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--maxiter", type=int, default=4000)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
+    ap.add_argument("--no-ski", action="store_true", help="skip the plain-SKI per-iteration comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -350,6 +389,12 @@ def main():
                      "loglik_mixed": Lg, "loglik_fp64": Lf, "grad": gg,
                      "cg_iters_mixed_max": max(ginfo["iters"]), "cg_iters_fp64_max": max(finfo["iters"])}
 
+    # plain SKI vs the factorized solver, per iteration (radar workload and the sine sweep)
+    comparison = None
+    if not args.no_ski:
+        comparison = [ski_vs_gsgp(api, synth, dev, X, y, grid, kern, "radar_3d (this step's workload)")]
+        comparison += sine_sweep(api, synth, dev)
+
     # CPU oracle baseline (rank 0 at N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample > 0:
@@ -393,6 +438,9 @@ def main():
     }
     if grad_info is not None:
         line["grad"] = grad_info
+    if comparison is not None:
+        line["ski_vs_gsgp"] = comparison
+    line["kg_autotune"] = [t for t in api.tuning_table().splitlines() if t]
     print(json.dumps(line), flush=True)
 
 

@@ -100,7 +100,9 @@ typedef struct {
     int keep_sort;        /* fkski_precompute keeps cell keys and the permutation for export   */
     int reliable_updates; /* true-residual replacement when the residual has dropped 10x since
                              the last one: 0 default (on for MIXED, off for DOUBLE), 1 on, 2 off */
-    int reserved[6];
+    int keep_points;      /* fkski_precompute keeps the points (local coordinates, y, cell keys) in
+                             cell order, as fkski_ski_solve needs                                */
+    int reserved[5];
 } fkski_opts;
 
 typedef struct {
@@ -131,6 +133,12 @@ FKSKI_API const char *fkski_last_error_detail(void);
  * solver captures its graphs); the choices give bit-identical results.  Writes at most len bytes
  * (NUL-terminated) to buf (may be NULL) and returns the size needed. */
 FKSKI_API size_t fkski_tuning_table(char *buf, size_t len);
+
+/* Stream-ordered temporaries (precompute scratch, covariance blocks, tuner buffers) come from a
+ * library memory pool per device that keeps freed blocks cached, so repeated calls map no new
+ * memory.  This returns the cached blocks to the device (the paper has no counterpart).  Call
+ * it with no library call in flight.  Returns OK or CUDA. */
+FKSKI_API int fkski_trim_memory(void);
 
 /* Number of kernel launches this library has issued in the process so far (a replayed CUDA graph
  * counts each of its kernel nodes).  Host-only; for instrumentation. */
@@ -231,6 +239,44 @@ FKSKI_API int fkski_solve(fkski_stats *st, const fkski_kernel *kern, const fkski
  * Errors: OUT_OF_GRID / NONFINITE for a test point (mu for other points still written). */
 FKSKI_API int fkski_predict(const fkski_stats *st, const void *v, int vdtype, const void *Xstar, int xdtype,
                   int64_t nstar, void *mu_out, void *stream);
+
+/* Plain SKI posterior mean (Def. 1) by n-space CG (Alg. 1) on W K_G W^T + sigma^2 I from x0 = 0:
+ * the O(n + m log m)-per-iteration method the paper's factorized solvers replace (Sec. 5,
+ * Fig. 2, Table 1), for comparison.  Needs the points kept by the precompute (opts.keep_points);
+ * otherwise UNSUPPORTED.  Vectors are in the points' precision (FP32 with FP64 cross-block
+ * inner products, or FP64).  Stops when ||r_k|| <= rtol ||y||; opts->maxiter, check_every as
+ * for fkski_solve.  Outputs as fkski_solve: a_out = W^T z, v_out = K_G W^T z (device, m, in the
+ * points' dtype).  Returns OK, NOT_CONVERGED, BREAKDOWN, INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+FKSKI_API int fkski_ski_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, void *a_out,
+                              void *v_out, fkski_info *info, void *stream);
+
+/* Posterior covariance at test points (Def. 1 / Fact 2, equal by Theorem 1):
+ *   cov(x_i, x_j) = w_i^T K_G w_j - (W K_G w_i)^T (W K_G W^T + sigma^2 I)^{-1} (W K_G w_j).
+ * The right-hand sides W K_G w_j lie in span(W): each is solved by the simplified EFCG from
+ * x0 = 0 with r_hat_0 = K_G w_j (App. B), blocks of 32 test points sharing one band read per
+ * iteration; opts as for fkski_solve (rtol relative to ||W K_G w_j||, precision, maxiter).
+ * Xstar device d x nstar (xdtype); cov_out device nstar x nstar FP64, row-major (cov_out[i*nstar+j]).
+ * info (host, may be NULL): max iterations and residual over the solves.  Returns OK,
+ * NOT_CONVERGED, BREAKDOWN, OUT_OF_GRID / NONFINITE (a test point; its row and column are 0),
+ * INVALID_ARG, OOM, CUDA.  Synchronizes the stream. */
+FKSKI_API int fkski_posterior_cov(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts,
+                                  const void *Xstar, int xdtype, int64_t nstar, double *cov_out, fkski_info *info,
+                                  void *stream);
+
+/* Rank-k approximation of the same covariance (the paper's predictive-covariance task with
+ * ref. [ConstantTimePD]): k steps of the efficiently factorized Lanczos method (App. B, EFLA) on
+ * W K_G W^T + sigma^2 I started at y / ||y||, in FP64 with full reorthogonalisation, give
+ * A^{-1} ~ Q T^{-1} Q^T with Q = W Q_hat + b d^T; then
+ *   cov(x, x') ~ w_x^T K_G w_x' - (R^T w_x)^T (R^T w_x'),   R = K_G (W^T W Q_hat + W^T b d^T) L^{-T},
+ * T = L L^T.  R (m x k FP64) is kept in the statistics object: later calls with the same kernel
+ * and k evaluate new test points in O(4^d k) each plus the prior term (one K_G product per 32
+ * test points).  Fewer than k steps are taken if the Krylov space closes (info->iters).  With k
+ * large enough the result equals fkski_posterior_cov.  Xstar / cov_out as there (nstar may be 0:
+ * build only).  Returns OK, BREAKDOWN (T not positive definite), OUT_OF_GRID / NONFINITE,
+ * INVALID_ARG, OOM, CUDA.  Synchronizes the stream. */
+FKSKI_API int fkski_posterior_cov_lowrank(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, int k,
+                                          const void *Xstar, int xdtype, int64_t nstar, double *cov_out,
+                                          fkski_info *info, void *stream);
 
 /* ------------------------------------------------------------------ batches of independent problems
  * Many unrelated GP problems of uneven sizes (serving-style batch), each with its own grid, data,

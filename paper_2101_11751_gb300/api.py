@@ -47,7 +47,8 @@ class COpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxiter", ctypes.c_int), ("x0_mode", ctypes.c_int),
                 ("precision", ctypes.c_int), ("check_every", ctypes.c_int), ("n_probes", ctypes.c_int),
                 ("probe_seed", ctypes.c_uint64), ("iterate_budget_bytes", ctypes.c_size_t),
-                ("keep_sort", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("keep_sort", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("keep_points", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class CInfo(ctypes.Structure):
@@ -76,12 +77,19 @@ SIGNATURES = {
     "fkski_kg_mvm": (ctypes.c_int, [ctypes.POINTER(CGrid), ctypes.POINTER(CKernel), ctypes.c_int, P, P,
                                     ctypes.c_int, ctypes.c_int, P]),
     "fkski_tuning_table": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
+    "fkski_trim_memory": (ctypes.c_int, []),
     "fkski_kg_mvm_noalloc": (ctypes.c_int, [ctypes.POINTER(CGrid), ctypes.POINTER(CKernel), ctypes.c_int, P, P,
                                             ctypes.c_int, ctypes.c_int, P]),
     "fkski_band_mvm": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, P]),
     "fkski_solve": (ctypes.c_int, [P, ctypes.POINTER(CKernel), ctypes.POINTER(COpts), P, P,
                                    ctypes.POINTER(CInfo), P]),
     "fkski_predict": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int64, P, P]),
+    "fkski_ski_solve": (ctypes.c_int, [P, ctypes.POINTER(CKernel), ctypes.POINTER(COpts), P, P,
+                                       ctypes.POINTER(CInfo), P]),
+    "fkski_posterior_cov": (ctypes.c_int, [P, ctypes.POINTER(CKernel), ctypes.POINTER(COpts), P, ctypes.c_int,
+                                           ctypes.c_int64, P, ctypes.POINTER(CInfo), P]),
+    "fkski_posterior_cov_lowrank": (ctypes.c_int, [P, ctypes.POINTER(CKernel), ctypes.POINTER(COpts), ctypes.c_int, P,
+                                                   ctypes.c_int, ctypes.c_int64, P, ctypes.POINTER(CInfo), P]),
     "fkski_precompute_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(CGrid), P, P,
                                                 ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(COpts),
                                                 P, P]),
@@ -203,12 +211,12 @@ class Stats:
 
 
 def precompute(X: torch.Tensor, y: torch.Tensor, grid, Z: Optional[torch.Tensor] = None, n_probes: int = 0,
-               probe_seed: int = 0, keep_sort: bool = False, stream=None) -> Stats:
+               probe_seed: int = 0, keep_sort: bool = False, keep_points: bool = False, stream=None) -> Stats:
     """fkski_precompute: X (d, n) and y (n) CUDA tensors of one dtype; Z optional (T, n)."""
     load()
     if Z is not None:
         n_probes = Z.shape[0]
-    o = opts(n_probes=n_probes, probe_seed=probe_seed, keep_sort=int(keep_sort))
+    o = opts(n_probes=n_probes, probe_seed=probe_seed, keep_sort=int(keep_sort), keep_points=int(keep_points))
     h = ctypes.c_void_p()
     g = c_grid(grid)
     code = _lib.fkski_precompute(ctypes.byref(g), _ptr(X), _ptr(y), _ptr(Z), X.shape[1], _dtype_code(X),
@@ -330,6 +338,54 @@ def predict(st: Stats, v: torch.Tensor, Xstar: torch.Tensor, stream=None) -> tor
     _check(_lib.fkski_predict(st.handle, _ptr(v), _dtype_code(v), _ptr(Xstar), _dtype_code(Xstar),
                               Xstar.shape[1], _ptr(mu), _stream(stream)), "fkski_predict")
     return mu
+
+
+def ski_solve(st: Stats, kernel, rtol: float = 1e-6, maxiter: int = 1000, check_every: int = 16, stream=None,
+              allow_not_converged: bool = False):
+    """fkski_ski_solve: plain SKI n-space CG (Alg. 1); needs precompute(..., keep_points=True)."""
+    load()
+    inf_ = st.info()
+    dt = torch.float32 if inf_["dtype"] == F32 else torch.float64
+    a = torch.empty(inf_["m"], dtype=dt, device="cuda")
+    v = torch.empty(inf_["m"], dtype=dt, device="cuda")
+    o = opts(rtol=rtol, maxiter=maxiter, check_every=check_every)
+    inf = CInfo()
+    k = c_kernel(kernel)
+    code = _lib.fkski_ski_solve(st.handle, ctypes.byref(k), ctypes.byref(o), _ptr(a), _ptr(v), ctypes.byref(inf),
+                                _stream(stream))
+    if not (allow_not_converged and code == E_NOT_CONVERGED):
+        _check(code, "fkski_ski_solve")
+    return a, v, dict(iters=inf.iters, rel_residual=inf.rel_residual, status=code)
+
+
+def posterior_cov(st: Stats, kernel, Xstar: torch.Tensor, rtol: float = 1e-6, maxiter: int = 1000,
+                  precision: int = MIXED, check_every: int = 16, stream=None, allow_not_converged: bool = False):
+    """fkski_posterior_cov: (nstar, nstar) FP64 posterior covariance at the test points."""
+    load()
+    ns = Xstar.shape[1]
+    cov = torch.empty(ns, ns, dtype=torch.float64, device="cuda")
+    o = opts(rtol=rtol, maxiter=maxiter, precision=precision, check_every=check_every)
+    inf = CInfo()
+    k = c_kernel(kernel)
+    code = _lib.fkski_posterior_cov(st.handle, ctypes.byref(k), ctypes.byref(o), _ptr(Xstar), _dtype_code(Xstar), ns,
+                                    _ptr(cov), ctypes.byref(inf), _stream(stream))
+    if not (allow_not_converged and code == E_NOT_CONVERGED):
+        _check(code, "fkski_posterior_cov")
+    return cov, dict(iters=inf.iters, rel_residual=inf.rel_residual, status=code)
+
+
+def posterior_cov_lowrank(st: Stats, kernel, Xstar: torch.Tensor, k: int, stream=None):
+    """fkski_posterior_cov_lowrank: rank-k (EFLA) approximation of the posterior covariance."""
+    load()
+    ns = Xstar.shape[1]
+    cov = torch.empty(ns, ns, dtype=torch.float64, device="cuda")
+    o = opts()
+    inf = CInfo()
+    kk = c_kernel(kernel)
+    _check(_lib.fkski_posterior_cov_lowrank(st.handle, ctypes.byref(kk), ctypes.byref(o), k, _ptr(Xstar),
+                                            _dtype_code(Xstar), ns, _ptr(cov), ctypes.byref(inf), _stream(stream)),
+           "fkski_posterior_cov_lowrank")
+    return cov, dict(steps=inf.iters)
 
 
 def precompute_batched(Xs: Sequence[torch.Tensor], ys: Sequence[torch.Tensor], grids, stream=None):

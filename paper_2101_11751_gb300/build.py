@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libfkski.so")
-SOURCES = ["precompute.cu", "kg.cu", "solve.cu", "grad.cu", "api.cu"]
+SOURCES = ["precompute.cu", "kg.cu", "solve.cu", "grad.cu", "ski.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

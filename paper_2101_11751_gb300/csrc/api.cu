@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 namespace fk {
@@ -14,7 +15,8 @@ void destroy_stats(fkski_stats *st) {
     cudaGetDevice(&cur);
     if (st->device != cur) cudaSetDevice(st->device);
     free_solve_work(st->work);
-    void *ptrs[] = {st->band, st->wty, st->wtz, st->band_alt, st->wty_alt, st->wtz_alt, st->keys, st->perm, st->offsets};
+    void *ptrs[] = {st->band, st->wty, st->wtz, st->band_alt, st->wty_alt, st->wtz_alt, st->keys, st->perm, st->offsets,
+                    st->lowrank, st->pts, st->pkeys};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (st->device != cur) cudaSetDevice(cur);
@@ -27,6 +29,52 @@ static thread_local char g_detail[256] = "";
 static std::atomic<long long> g_launches{0};
 
 void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Library memory pool per device for stream-ordered temporaries (precompute scratch and the
+// like): freed blocks stay cached in the pool (release threshold: unlimited), so repeated calls
+// of the same size map no new memory.  fkski_trim_memory() hands the cache back.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+
+static cudaError_t pool_for(int dev, cudaMemPool_t *out) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaError_t e = cudaMemPoolCreate(&g_pool[dev], &props);
+        if (e != cudaSuccess) return e;
+        uint64_t thr = UINT64_MAX;
+        e = cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &thr);
+        if (e != cudaSuccess) return e;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+int pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    int dev = 0;
+    FK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return FKSKI_E_UNSUPPORTED;
+    cudaMemPool_t pool;
+    FK_CUDA(pool_for(dev, &pool));
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, s);
+    if (e == cudaErrorMemoryAllocation) {  // give the cached blocks back and try once more
+        cudaGetLastError();
+        cudaStreamSynchronize(s);
+        cudaMemPoolTrimTo(pool, 0);
+        e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, s);
+    }
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return note_cuda_error(e, __FILE__, __LINE__);
+    }
+    return FKSKI_OK;
+}
 
 int note_cuda_error(cudaError_t e, const char *file, int line) {
     const char *base = strrchr(file, '/');
@@ -78,6 +126,13 @@ const char *fkski_last_error_detail(void) { return g_detail; }
 size_t fkski_tuning_table(char *buf, size_t len) { return kg_tuning_table(buf, len); }
 
 long long fkski_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int fkski_trim_memory(void) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    for (int d = 0; d < 64; ++d)
+        if (g_pool[d] && cudaMemPoolTrimTo(g_pool[d], 0) != cudaSuccess) return note_cuda_error(cudaGetLastError(), __FILE__, __LINE__);
+    return FKSKI_OK;
+}
 
 int fkski_precompute(const fkski_grid *grid, const void *X, const void *y, const void *Z, int64_t n, int dtype,
                      const fkski_opts *opts, fkski_stats **out, void *stream) {
@@ -258,6 +313,22 @@ int fkski_band_mvm(const fkski_stats *st, const void *x, void *u, int nrhs, int 
 int fkski_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, void *a_out, void *v_out,
                 fkski_info *info, void *stream) {
     return solve_impl(st, kern, opts, a_out, v_out, info, S(stream));
+}
+
+int fkski_ski_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, void *a_out, void *v_out,
+                    fkski_info *info, void *stream) {
+    return ski_solve_impl(st, kern, opts, a_out, v_out, info, S(stream));
+}
+
+int fkski_posterior_cov(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, const void *Xstar, int xdtype,
+                        int64_t nstar, double *cov_out, fkski_info *info, void *stream) {
+    return posterior_cov_impl(st, kern, opts, Xstar, xdtype, nstar, cov_out, info, S(stream));
+}
+
+int fkski_posterior_cov_lowrank(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, int k,
+                                const void *Xstar, int xdtype, int64_t nstar, double *cov_out, fkski_info *info,
+                                void *stream) {
+    return posterior_cov_lowrank_impl(st, kern, opts, k, Xstar, xdtype, nstar, cov_out, info, S(stream));
 }
 
 int fkski_precompute_batched(int nprob, const fkski_grid *grids, const void *const *X, const void *const *y,

@@ -13,6 +13,8 @@
 namespace fk {
 // Records the failing CUDA call (thread-local) for fkski_last_error_detail(); returns the status.
 int note_cuda_error(cudaError_t e, const char *file, int line);
+// Stream-ordered temporary from the library's per-device caching pool (free with cudaFreeAsync).
+int pool_alloc(void **p, size_t bytes, cudaStream_t s);
 }  // namespace fk
 
 #define FK_CUDA(call)                                                  \
@@ -116,8 +118,17 @@ struct fkski_stats {
     uint32_t *keys;
     uint32_t *perm;
     uint32_t *offsets;  // ncells + 1
+    // points in cell order for plain SKI (opts.keep_points): {t_1..t_d, y} records and cell keys
+    void *pts;
+    uint32_t *pkeys;
     // solver workspace (owned)
     fk::SolveWork *work;
+    // rank-k predictive-covariance factor (owned): R = K (P_hat + W^T b d^T) L^{-T}, m x k FP64
+    // row-major, for the kernel it was built with
+    double *lowrank;
+    int lowrank_k;      // Lanczos steps taken (fewer than requested if the Krylov space closed)
+    int lowrank_kreq;   // steps requested
+    fkski_kernel lowrank_kern;
 };
 
 namespace fk {
@@ -135,6 +146,12 @@ int solve_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts
                void *v_out, fkski_info *info, cudaStream_t s);
 int predict_impl(const fkski_stats *st, const void *v, int vdtype, const void *Xs, int xdtype,
                  int64_t ns, void *mu, cudaStream_t s);
+int posterior_cov_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, const void *Xs, int xdtype,
+                       int64_t ns, double *cov, fkski_info *info, cudaStream_t s);
+int posterior_cov_lowrank_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, int k,
+                               const void *Xs, int xdtype, int64_t ns, double *cov, fkski_info *info, cudaStream_t s);
+int ski_solve_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, void *a_out, void *v_out,
+                   fkski_info *info, cudaStream_t s);
 int solve_batched_impl(int P, fkski_stats *const *sts, const fkski_kernel *kernels, const fkski_opts *opts,
                        void *const *a_out, void *const *v_out, fkski_info *info, cudaStream_t s);
 int predict_batched_impl(int P, const fkski_stats *const *st, const void *const *v, int vdtype, const void *const *Xs,
@@ -223,6 +240,13 @@ template <>
 __device__ __forceinline__ int axis_cell<double>(double x, const KeyParams &kp, int k, int &cell, double &t) {
     return axis_cell_f64(x, kp.g[k], cell, t);
 }
+
+// Point record: local cell coordinates t_1..t_d (unused axes 0) and the target y.
+template <typename T>
+struct alignas(4 * sizeof(T)) Rec4 {
+    T t[3];
+    T y;
+};
 
 // Cubic-convolution weights (Keys, a = -1/2) on nodes c-1..c+2 written in the cubic Bernstein
 // basis, which has no cancellation on [0, 1]:

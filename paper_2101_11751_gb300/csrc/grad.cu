@@ -251,7 +251,7 @@ static int forward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_
     FK_TRY(grad_view(st, dt, &gv));
     double *est = sl.part;  // R doubles of scratch
     int *dstat;
-    FK_CUDA(cudaMallocAsync((void **)&dstat, sizeof(int), s));
+    FK_TRY(pool_alloc((void **)&dstat, sizeof(int), s));
     FK_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int), s));
     int kmax = 0;
     for (int r = 1; r < R; ++r) kmax = std::max(kmax, it[r]);
@@ -308,10 +308,10 @@ static int backward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski
     T *src, *dK;
     double *dd, *v64;
     const size_t sol_bytes = sizeof(T) * (size_t)R * m;
-    FK_CUDA(cudaMallocAsync((void **)&src, 2 * sol_bytes, s));
+    FK_TRY(pool_alloc((void **)&src, 2 * sol_bytes, s));
     dK = src + (size_t)R * m;
-    FK_CUDA(cudaMallocAsync((void **)&v64, sizeof(double) * 3 * m, s));
-    FK_CUDA(cudaMallocAsync((void **)&dd, sizeof(double) * ((d + 1) * R + 8 + 8), s));
+    FK_TRY(pool_alloc((void **)&v64, sizeof(double) * 3 * m, s));
+    FK_TRY(pool_alloc((void **)&dd, sizeof(double) * ((d + 1) * R + 8 + 8), s));
     double *s2dots = dd + (d + 1) * R;
     double *dgrad = s2dots + 4;
     const unsigned gb = (unsigned)std::min<int64_t>(cdiv((int64_t)R * m, 256), 152 * 8);

@@ -545,8 +545,8 @@ static int bttb_spectrum(KgOp *op, const fkski_kernel *kern, int param, cudaStre
     size_t have = 0;
     if (!op->lamN) FK_TRY(ensure(&op->lamN, have, sizeof(T) * N));
     C *z0 = nullptr, *z1 = nullptr;
-    FK_CUDA(cudaMallocAsync((void **)&z0, sizeof(C) * N, s));
-    FK_CUDA(cudaMallocAsync((void **)&z1, sizeof(C) * N, s));
+    FK_TRY(pool_alloc((void **)&z0, sizeof(C) * N, s));
+    FK_TRY(pool_alloc((void **)&z1, sizeof(C) * N, s));
     EmbedParams ep;
     memset(&ep, 0, sizeof(ep));
     ep.d = d;
@@ -731,7 +731,7 @@ template <typename T>
 static int kron_tune(KgOp *op, int nrhs, cudaStream_t s) {
     const int64_t m = op->m;
     T *buf = nullptr;
-    FK_CUDA(cudaMallocAsync((void **)&buf, sizeof(T) * 2 * (size_t)nrhs * m, s));
+    FK_TRY(pool_alloc((void **)&buf, sizeof(T) * 2 * (size_t)nrhs * m, s));
     int rc = cudaMemsetAsync(buf, 0, sizeof(T) * 2 * (size_t)nrhs * m, s) == cudaSuccess ? FKSKI_OK : FKSKI_E_CUDA;
     for (int a = 0; a < op->d && rc == FKSKI_OK; ++a) {
         RealPass p;

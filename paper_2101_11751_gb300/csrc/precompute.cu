@@ -83,12 +83,18 @@ static ETab<T> make_etab() {
     return E;
 }
 
-// ------------------------------------------------------------------ point records
+
+// Points in cell order for plain SKI: pts[k] = rec[perm[k]], pkeys[k] = keys[perm[k]].
 template <typename T>
-struct alignas(4 * sizeof(T)) Rec4 {
-    T t[3];
-    T y;
-};
+__global__ void k_gather_points(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ keys,
+                                const Rec4<T> *__restrict__ rec, int64_t n, Rec4<T> *__restrict__ pts,
+                                uint32_t *__restrict__ pkeys) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = perm[k];
+        pts[k] = rec[i];
+        pkeys[k] = keys[i];
+    }
+}
 
 // ------------------------------------------------------------------ K1: cell keys
 // One thread per point (uniform trip count per block so warp collectives stay converged).
@@ -308,16 +314,10 @@ constexpr int RS_ITEMS = 32;
 constexpr int RS_TILE = RS_T * RS_ITEMS;  // 8192; each warp owns 1024 contiguous keys
 constexpr int RS_MAXBITS = 10;
 
-// Lanes of the warp holding the same `bits`-bit digit, from one ballot per bit (lanes outside
-// `valid_mask` never match).
+// Lanes of the warp holding the same digit (lanes outside `valid_mask` never match).
 __device__ __forceinline__ unsigned digit_peers(uint32_t dg, int bits, unsigned valid_mask) {
-    unsigned peers = valid_mask;
-    for (int b = 0; b < bits; ++b) {
-        const unsigned bit = (dg >> b) & 1u;
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, bit);
-        peers &= bit ? bal : ~bal;
-    }
-    return peers;
+    (void)bits;
+    return __match_any_sync(0xFFFFFFFFu, dg) & valid_mask;
 }
 
 __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
@@ -823,23 +823,45 @@ __global__ void __launch_bounds__(MOM_WARPS * 32) k_moments(const uint32_t *__re
 // ------------------------------------------------------------------ FP32 3-D moments, point-balanced
 // The same per-cell sums as k_moments<float, 3>, with the work of a column tile split evenly by
 // points instead of by cells: warp w takes the w-th eighth of the tile's sorted point range,
-// walks it cell by cell in chunks of at most 32 points of one cell, and keeps 49 + 8 FP32 sums
+// walks it cell by cell in chunks of at most 16 points of one cell, and keeps 49 + 8 FP32 sums
 // per lane (4 sub-groups x 8 roles, as in cell_moments_d3).  Every M3_FLUSH chunks and at the
 // end of its part of a cell it folds the sub-groups together and adds the sums to shared
 // memory: straight into the cell's slot when the warp owns the whole cell, else into one of its
 // two edge buffers (first / last cell, shared with the neighbouring warps).  The edge buffers
 // are added to the slots in warp order afterwards, so the result does not depend on timing.
-// Records of the next chunk are loaded before the current one is computed.
+// Records of the next chunk are loaded before the current one is computed.  The 49 moment sums
+// of a role are kept as packed FP32 pairs over p2 and updated with fma.rn.f32x2 (two FMAs per
+// instruction; each element is rounded as a scalar FMA would be).
 constexpr int M3_WARPS = 8;
-constexpr int M3_PS = 36;     // staged floats per point: B1[7], y | B2[7], 0 | B3[7], 0 | w1[4] | w2[4] | w3[4]
-constexpr int M3_SLOT = 408;  // 343 moments + 64 y-moments + 1 pad
-constexpr int M3_FLUSH = 8;   // chunks between folds of the register sums
+constexpr int M3_PS = 44;     // staged floats per point: B1[7], y | B2[7], 0 | B3[p] twice each (14), 0, 0 |
+                              // w1[4] | w2[4] | w3[4]  (44 / 4 odd: conflict-free 16-byte rows)
+constexpr int M3_SLOT = 409;  // 343 moments + 64 y-moments + 2 pad (odd stride: the contraction's
+                              // threads read slots of consecutive cells without bank conflicts)
+constexpr int M3_CH = 16;     // points per chunk (staged by lanes 0..15)
+constexpr int M3_FLUSH = 16;  // chunks between folds of the register sums
 constexpr int M3_NCT = 64;    // cells per tile
 
 static size_t moments3f_smem(int nct) {
-    return sizeof(float) * ((size_t)M3_WARPS * 32 * M3_PS + (size_t)nct * M3_SLOT + (size_t)M3_WARPS * 2 * M3_SLOT) +
+    return sizeof(float) * ((size_t)M3_WARPS * M3_CH * M3_PS + (size_t)nct * M3_SLOT + (size_t)M3_WARPS * 2 * M3_SLOT) +
            sizeof(uint32_t) * (size_t)(nct + 1) + sizeof(int) * 2 * M3_WARPS;
 }
+
+// Packed FP32 pairs (fma.rn.f32x2 / mul.rn.f32x2): two lanes of a 64-bit register, low half first.
+__device__ __forceinline__ unsigned long long f2_dup(float a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_fma(unsigned long long &acc, unsigned long long a, unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ float f2_lo(unsigned long long a) { return __uint_as_float((unsigned)(a & 0xFFFFFFFFull)); }
+__device__ __forceinline__ float f2_hi(unsigned long long a) { return __uint_as_float((unsigned)(a >> 32)); }
 
 __device__ __forceinline__ int m3_find_cell(const uint32_t *coff, int nct, uint32_t p) {
     int lo = 0, hi = nct - 1;  // largest i with coff[i] <= p
@@ -850,7 +872,7 @@ __device__ __forceinline__ int m3_find_cell(const uint32_t *coff, int nct, uint3
     return lo;
 }
 
-__global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__restrict__ perm, const Rec4<float> *__restrict__ rec,
+__global__ void __launch_bounds__(M3_WARPS * 32, 2) k_moments3f(const uint32_t *__restrict__ perm, const Rec4<float> *__restrict__ rec,
                                                               const uint32_t *__restrict__ offsets, ColTiling tl, ETab<float> E,
                                                               float *__restrict__ outM, float *__restrict__ outY) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -864,7 +886,7 @@ __global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__r
     const int cend = min(je, tl.C);
     const int nct = cend - cfirst;
     float *stage = reinterpret_cast<float *>(smraw);
-    float *slots = stage + M3_WARPS * 32 * M3_PS;
+    float *slots = stage + M3_WARPS * M3_CH * M3_PS;
     float *edge = slots + nct * M3_SLOT;
     uint32_t *coff = reinterpret_cast<uint32_t *>(edge + M3_WARPS * 2 * M3_SLOT);
     int *ecell = reinterpret_cast<int *>(coff + nct + 1);
@@ -886,15 +908,19 @@ __global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__r
         ecell[2 * warp] = e0;
         ecell[2 * warp + 1] = e1;
     }
-    float *pb = stage + warp * 32 * M3_PS;
-    float m[49], yacc[8];
+    float *pb = stage + warp * M3_CH * M3_PS;
+    // m2[p3][pp] = (M[a][2pp][p3], M[a][2pp + 1][p3]) for role a = r (pp = 3: p2 = 6 and padding)
+    unsigned long long m2[7][4];
+    float yacc[8];
 #pragma unroll
-    for (int i = 0; i < 49; ++i) m[i] = 0.f;
+    for (int i = 0; i < 7; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m2[i][j] = 0ull;
 #pragma unroll
     for (int i = 0; i < 8; ++i) yacc[i] = 0.f;
     uint32_t p = ws;
     int c = ws < we ? m3_find_cell(coff, nct, ws) : 0;
-    int nh = ws < we ? (int)min(32u, min(coff[c + 1], we) - p) : 0;
+    int nh = ws < we ? (int)min((uint32_t)M3_CH, min(coff[c + 1], we) - p) : 0;
     Rec4<float> my;
     my.t[0] = my.t[1] = my.t[2] = my.y = 0.f;
     if (lane < nh) my = rec[perm[p + lane]];
@@ -913,13 +939,13 @@ __global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__r
             q[15] = 0.f;
             bern6<float>(my.t[2], b);
 #pragma unroll
-            for (int i = 0; i < 7; ++i) q[16 + i] = b[i];
-            q[23] = 0.f;
+            for (int i = 0; i < 7; ++i) q[16 + 2 * i] = q[17 + 2 * i] = b[i];
+            q[30] = q[31] = 0.f;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 keys_weights<float>(my.t[k], w);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) q[24 + 4 * k + i] = w[i];
+                for (int i = 0; i < 4; ++i) q[32 + 4 * k + i] = w[i];
             }
             float4 *dst = reinterpret_cast<float4 *>(pb + lane * M3_PS);
 #pragma unroll
@@ -932,7 +958,7 @@ __global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__r
         int nhn = 0;
         if (pn < we) {
             while (coff[cn + 1] <= pn) ++cn;
-            nhn = (int)min(32u, min(coff[cn + 1], we) - pn);
+            nhn = (int)min((uint32_t)M3_CH, min(coff[cn + 1], we) - pn);
             if (lane < nhn) my = rec[perm[pn + lane]];
         }
         __syncwarp();
@@ -940,19 +966,24 @@ __global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__r
             const float *q = pb + k * M3_PS;
             const float alpha = r < 7 ? q[r] : 0.f;
             const float yv = q[7];
-            const float4 b2a = *reinterpret_cast<const float4 *>(q + 8), b2b = *reinterpret_cast<const float4 *>(q + 12);
-            const float4 b3a = *reinterpret_cast<const float4 *>(q + 16), b3b = *reinterpret_cast<const float4 *>(q + 20);
-            const float b2[7] = {b2a.x, b2a.y, b2a.z, b2a.w, b2b.x, b2b.y, b2b.z};
-            const float b3[7] = {b3a.x, b3a.y, b3a.z, b3a.w, b3b.x, b3b.y, b3b.z};
+            const ulonglong2 b2a = *reinterpret_cast<const ulonglong2 *>(q + 8);
+            const ulonglong2 b2b = *reinterpret_cast<const ulonglong2 *>(q + 12);
+            const unsigned long long aa = f2_dup(alpha);
+            const unsigned long long ab[4] = {f2_mul(aa, b2a.x), f2_mul(aa, b2a.y), f2_mul(aa, b2b.x), f2_mul(aa, b2b.y)};
+            const ulonglong2 *b3 = reinterpret_cast<const ulonglong2 *>(q + 16);
 #pragma unroll
-            for (int p2 = 0; p2 < 7; ++p2) {
-                const float ab = alpha * b2[p2];
+            for (int h = 0; h < 4; ++h) {
+                const ulonglong2 bb = b3[h];
 #pragma unroll
-                for (int p3 = 0; p3 < 7; ++p3) m[p2 * 7 + p3] = fmaf(ab, b3[p3], m[p2 * 7 + p3]);
+                for (int pp = 0; pp < 4; ++pp) f2_fma(m2[2 * h][pp], ab[pp], bb.x);
+                if (h < 3) {
+#pragma unroll
+                    for (int pp = 0; pp < 4; ++pp) f2_fma(m2[2 * h + 1][pp], ab[pp], bb.y);
+                }
             }
-            const float ywa = yv * q[24 + (r >> 1)];
-            const float2 w2 = *reinterpret_cast<const float2 *>(q + 28 + 2 * (r & 1));
-            const float4 w3 = *reinterpret_cast<const float4 *>(q + 32);
+            const float ywa = yv * q[32 + (r >> 1)];
+            const float2 w2 = *reinterpret_cast<const float2 *>(q + 36 + 2 * (r & 1));
+            const float4 w3 = *reinterpret_cast<const float4 *>(q + 40);
             const float q0 = ywa * w2.x, q1 = ywa * w2.y;
             yacc[0] = fmaf(q0, w3.x, yacc[0]);
             yacc[1] = fmaf(q0, w3.y, yacc[1]);
@@ -965,6 +996,14 @@ __global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__r
         }
         __syncwarp();
         if (cell_done || ++nacc == M3_FLUSH) {
+            float m[49];
+#pragma unroll
+            for (int p3 = 0; p3 < 7; ++p3)
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) {
+                    m[(2 * pp) * 7 + p3] = f2_lo(m2[p3][pp]);
+                    if (pp < 3) m[(2 * pp + 1) * 7 + p3] = f2_hi(m2[p3][pp]);
+                }
 #pragma unroll
             for (int i = 0; i < 49; ++i) {
                 m[i] += __shfl_xor_sync(0xFFFFFFFFu, m[i], 8);
@@ -991,7 +1030,9 @@ __global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__r
             }
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < 49; ++i) m[i] = 0.f;
+            for (int i = 0; i < 7; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) m2[i][j] = 0ull;
 #pragma unroll
             for (int i = 0; i < 8; ++i) yacc[i] = 0.f;
             nacc = 0;
@@ -1189,32 +1230,56 @@ struct AxisPass {
     int S_in, S_out;
 };
 
+// One thread owns a run of AXJ consecutive output nodes j along the contracted axis (fixed
+// co, ci, so, si) and slides over the cells j-3 .. j+AXJ-1 once: each cell's values are loaded
+// once per run instead of once per output (4x fewer loads).  Consecutive threads take
+// consecutive si, so loads and stores stay coalesced.
+constexpr int AXJ = 8;
+
 template <typename T, bool MPART>
 __global__ void __launch_bounds__(256) k_axis_pass(const T *__restrict__ in, T *__restrict__ out, AxisPass ap, ETab<T> E) {
     constexpr int P = MPART ? 7 : 4;
     constexpr int DO = MPART ? 7 : 1;
     const int64_t Sin_tot = ap.n_so * ap.S_in * ap.n_si;
     const int64_t Sout_tot = ap.n_so * ap.S_out * ap.n_si;
-    const int64_t total = ap.n_co * ap.n_ci * Sout_tot;
+    const int nrun = (ap.S_out + AXJ - 1) / AXJ;
+    const int64_t total = ap.n_co * ap.n_ci * ap.n_so * nrun * ap.n_si;
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total; it += (int64_t)gridDim.x * blockDim.x) {
         int64_t r = it;
         const int64_t si = r % ap.n_si; r /= ap.n_si;
-        const int j = (int)(r % ap.S_out); r /= ap.S_out;
+        const int jr = (int)(r % nrun); r /= nrun;
         const int64_t so = r % ap.n_so; r /= ap.n_so;
         const int64_t ci = r % ap.n_ci;
         const int64_t co = r / ap.n_ci;
-        T acc[DO];
+        const int j0 = jr * AXJ;
+        const int jn = min(AXJ, ap.S_out - j0);
+        // win[3 - a] holds cell j - a; the window shifts by one cell per output
+        T win[4][P];
 #pragma unroll
-        for (int dl = 0; dl < DO; ++dl) acc[dl] = T(0);
+        for (int k = 0; k < 3; ++k) {
+            const int c = j0 - 3 + k;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int c = j - a;
-            if (c >= 0 && c < ap.S_in) {
-                const int64_t sp = (so * ap.S_in + c) * ap.n_si + si;
+            for (int p = 0; p < P; ++p)
+                win[k + 1][p] = (c >= 0 && c < ap.S_in) ? in[((co * P + p) * ap.n_ci + ci) * Sin_tot + (so * ap.S_in + c) * ap.n_si + si]
+                                                         : T(0);
+        }
+#pragma unroll 1
+        for (int jj = 0; jj < jn; ++jj) {
+            const int j = j0 + jj;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int p = 0; p < P; ++p) win[k][p] = win[k + 1][p];
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+                win[3][p] = (j < ap.S_in) ? in[((co * P + p) * ap.n_ci + ci) * Sin_tot + (so * ap.S_in + j) * ap.n_si + si] : T(0);
+            T acc[DO];
+#pragma unroll
+            for (int dl = 0; dl < DO; ++dl) acc[dl] = T(0);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const T *v = win[3 - a];  // cell j - a
                 if (MPART) {
-                    T v[7];
-#pragma unroll
-                    for (int p = 0; p < 7; ++p) v[p] = in[((co * P + p) * ap.n_ci + ci) * Sin_tot + sp];
 #pragma unroll
                     for (int dl = 0; dl < DO; ++dl) {
                         const int b = a + dl - 3;
@@ -1224,19 +1289,19 @@ __global__ void __launch_bounds__(256) k_axis_pass(const T *__restrict__ in, T *
                         }
                     }
                 } else {
-                    acc[0] += in[((co * P + a) * ap.n_ci + ci) * Sin_tot + sp];
+                    acc[0] += v[a];
                 }
             }
-        }
-        const int64_t spo = (so * ap.S_out + j) * ap.n_si + si;
+            const int64_t spo = (so * ap.S_out + j) * ap.n_si + si;
 #pragma unroll
-        for (int dl = 0; dl < DO; ++dl) out[((co * DO + dl) * ap.n_ci + ci) * Sout_tot + spo] = acc[dl];
+            for (int dl = 0; dl < DO; ++dl) out[((co * DO + dl) * ap.n_ci + ci) * Sout_tot + spo] = acc[dl];
+        }
     }
 }
 
 template <typename T, bool MPART>
 static int launch_axis_pass(const T *in, T *out, AxisPass ap, const ETab<T> &E, cudaStream_t s) {
-    const int64_t total = ap.n_co * ap.n_ci * ap.n_so * ap.S_out * ap.n_si;
+    const int64_t total = ap.n_co * ap.n_ci * ap.n_so * ((ap.S_out + AXJ - 1) / AXJ) * ap.n_si;
     const int64_t nb = std::min<int64_t>(cdiv(total, 256), 152 * 16);
     k_axis_pass<T, MPART><<<(unsigned)std::max<int64_t>(nb, 1), 256, 0, s>>>(in, out, ap, E);
     FK_LAUNCH();
@@ -1251,11 +1316,7 @@ struct Scratch {
     template <typename P>
     int get(P **p, size_t bytes) {
         void *q = nullptr;
-        if (bytes == 0) bytes = 16;
-        if (cudaMallocAsync(&q, bytes, s) != cudaSuccess) {
-            cudaGetLastError();
-            return FKSKI_E_OOM;
-        }
+        FK_TRY(pool_alloc(&q, bytes, s));
         ptrs.push_back(q);
         *p = reinterpret_cast<P *>(q);
         return FKSKI_OK;
@@ -1426,10 +1487,19 @@ static int precompute_typed(fkski_stats *st, const T *X, const T *y, const T *Z,
     if (opts && opts->keep_sort) {
         FK_CUDA(cudaMallocAsync((void **)&st->keys, sizeof(uint32_t) * n, s));
         FK_CUDA(cudaMallocAsync((void **)&st->perm, sizeof(uint32_t) * n, s));
-        FK_CUDA(cudaMallocAsync((void **)&st->offsets, sizeof(uint32_t) * (ncell + 1), s));
         FK_CUDA(cudaMemcpyAsync(st->keys, keys, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
         FK_CUDA(cudaMemcpyAsync(st->perm, perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    if (opts && (opts->keep_sort || opts->keep_points)) {
+        FK_CUDA(cudaMallocAsync((void **)&st->offsets, sizeof(uint32_t) * (ncell + 1), s));
         FK_CUDA(cudaMemcpyAsync(st->offsets, offsets, sizeof(uint32_t) * (ncell + 1), cudaMemcpyDeviceToDevice, s));
+    }
+    if (opts && opts->keep_points) {
+        FK_CUDA(cudaMallocAsync((void **)&st->pts, sizeof(Rec4<T>) * n, s));
+        FK_CUDA(cudaMallocAsync((void **)&st->pkeys, sizeof(uint32_t) * n, s));
+        const unsigned gbk = (unsigned)std::min<int64_t>(cdiv(n, 256), 152 * 16);
+        k_gather_points<T><<<gbk, 256, 0, s>>>(perm, keys, rec, n, (Rec4<T> *)st->pts, st->pkeys);
+        FK_LAUNCH();
     }
     int hstatus[4] = {0, 0, 0, 0};
     double hy[1 + kMaxProbes];

@@ -251,6 +251,129 @@ __global__ void __launch_bounds__(CG_T, Spmv4Occ<RB>::blocks) k_band_spmv4(const
     }
 }
 
+// Symmetric form for one FP32 right-hand side: W^T W is symmetric, so only the diagonals with
+// offset >= 0 are read -- a contiguous suffix of the stored band (centre row dx = 0..3, then
+// the 7 diagonals of every later row) -- about half the bytes.  The lower part of row i is
+// entry (i - off, i) of the stored upper diagonal:  u_i += H_off[i - off] x[i - off].  A thread
+// reads, per upper row, its 7 direct quads at i0 and two quads around i0 - rowbase per
+// diagonal for the mirrored term; the mirrored quads are the direct quads of the thread
+// rowbase/4 positions back, read at about the same time, so they come from L2.
+template <int NROW>
+__global__ void __launch_bounds__(CG_T, 3) k_band_spmv4h(const float *__restrict__ hb, const float *__restrict__ x,
+                                                          float *__restrict__ u, int64_t m, RowOffs rows,
+                                                          double *__restrict__ part, int NQ, const float *__restrict__ g,
+                                                          const int *__restrict__ gate, int Rtot, int r0, int nwork) {
+    if (gate && *gate) return;
+    __shared__ double sh[CG_T / 32];
+    if ((int)blockIdx.x >= nwork) {
+        if (part && threadIdx.x == 0)
+            for (int q = 0; q < NQ && q < 2; ++q) part[(int64_t)blockIdx.x * NQ * Rtot + r0 * NQ + q] = 0.0;
+        return;
+    }
+    constexpr int C = NROW / 2;  // centre row
+    float dq0 = 0.f, dq1 = 0.f;
+    const int64_t nquad = m >> 2;
+    auto ld4 = [&](const float *base, int64_t j) -> float4 {  // quad at j (multiple of 4), zero off the ends
+        if (j >= 0 && j + 4 <= m) return __ldcs(reinterpret_cast<const float4 *>(base + j));
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto xwin = [&](int64_t w0, float v[12]) {  // x[w0 .. w0 + 11], zero off the ends
+        if (w0 >= 0 && w0 + 12 <= m) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float4 f = __ldg(reinterpret_cast<const float4 *>(x + w0) + c);
+                v[4 * c] = f.x; v[4 * c + 1] = f.y; v[4 * c + 2] = f.z; v[4 * c + 3] = f.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 12; ++j) v[j] = (w0 + j >= 0 && w0 + j < m) ? __ldg(x + w0 + j) : 0.f;
+        }
+    };
+    auto comp = [](const float4 &f, int q) { return q == 0 ? f.x : (q == 1 ? f.y : (q == 2 ? f.z : f.w)); };
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nquad; t += (int64_t)nwork * blockDim.x) {
+        const int64_t i0 = t << 2;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        {
+            // centre row: direct dx = 0..3, mirrored dx = 1..3
+            float v[12];
+            xwin(i0 - 4, v);
+            float4 hc[4], hp[4];
+#pragma unroll
+            for (int dx = 0; dx < 4; ++dx) {
+                hc[dx] = ld4(hb + (int64_t)dx * m, i0);
+                hp[dx] = dx ? ld4(hb + (int64_t)dx * m, i0 - 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int dx = 0; dx < 4; ++dx)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[q] = fmaf(comp(hc[dx], q), v[q + dx + 4], acc[q]);
+                    if (dx > 0) {
+                        const int j = q - dx;  // mirrored entry at i0 + j
+                        const float h = j < 0 ? comp(hp[dx], j + 4) : comp(hc[dx], j);
+                        acc[q] = fmaf(h, v[j + 4], acc[q]);
+                    }
+                }
+        }
+#pragma unroll 1
+        for (int u_ = 0; u_ < C; ++u_) {
+            const int row = C + 1 + u_;
+            const int64_t rb = rows.base[row];
+            const float *hrow = hb + (int64_t)(4 + u_ * 7) * m;
+            {
+                float4 dq[7];
+#pragma unroll
+                for (int e = 0; e < 7; ++e) dq[e] = ld4(hrow + (int64_t)e * m, i0);
+                float v[12];
+                xwin(i0 + rb - 4, v);
+#pragma unroll
+                for (int e = 0; e < 7; ++e)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] = fmaf(comp(dq[e], q), v[q + e + 1], acc[q]);
+            }
+            float vm[12];
+            xwin(i0 - rb - 4, vm);
+            const int64_t j0 = i0 - rb;
+#pragma unroll
+            for (int e = 0; e < 7; ++e) {
+                // entries j0 + 3 - e + q, q = 0..3, of diagonal e
+                const float *hd = hrow + (int64_t)e * m;
+                const float4 qa = e > 3 ? ld4(hd, j0 - 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 qb = ld4(hd, j0);
+                const float4 qc = e < 3 ? ld4(hd, j0 + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int tt = 3 - e + q;  // offset from j0, in [-3, 6]
+                    const float h = tt < 0 ? comp(qa, tt + 4) : (tt < 4 ? comp(qb, tt) : comp(qc, tt - 4));
+                    acc[q] = fmaf(h, vm[tt + 4], acc[q]);
+                }
+            }
+        }
+        *reinterpret_cast<float4 *>(u + i0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        if (part) {
+            const float4 xv = __ldg(reinterpret_cast<const float4 *>(x + i0));
+            dq0 = fmaf(acc[0], xv.x, dq0);
+            dq0 = fmaf(acc[1], xv.y, dq0);
+            dq0 = fmaf(acc[2], xv.z, dq0);
+            dq0 = fmaf(acc[3], xv.w, dq0);
+            if (g) {
+                const float4 gv = __ldg(reinterpret_cast<const float4 *>(g + i0));
+                dq1 = fmaf(xv.x, gv.x, dq1);
+                dq1 = fmaf(xv.y, gv.y, dq1);
+                dq1 = fmaf(xv.z, gv.z, dq1);
+                dq1 = fmaf(xv.w, gv.w, dq1);
+            }
+        }
+    }
+    if (!part) return;
+    const double s0 = block_sum<float>(dq0, sh);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ * Rtot + r0 * NQ + 0] = s0;
+    if (NQ > 1) {
+        const double s1 = block_sum<float>(dq1, sh);
+        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ * Rtot + r0 * NQ + 1] = s1;
+    }
+}
+
 static int num_sms() {
     static int n = 0;
     if (n == 0) {
@@ -261,6 +384,120 @@ static int num_sms() {
             n = 1;
     }
     return n;
+}
+
+// The same vectorised form for FP64 vectors (true residuals, W^T x, FP64 solves) and FP64 bands:
+// 4 nodes per thread, the band quad and the 12-wide x window loaded as 16-byte vectors.
+template <typename T>
+struct Quad {
+    T v[4];
+};
+
+template <typename T>
+__device__ __forceinline__ Quad<T> ld_quad(const T *p, bool stream);
+template <>
+__device__ __forceinline__ Quad<float> ld_quad<float>(const float *p, bool stream) {
+    const float4 f = stream ? __ldcs(reinterpret_cast<const float4 *>(p)) : __ldg(reinterpret_cast<const float4 *>(p));
+    return Quad<float>{{f.x, f.y, f.z, f.w}};
+}
+template <>
+__device__ __forceinline__ Quad<double> ld_quad<double>(const double *p, bool stream) {
+    const double2 a = stream ? __ldcs(reinterpret_cast<const double2 *>(p)) : __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = stream ? __ldcs(reinterpret_cast<const double2 *>(p) + 1) : __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return Quad<double>{{a.x, a.y, b.x, b.y}};
+}
+
+template <typename T>
+__device__ __forceinline__ void st_quad(T *p, const T v[4]);
+template <>
+__device__ __forceinline__ void st_quad<float>(float *p, const float v[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st_quad<double>(double *p, const double v[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
+template <typename TB, typename TX, int NROW, int RB>
+__global__ void __launch_bounds__(CG_T, RB <= 2 ? 2 : 1) k_band_spmv4g(const TB *__restrict__ band, const TX *__restrict__ x,
+                                                          TX *__restrict__ u, int64_t m, int R, RowOffs rows,
+                                                          double *__restrict__ part, int NQ, const TX *__restrict__ g,
+                                                          const int *__restrict__ gate, int Rtot, int r0, int nwork) {
+    if (gate && *gate) return;
+    __shared__ double sh[CG_T / 32];
+    if ((int)blockIdx.x >= nwork) {
+        if (part && threadIdx.x == 0)
+            for (int k = 0; k < R && k < RB; ++k)
+                for (int q = 0; q < NQ && q < 2; ++q) part[(int64_t)blockIdx.x * NQ * Rtot + (r0 + k) * NQ + q] = 0.0;
+        return;
+    }
+    TX dq0[RB], dq1[RB];
+#pragma unroll
+    for (int k = 0; k < RB; ++k) dq0[k] = dq1[k] = TX(0);
+    const int64_t nquad = m >> 2;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nquad; t += (int64_t)nwork * blockDim.x) {
+        const int64_t i0 = t << 2;
+        TX acc[RB][4];
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[k][q] = TX(0);
+#pragma unroll 1
+        for (int row = 0; row < NROW; ++row) {
+            Quad<TB> b[7];
+#pragma unroll
+            for (int e = 0; e < 7; ++e) b[e] = ld_quad<TB>(band + (int64_t)(row * 7 + e) * m + i0, true);
+            const int64_t w0 = i0 + rows.base[row] - 4;
+            const bool inside = w0 >= 0 && w0 + 12 <= m;
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                if (k < R) {
+                    const TX *xk = x + (int64_t)k * m;
+                    TX v[12];
+                    if (inside) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const Quad<TX> f = ld_quad<TX>(xk + w0 + 4 * c, false);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) v[4 * c + q] = f.v[q];
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 12; ++j) v[j] = (w0 + j >= 0 && w0 + j < m) ? xk[w0 + j] : TX(0);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 7; ++e)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[k][q] = fma((TX)b[e].v[q], v[e + 1 + q], acc[k][q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+            if (k < R) {
+                st_quad<TX>(u + (int64_t)k * m + i0, acc[k]);
+                if (part) {
+                    const Quad<TX> xv = ld_quad<TX>(x + (int64_t)k * m + i0, false);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dq0[k] = fma(acc[k][q], xv.v[q], dq0[k]);
+                    if (g) {
+                        const Quad<TX> gv = ld_quad<TX>(g + (int64_t)k * m + i0, false);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) dq1[k] = fma(xv.v[q], gv.v[q], dq1[k]);
+                    }
+                }
+            }
+    }
+    if (!part) return;
+    for (int k = 0; k < R && k < RB; ++k) {
+        const double s0 = block_sum<TX>(dq0[k], sh);
+        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ * Rtot + (r0 + k) * NQ + 0] = s0;
+        if (NQ > 1) {
+            const double s1 = block_sum<TX>(dq1[k], sh);
+            if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ * Rtot + (r0 + k) * NQ + 1] = s1;
+        }
+    }
 }
 
 static bool spmv4_ok(const fkski_grid &g, int64_t m, const void *band, const void *x, const void *u, const void *gv) {
@@ -322,6 +559,17 @@ static int launch_spmv(const TB *band, const fkski_grid &g, const TX *x, TX *u, 
     if constexpr (std::is_same<TB, float>::value && std::is_same<TX, float>::value) {
         if (spmv4_ok(g, m, band, x, u, gv)) {
             const RowOffs ro = make_rows(g);
+            if (R == 1) {
+                // one rhs: symmetric half (the stored band from the centre row's dx = 0 onwards)
+                const int nrow = g.d == 3 ? 49 : (g.d == 2 ? 7 : 1);
+                const float *hb = band + (int64_t)((nrow / 2) * 7 + 3) * m;
+                const int nwork = std::min(nblocks, num_sms() * 3);
+                if (g.d == 3) k_band_spmv4h<49><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork);
+                else if (g.d == 2) k_band_spmv4h<7><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork);
+                else k_band_spmv4h<1><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork);
+                FK_LAUNCH();
+                return FKSKI_OK;
+            }
             // rhs in even groups of at most 8: the band is read once per group
             const int ng = (int)cdiv(R, 8), per = (int)cdiv(R, ng);
             for (int r0 = 0; r0 < R; r0 += per) {
@@ -332,6 +580,35 @@ static int launch_spmv(const TB *band, const fkski_grid &g, const TX *x, TX *u, 
                 if (g.d == 3) launch_spmv4_rows<49>(band, xb, ub, m, Rb, ro, part, NQ, gb, gate, nblocks, R, r0, s);
                 else if (g.d == 2) launch_spmv4_rows<7>(band, xb, ub, m, Rb, ro, part, NQ, gb, gate, nblocks, R, r0, s);
                 else launch_spmv4_rows<1>(band, xb, ub, m, Rb, ro, part, NQ, gb, gate, nblocks, R, r0, s);
+                FK_LAUNCH();
+            }
+            return FKSKI_OK;
+        }
+    }
+    if constexpr (!(std::is_same<TB, float>::value && std::is_same<TX, float>::value)) {
+        if (spmv4_ok(g, m, band, x, u, gv)) {
+            const RowOffs ro = make_rows(g);
+            // rhs in even groups of at most 4 (FP64 accumulators)
+            const int ng = (int)cdiv(R, 4), per = (int)cdiv(R, ng);
+            for (int r0 = 0; r0 < R; r0 += per) {
+                const int Rb = std::min(per, R - r0);
+                const int nwork = std::min(nblocks, num_sms() * (Rb <= 2 ? 2 : 1));
+                const TX *xb = x + (int64_t)r0 * m;
+                TX *ub = u + (int64_t)r0 * m;
+                const TX *gb2 = gv ? gv + (int64_t)r0 * m : nullptr;
+#define FK_SPMV4G(NR, RBV) \
+    k_band_spmv4g<TB, TX, NR, RBV><<<nblocks, CG_T, 0, s>>>(band, xb, ub, m, Rb, ro, part, NQ, gb2, gate, R, r0, nwork)
+#define FK_SPMV4G_R(NR)                   \
+    do {                                  \
+        if (Rb <= 1) FK_SPMV4G(NR, 1);    \
+        else if (Rb <= 2) FK_SPMV4G(NR, 2); \
+        else FK_SPMV4G(NR, 4);            \
+    } while (0)
+                if (g.d == 3) FK_SPMV4G_R(49);
+                else if (g.d == 2) FK_SPMV4G_R(7);
+                else FK_SPMV4G_R(1);
+#undef FK_SPMV4G_R
+#undef FK_SPMV4G
                 FK_LAUNCH();
             }
             return FKSKI_OK;
@@ -977,9 +1254,14 @@ struct FcgGraphs {
     }
 };
 
+// r0_in (optional, non-GEN only): right-hand sides b_r = W r0_in[r] in span(W) with x0 = 0 (the
+// second start of App. B that puts r0 in span(W), e.g. posterior covariance); device FP64 R x m,
+// with ||b_r||^2 in rho0_in (host).  Without it row 0 solves for y from x0 = y / sigma^2.
 template <typename T, bool GEN>
 static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int R, const int *rebase,
-                       CgVecs<T> &V, FcgGraphs &G, cudaStream_t s) {
+                       CgVecs<T> &V, FcgGraphs &G, cudaStream_t s, const double *r0_in = nullptr,
+                       const double *rho0_in = nullptr) {
+    if (r0_in && (GEN || !rho0_in)) return FKSKI_E_INVALID_ARG;
     SolveWork *w;
     FK_TRY(work_get(st, &w));
     const int dt = sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64;
@@ -1012,10 +1294,10 @@ static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_op
     FK_CUDA(cudaMemcpyAsync(w->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, s));
     std::vector<double> hS((size_t)NF * R, 0.0);
     for (int r = 0; r < R; ++r) {
-        const double rho = r == 0 ? st->yty : st->ztz[r - 1];
+        const double rho = r0_in ? rho0_in[r] : (r == 0 ? st->yty : st->ztz[r - 1]);
         hS[F_RHO0 * R + r] = rho;
         hS[F_EPS * R + r] = o->rtol * o->rtol * rho;
-        hS[F_C0 * R + r] = 1.0 / s2;
+        hS[F_C0 * R + r] = r0_in ? 0.0 : 1.0 / s2;
     }
     FK_CUDA(cudaMemcpyAsync(w->S, hS.data(), sizeof(double) * NF * R, cudaMemcpyHostToDevice, s));
     FK_CUDA(cudaMemsetAsync(w->state, 0, sizeof(int) * R, s));
@@ -1029,13 +1311,17 @@ static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_op
     const int *gate_done = &w->ctl->all_done;
     const int *gate_conf = &w->ctl->all_conf;
     const int NQ = GEN ? 2 : 1;
-    // W^T b for every rhs
-    FK_CUDA(cudaMemcpyAsync(V.g0, wty, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
-    if (R > 1) FK_CUDA(cudaMemcpyAsync(V.g0 + m, wtz, sizeof(T) * (R - 1) * m, cudaMemcpyDeviceToDevice, s));
-    // K_G W^T b in FP64 (for the Alg. 5 starts)
-    k_convert_t<T, double><<<gv, 256, 0, s>>>(V.g0, V.t64, (int64_t)nT, 1.0);
-    FK_LAUNCH();
-    FK_TRY(kgop_apply(kg64, V.t64, V.w64, R, nullptr, 0.0, s));
+    if (r0_in) {
+        FK_CUDA(cudaMemsetAsync(V.g0, 0, sizeof(T) * nT, s));  // x0 = 0: no W^T b term in W^T x
+    } else {
+        // W^T b for every rhs
+        FK_CUDA(cudaMemcpyAsync(V.g0, wty, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
+        if (R > 1) FK_CUDA(cudaMemcpyAsync(V.g0 + m, wtz, sizeof(T) * (R - 1) * m, cudaMemcpyDeviceToDevice, s));
+        // K_G W^T b in FP64 (for the Alg. 5 starts)
+        k_convert_t<T, double><<<gv, 256, 0, s>>>(V.g0, V.t64, (int64_t)nT, 1.0);
+        FK_LAUNCH();
+        FK_TRY(kgop_apply(kg64, V.t64, V.w64, R, nullptr, 0.0, s));
+    }
     int *mask = w->want;  // reused below as the replacement flags (reset after setup)
     if (GEN) {
         std::vector<int> hm(R);
@@ -1080,6 +1366,11 @@ static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_op
         FK_CUDA(cudaMemsetAsync(mask, 0, sizeof(int) * R, s));
         FK_CUDA(cudaMemsetAsync(V.u, 0, sizeof(T) * 3 * nT, s));  // u, v, p back to zero (s below)
         FK_CUDA(cudaMemsetAsync(V.s, 0, sizeof(T) * nT, s));
+    } else if (r0_in) {
+        // b = W r0_in with x0 = 0: r = b, so r_hat_0 = r0_in
+        FK_CUDA(cudaMemcpyAsync(V.r0, r0_in, sizeof(double) * nT, cudaMemcpyDeviceToDevice, s));
+        k_convert_t<double, T><<<gv, 256, 0, s>>>(V.r0, V.r, (int64_t)nT, 1.0);
+        FK_LAUNCH();
     } else {
         // r_hat_0 = -K_G W^T y / sigma^2 in FP64; r_hat = r_hat_0 in T
         k_convert_t<double, double><<<gv, 256, 0, s>>>(V.w64, V.r0, m, -1.0 / s2);
@@ -1328,8 +1619,8 @@ static int solve_batched_typed(int P, fkski_stats *const *sts, const fkski_kerne
     if (rc == FKSKI_OK) {
         std::vector<CgCtl *> hctls(P);
         for (int p = 0; p < P; ++p) hctls[p] = sts[p]->work->ctl;
-        cudaError_t e = cudaMallocAsync((void **)&dctls, sizeof(CgCtl *) * P, s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&dflags, sizeof(int) * 2 * P, s);
+        cudaError_t e = pool_alloc((void **)&dctls, sizeof(CgCtl *) * P, s) == FKSKI_OK ? cudaSuccess : cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = pool_alloc((void **)&dflags, sizeof(int) * 2 * P, s) == FKSKI_OK ? cudaSuccess : cudaErrorMemoryAllocation;
         if (e == cudaSuccess) e = cudaMemcpyAsync(dctls, hctls.data(), sizeof(CgCtl *) * P, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMallocHost((void **)&hflags, sizeof(int) * 2 * P);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // hctls is a host temporary
@@ -1572,7 +1863,7 @@ template <typename TX, typename TV>
 static int predict_typed(const fkski_stats *st, const TV *v, const TX *Xs, int64_t ns, TV *mu, cudaStream_t s) {
     const KeyParams kp = make_key_params(st->grid);
     int *dst;
-    FK_CUDA(cudaMallocAsync((void **)&dst, sizeof(int), s));
+    FK_TRY(pool_alloc((void **)&dst, sizeof(int), s));
     FK_CUDA(cudaMemsetAsync(dst, 0, sizeof(int), s));
     const int64_t M1 = st->grid.M[1], M2 = st->grid.M[2];
     const int64_t s1 = st->d == 2 ? M1 : M1 * M2, s2 = M2;
@@ -1632,8 +1923,8 @@ static int predict_batched_typed(int P, const fkski_stats *const *st, const void
     for (int k = 0; k < 3; ++k) jb += jobs[k].size();
     PredJob<TX, TV> *dj = nullptr;
     int *dst = nullptr;
-    FK_CUDA(cudaMallocAsync((void **)&dj, sizeof(PredJob<TX, TV>) * std::max<size_t>(jb, 1), s));
-    FK_CUDA(cudaMallocAsync((void **)&dst, sizeof(int) * std::max<size_t>(jb, 1), s));
+    FK_TRY(pool_alloc((void **)&dj, sizeof(PredJob<TX, TV>) * std::max<size_t>(jb, 1), s));
+    FK_TRY(pool_alloc((void **)&dst, sizeof(int) * std::max<size_t>(jb, 1), s));
     FK_CUDA(cudaMemsetAsync(dst, 0, sizeof(int) * std::max<size_t>(jb, 1), s));
     std::vector<PredJob<TX, TV>> all;
     for (int k = 0; k < 3; ++k) all.insert(all.end(), jobs[k].begin(), jobs[k].end());
@@ -1678,6 +1969,558 @@ int predict_batched_impl(int P, const fkski_stats *const *st, const void *const 
     if (vdtype == FKSKI_F32 && xdtype == FKSKI_F64) return predict_batched_typed<double, float>(P, st, v, Xs, ns, mu, so, s);
     if (vdtype == FKSKI_F64 && xdtype == FKSKI_F64) return predict_batched_typed<double, double>(P, st, v, Xs, ns, mu, so, s);
     return FKSKI_E_INVALID_ARG;
+}
+
+// ------------------------------------------------------------------ posterior covariance
+// Exact SKI / GSGP posterior covariance at test points (Theorem 1, Claim 6):
+//   cov(x_i, x_j) = w_i^T K w_j - (W K w_i)^T A^{-1} (W K w_j),  A = W K W^T + sigma^2 I
+//                 = w_i^T c_j,   c_j = K w_j - K W^T A^{-1} W (K w_j).
+// The right-hand side W (K w_j) lies in span(W), so each solve is the simplified EFCG from
+// x0 = 0 with r_hat_0 = K w_j (App. B, second start), which returns W^T x = W^T W x_hat.
+// Test points are solved in blocks of COV_R right-hand sides sharing one band read per
+// iteration; c_j is gathered at all test points with the prediction weights.
+constexpr int COV_R = 32;
+
+// e[r] = w_{j0 + r} scattered on the grid (FP64); a point off the grid scatters nothing.
+template <typename TX, int D>
+__global__ void k_scatter_w(const TX *__restrict__ Xs, int64_t ns, int64_t j0, int R, KeyParams kp,
+                            double *__restrict__ e, int64_t m, int64_t s1, int64_t s2, int *__restrict__ status) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int64_t i = j0 + r;
+    int c[3] = {1, 1, 1};
+    TX t[3] = {TX(0), TX(0), TX(0)};
+    int st = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) st |= axis_cell<TX>(Xs[(int64_t)k * ns + i], kp, k, c[k], t[k]);
+    if (st) {
+        atomicOr(status, (st & 2) ? ST_NONFINITE : ST_OUT_OF_GRID);
+        return;
+    }
+    double w[3][4];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        TX wx[4];
+        keys_weights<TX>(t[k], wx);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) w[k][a] = (double)wx[a];
+    }
+    double *er = e + (int64_t)r * m;
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < (D > 1 ? 4 : 1); ++b)
+            for (int q = 0; q < (D > 2 ? 4 : 1); ++q) {
+                int64_t idx;
+                double v;
+                if (D == 1) { idx = c[0] - 1 + a; v = w[0][a]; }
+                else if (D == 2) { idx = (int64_t)(c[0] - 1 + a) * s1 + (c[1] - 1 + b); v = w[0][a] * w[1][b]; }
+                else {
+                    idx = (int64_t)(c[0] - 1 + a) * s1 + (int64_t)(c[1] - 1 + b) * s2 + (c[2] - 1 + q);
+                    v = w[0][a] * w[1][b] * w[2][q];
+                }
+                er[idx] = v;
+            }
+}
+
+// cov[i][j0 + r] = w_i^T c_r for all test points i (row-major ns x ns, FP64)
+template <typename TX, int D>
+__global__ void k_cov_gather(const TX *__restrict__ Xs, int64_t ns, KeyParams kp, const double *__restrict__ C, int R,
+                             int64_t m, int64_t j0, double *__restrict__ cov, int64_t s1, int64_t s2) {
+    const int64_t total = ns * (int64_t)R;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % R);
+        const int64_t i = e / R;
+        int bad = 0;
+        cov[i * ns + j0 + r] = predict_point<TX, double, D>(Xs, ns, i, kp, C + (int64_t)r * m, s1, s2, bad);
+    }
+}
+
+__global__ void k_sub64(double *__restrict__ a, const double *__restrict__ b, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) a[e] -= b[e];
+}
+
+template <typename T, typename TX>
+static int posterior_cov_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, const TX *Xs, int64_t ns,
+                               double *cov, fkski_info *info, cudaStream_t s) {
+    const int64_t m = st->m;
+    const int d = st->d;
+    const KeyParams kp = make_key_params(st->grid);
+    const int64_t M1 = st->grid.M[1], M2 = st->grid.M[2];
+    const int64_t s1 = d == 2 ? M1 : M1 * M2, s2 = M2;
+    SolveWork *w;
+    FK_TRY(work_get(st, &w));
+    KgOp *kg64;
+    FK_TRY(work_kg(st, w, FKSKI_F64, &kg64));
+    const T *band, *wty, *wtz;
+    FK_TRY(stats_as<T>(st, &band, &wty, &wtz, s));
+    double *bh = nullptr, *tmp = nullptr, *sums = nullptr;
+    int *dstatus = nullptr;
+    const size_t nR = (size_t)COV_R * m;
+    FK_TRY(pool_alloc((void **)&bh, sizeof(double) * nR, s));
+    FK_TRY(pool_alloc((void **)&tmp, sizeof(double) * nR, s));
+    FK_TRY(pool_alloc((void **)&sums, sizeof(double) * 4 * COV_R, s));
+    FK_TRY(pool_alloc((void **)&dstatus, sizeof(int), s));
+    FK_CUDA(cudaMemsetAsync(dstatus, 0, sizeof(int), s));
+    const unsigned gb = (unsigned)grid_blocks(m);
+    int rc = FKSKI_OK, worst = FKSKI_OK, itmax = 0;
+    double resmax = 0.0;
+    for (int64_t j0 = 0; j0 < ns && rc == FKSKI_OK; j0 += COV_R) {
+        const int R = (int)std::min<int64_t>(COV_R, ns - j0);
+        const int64_t nT = (int64_t)R * m;
+        const unsigned gv = (unsigned)std::min<int64_t>(cdiv(nT, 256), 152 * 8);
+        // b_hat_r = K w_r
+        FK_CUDA(cudaMemsetAsync(tmp, 0, sizeof(double) * nT, s));
+        if (d == 1) k_scatter_w<TX, 1><<<(R + 63) / 64, 64, 0, s>>>(Xs, ns, j0, R, kp, tmp, m, s1, s2, dstatus);
+        else if (d == 2) k_scatter_w<TX, 2><<<(R + 63) / 64, 64, 0, s>>>(Xs, ns, j0, R, kp, tmp, m, s1, s2, dstatus);
+        else k_scatter_w<TX, 3><<<(R + 63) / 64, 64, 0, s>>>(Xs, ns, j0, R, kp, tmp, m, s1, s2, dstatus);
+        FK_LAUNCH();
+        FK_TRY(kgop_set(kg64, kern, -1, s));
+        FK_TRY(kgop_apply(kg64, tmp, bh, R, nullptr, 0.0, s));
+        // ||W b_hat_r||^2 = b_hat_r^T (W^T W) b_hat_r
+        FK_TRY((launch_spmv<T, double>(band, st->grid, bh, tmp, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
+        k_dots4<double, double><<<gb, CG_T, 0, s>>>(bh, tmp, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R,
+                                                    w->part, nullptr);
+        k_fin_sums<<<(unsigned)cdiv(R * 4 * 32, 256), 256, 0, s>>>(w->part, gb, R, 4, sums);
+        FK_LAUNCH();
+        std::vector<double> hs(4 * R), rho(R);
+        FK_CUDA(cudaMemcpyAsync(hs.data(), sums, sizeof(double) * 4 * R, cudaMemcpyDeviceToHost, s));
+        FK_CUDA(cudaStreamSynchronize(s));
+        for (int r = 0; r < R; ++r) rho[r] = std::max(hs[4 * r], 1e-300);
+        // solve A x_r = W b_hat_r from x0 = 0
+        CgVecs<T> V;
+        FcgGraphs G;
+        rc = fcg_prepare<T, false>(st, kern, o, R, nullptr, V, G, s, bh, rho.data());
+        cudaGraphExec_t eb = nullptr, er = nullptr;
+        if (rc == FKSKI_OK) {
+            cudaError_t e = cudaGraphInstantiate(&eb, G.body, 0);
+            if (e == cudaSuccess && G.rep) e = cudaGraphInstantiate(&er, G.rep, 0);
+            if (e != cudaSuccess) rc = note_cuda_error(e, __FILE__, __LINE__);
+        }
+        if (rc == FKSKI_OK) rc = run_graph_loop(eb, er, w, o->maxiter, G.check, s, G.nbody, G.nrep);
+        if (eb) cudaGraphExecDestroy(eb);
+        if (er) cudaGraphExecDestroy(er);
+        G.release();
+        std::vector<int> its(R);
+        std::vector<double> res(R);
+        int status = FKSKI_OK;
+        if (rc == FKSKI_OK) rc = fcg_collect<T>(st, R, its.data(), res.data(), &status, s);
+        if (rc != FKSKI_OK) break;
+        for (int r = 0; r < R; ++r) {
+            itmax = std::max(itmax, its[r]);
+            resmax = std::max(resmax, res[r]);
+        }
+        if (status == FKSKI_E_BREAKDOWN || (status != FKSKI_OK && worst == FKSKI_OK)) worst = status;
+        // c_r = b_hat_r - K W^T x_r  (W^T x_r = W^T W x_hat_r, FP64)
+        FK_TRY(fcg_wtx64<T>(st, V, R, V.w64, s));
+        FK_TRY(kgop_set(kg64, kern, -1, s));
+        FK_TRY(kgop_apply(kg64, V.w64, tmp, R, nullptr, 0.0, s));
+        k_sub64<<<gv, 256, 0, s>>>(bh, tmp, nT);
+        FK_LAUNCH();
+        const unsigned gg = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(ns * R, 256), 152 * 16));
+        if (d == 1) k_cov_gather<TX, 1><<<gg, 256, 0, s>>>(Xs, ns, kp, bh, R, m, j0, cov, s1, s2);
+        else if (d == 2) k_cov_gather<TX, 2><<<gg, 256, 0, s>>>(Xs, ns, kp, bh, R, m, j0, cov, s1, s2);
+        else k_cov_gather<TX, 3><<<gg, 256, 0, s>>>(Xs, ns, kp, bh, R, m, j0, cov, s1, s2);
+        FK_LAUNCH();
+    }
+    int hst = 0;
+    FK_CUDA(cudaMemcpyAsync(&hst, dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(bh, s);
+    cudaFreeAsync(tmp, s);
+    cudaFreeAsync(sums, s);
+    cudaFreeAsync(dstatus, s);
+    FK_CUDA(cudaStreamSynchronize(s));
+    if (info) {
+        info->iters = itmax;
+        info->rel_residual = resmax;
+        info->status = worst;
+    }
+    if (rc != FKSKI_OK) return rc;
+    const int pst = status_from_bits(hst);
+    return pst != FKSKI_OK ? pst : worst;
+}
+
+int posterior_cov_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, const void *Xs, int xdtype,
+                       int64_t ns, double *cov, fkski_info *info, cudaStream_t s) {
+    if (!st || !kern || !Xs || !cov || ns < 1) return FKSKI_E_INVALID_ARG;
+    fkski_opts o;
+    if (opts) o = *opts; else fkski_default_opts(&o);
+    if (!(kern->noise_var > 0.0) || !std::isfinite(kern->noise_var)) return FKSKI_E_INVALID_ARG;
+    if (o.maxiter < 1 || !(o.rtol >= 0.0)) return FKSKI_E_INVALID_ARG;
+    if (info) memset(info, 0, sizeof(*info));
+    const bool dbl = o.precision == FKSKI_DOUBLE;
+    if (xdtype == FKSKI_F32)
+        return dbl ? posterior_cov_typed<double, float>(st, kern, &o, (const float *)Xs, ns, cov, info, s)
+                   : posterior_cov_typed<float, float>(st, kern, &o, (const float *)Xs, ns, cov, info, s);
+    if (xdtype == FKSKI_F64)
+        return dbl ? posterior_cov_typed<double, double>(st, kern, &o, (const double *)Xs, ns, cov, info, s)
+                   : posterior_cov_typed<float, double>(st, kern, &o, (const double *)Xs, ns, cov, info, s);
+    return FKSKI_E_INVALID_ARG;
+}
+
+// ------------------------------------------------------------------ rank-k covariance (EFLA)
+// Efficiently factorized Lanczos (App. B, EFLA; garbles read as in the oracle) on
+// A = W K W^T + sigma^2 I started at b = y / ||y||, in FP64 with full reorthogonalisation.
+// Lanczos vectors are kept compressed, q_i = W q_hat_i + d_i b, with P_hat_i = W^T W q_hat_i and
+// s_hat_i = (K W^T W + sigma^2 I) q_hat_i, so one B(x) and no product with W per step.  Then
+//   Q^T (W K w_x) = (P_hat + W^T b d^T)^T K w_x = G^T w_x,  G = K (P_hat + W^T b d^T),
+// and with T = L L^T the predictive covariance is approximated (ref. [ConstantTimePD]) as
+//   cov(x, x') ~ w_x^T K w_x' - (R^T w_x)^T (R^T w_x'),  R = G L^{-T}  (m x k, kept in st).
+__global__ void k_efla_next(double *__restrict__ qn, const double *__restrict__ sh, const double *__restrict__ kwb,
+                            const double *__restrict__ qprev, double c, double beta, int64_t m) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        qn[e] = sh[e] + c * kwb[e] - beta * qprev[e];
+}
+
+__global__ void k_axpy_d(double *__restrict__ y, const double *__restrict__ x, double a, int64_t m) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = fma(a, x[e], y[e]);
+}
+
+__global__ void k_scale_d(double *__restrict__ y, double a, int64_t m) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) y[e] *= a;
+}
+
+// out[j] = A[:, j] . v for the ncol columns of A (column stride m); one block per column.
+__global__ void __launch_bounds__(256) k_gemv_t(const double *__restrict__ A, int ncol, int64_t m,
+                                                 const double *__restrict__ v, double *__restrict__ out) {
+    __shared__ double sh[8];
+    const int j = blockIdx.x;
+    if (j >= ncol) return;
+    const double *a = A + (int64_t)j * m;
+    double acc = 0.0;
+    for (int64_t e = threadIdx.x; e < m; e += blockDim.x) acc = fma(a[e], v[e], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        out[j] = t;
+    }
+}
+
+// v -= A[:, 0:ncol] c (column stride m), fixed summation order per element
+__global__ void k_gemv_sub(const double *__restrict__ A, int ncol, int64_t m, const double *__restrict__ c,
+                           double *__restrict__ v) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < ncol; ++j) acc = fma(A[(int64_t)j * m + e], c[j], acc);
+        v[e] -= acc;
+    }
+}
+
+// R[e][j] = sum_l G[l][e] Linvt[l][j] (G column-major m x k, R row-major m x k)
+__global__ void k_lowrank_R(const double *__restrict__ G, const double *__restrict__ Linvt, int k, int64_t m,
+                            double *__restrict__ R) {
+    const int64_t total = m * (int64_t)k;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = t / k;
+        const int j = (int)(t % k);
+        double acc = 0.0;
+        for (int l = 0; l <= j; ++l) acc = fma(G[(int64_t)l * m + e], Linvt[(int64_t)l * k + j], acc);
+        R[t] = acc;
+    }
+}
+
+// a[i][:] = R^T w_i for test points (k-vectors, row-major ns x k); off-grid points get zeros
+template <typename TX, int D>
+__global__ void k_lowrank_a(const TX *__restrict__ Xs, int64_t ns, KeyParams kp, const double *__restrict__ R, int k,
+                            double *__restrict__ a, int64_t s1, int64_t s2, int *__restrict__ status) {
+    const int64_t total = ns * (int64_t)k;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k;
+        const int l = (int)(t % k);
+        int bad = 0;
+        // the column l of R as a grid vector is R[node * k + l]: gather with the prediction weights
+        int c[3] = {1, 1, 1};
+        TX tt[3] = {TX(0), TX(0), TX(0)};
+        int st = 0;
+#pragma unroll
+        for (int q = 0; q < D; ++q) st |= axis_cell<TX>(Xs[(int64_t)q * ns + i], kp, q, c[q], tt[q]);
+        if (st) {
+            bad |= (st & 2) ? ST_NONFINITE : ST_OUT_OF_GRID;
+            a[t] = 0.0;
+            if (l == 0) atomicOr(status, bad);
+            continue;
+        }
+        double w[3][4];
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            TX wx[4];
+            keys_weights<TX>(tt[q], wx);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) w[q][b] = (double)wx[b];
+        }
+        double acc = 0.0;
+        for (int a0 = 0; a0 < 4; ++a0)
+            for (int a1 = 0; a1 < (D > 1 ? 4 : 1); ++a1) {
+                double row = 0.0;
+                for (int a2 = 0; a2 < (D > 2 ? 4 : 1); ++a2) {
+                    int64_t node;
+                    double wv;
+                    if (D == 1) { node = c[0] - 1 + a0; wv = 1.0; }
+                    else if (D == 2) { node = (int64_t)(c[0] - 1 + a0) * s1 + (c[1] - 1 + a1); wv = 1.0; }
+                    else { node = (int64_t)(c[0] - 1 + a0) * s1 + (int64_t)(c[1] - 1 + a1) * s2 + (c[2] - 1 + a2); wv = w[2][a2]; }
+                    row = fma(wv, R[node * k + l], row);
+                }
+                acc = fma(w[0][a0] * (D > 1 ? w[1][a1] : 1.0), row, acc);
+            }
+        a[t] = acc;
+    }
+}
+
+// cov[i][j] -= a_i . a_j
+__global__ void k_lowrank_sub(const double *__restrict__ a, int k, int64_t ns, double *__restrict__ cov) {
+    const int64_t total = ns * ns;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / ns, j = t % ns;
+        double acc = 0.0;
+        for (int l = 0; l < k; ++l) acc = fma(a[i * k + l], a[j * k + l], acc);
+        cov[t] -= acc;
+    }
+}
+
+template <typename TB>
+static int efla_build(fkski_stats *st, const fkski_kernel *kern, int k, fkski_info *info, cudaStream_t s) {
+    const int64_t m = st->m;
+    const double s2 = kern->noise_var;
+    SolveWork *w;
+    FK_TRY(work_get(st, &w));
+    KgOp *kg64;
+    FK_TRY(work_kg(st, w, FKSKI_F64, &kg64));
+    FK_TRY(kgop_set(kg64, kern, -1, s));
+    const TB *band = (const TB *)st->band;
+    const unsigned gb = (unsigned)grid_blocks(m);
+    const unsigned gv = (unsigned)std::min<int64_t>(cdiv(m, 256), 152 * 8);
+    // device buffers: Qh, Ph (m x (k+1)), wtb, kwb, sh, qn, qprev, G, vectors of scalars
+    double *buf = nullptr;
+    const size_t nv = (size_t)m;
+    const size_t need = nv * (2 * (size_t)(k + 1) + 6) + 4 * (size_t)(k + 1) + 64;
+    FK_TRY(pool_alloc((void **)&buf, sizeof(double) * need, s));
+    double *Qh = buf, *Ph = Qh + nv * (k + 1), *wtb = Ph + nv * (k + 1), *kwb = wtb + nv, *sh = kwb + nv;
+    double *qn = sh + nv, *tmp = qn + nv, *tmp2 = tmp + nv, *lam = tmp2 + nv, *dsc = lam + (k + 1);
+    double *sums = dsc + 2 * (k + 1);
+    // W^T b = W^T y / ||y|| (FP64), K W^T b
+    const double ynorm = std::sqrt(std::max(st->yty, 1e-300));
+    k_convert<double><<<gv, 256, 0, s>>>(st->wty, st->dtype == FKSKI_F64, wtb, m);
+    FK_LAUNCH();
+    k_scale_d<<<gv, 256, 0, s>>>(wtb, 1.0 / ynorm, m);
+    FK_LAUNCH();
+    FK_TRY(kgop_apply(kg64, wtb, kwb, 1, nullptr, 0.0, s));
+    FK_CUDA(cudaMemsetAsync(Qh, 0, sizeof(double) * nv * 2 * (k + 1), s));
+    FK_CUDA(cudaMemsetAsync(sh, 0, sizeof(double) * nv, s));
+    std::vector<double> T((size_t)k * k, 0.0), d(k + 1, 0.0), qw(k + 1, 0.0);
+    auto dots = [&](const double *a0, const double *b0, const double *a1, const double *b1, const double *a2,
+                    const double *b2, double *out3) -> int {
+        k_dots4<double, double><<<gb, CG_T, 0, s>>>(a0, b0, a1, b1, a2, b2, nullptr, nullptr, m, 1, w->part, nullptr);
+        k_fin_sums<<<1, 128, 0, s>>>(w->part, gb, 1, 4, sums);
+        FK_LAUNCH();
+        double h[4];
+        FK_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+        FK_CUDA(cudaStreamSynchronize(s));
+        out3[0] = h[0];
+        out3[1] = h[1];
+        out3[2] = h[2];
+        return FKSKI_OK;
+    };
+    // q_1 = b: q_hat_1 = 0 (column 0), c_1 = 1
+    double c = 1.0, c_prev = 0.0, beta = 0.0;
+    d[0] = 1.0;
+    qw[0] = 0.0;  // q_hat_1 . W^T b
+    int kk = k;
+    double *qprev = tmp2;
+    FK_CUDA(cudaMemsetAsync(qprev, 0, sizeof(double) * nv, s));
+    for (int i = 0; i < k; ++i) {
+        double *qi = Qh + nv * i, *pi = Ph + nv * i;
+        // q_{i+1} = A q_i - beta_i q_{i-1}  (compressed: s_hat_i + c_i K W^T b - beta_i q_hat_{i-1})
+        k_efla_next<<<gv, 256, 0, s>>>(qn, sh, kwb, qprev, c, beta, m);
+        FK_LAUNCH();
+        const double cn0 = s2 * c - beta * c_prev;
+        double t3[3];
+        FK_TRY(dots(pi, qn, qn, wtb, qi, wtb, t3));  // P_hat_i.qn, qn.W^T b, q_hat_i.W^T b
+        const double alpha = t3[0] + c * cn0 + c * t3[1] + cn0 * t3[2];
+        T[(size_t)i * k + i] = alpha;
+        if (i == k - 1) break;
+        // q_{i+1} -= alpha q_i; then two passes of full reorthogonalisation against q_1..q_i
+        k_axpy_d<<<gv, 256, 0, s>>>(qn, qi, -alpha, m);
+        FK_LAUNCH();
+        double cn = cn0 - alpha * c;
+        for (int pass = 0; pass < 2; ++pass) {
+            k_gemv_t<<<i + 1, 256, 0, s>>>(Ph, i + 1, m, qn, lam);  // P_hat_j . q_hat_{i+1}
+            FK_LAUNCH();
+            FK_TRY(dots(qn, wtb, qn, wtb, qn, wtb, t3));             // q_hat_{i+1} . W^T b
+            std::vector<double> L(i + 1);
+            FK_CUDA(cudaMemcpyAsync(L.data(), lam, sizeof(double) * (i + 1), cudaMemcpyDeviceToHost, s));
+            FK_CUDA(cudaStreamSynchronize(s));
+            double dl = 0.0;
+            for (int j = 0; j <= i; ++j) {
+                L[j] += d[j] * cn + d[j] * t3[0] + cn * qw[j];
+                dl += d[j] * L[j];
+            }
+            FK_CUDA(cudaMemcpyAsync(lam, L.data(), sizeof(double) * (i + 1), cudaMemcpyHostToDevice, s));
+            k_gemv_sub<<<gv, 256, 0, s>>>(Qh, i + 1, m, lam, qn);
+            FK_LAUNCH();
+            cn -= dl;
+        }
+        // B(q_hat_{i+1}): P_hat = W^T W q_hat, s_hat = K P_hat + sigma^2 q_hat
+        double *pn = Ph + nv * (i + 1);
+        FK_TRY((launch_spmv<TB, double>(band, st->grid, qn, pn, m, 1, nullptr, 1, nullptr, nullptr, gb, s)));
+        FK_TRY(kgop_apply(kg64, pn, sh, 1, qn, s2, s));
+        FK_TRY(dots(pn, qn, qn, wtb, qn, qn, t3));  // P.q, q.W^T b, q.q
+        const double b2 = t3[0] + cn * cn + 2.0 * cn * t3[1];
+        const double scale_ref = std::fabs(alpha) + std::fabs(beta) + 1e-300;
+        if (!(b2 > 0.0) || std::sqrt(b2) <= 1e-10 * scale_ref) {  // invariant Krylov space
+            kk = i + 1;
+            break;
+        }
+        const double bn = std::sqrt(b2);
+        T[(size_t)i * k + i + 1] = T[(size_t)(i + 1) * k + i] = bn;
+        FK_CUDA(cudaMemcpyAsync(qprev, qi, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+        k_scale_d<<<gv, 256, 0, s>>>(qn, 1.0 / bn, m);
+        k_scale_d<<<gv, 256, 0, s>>>(pn, 1.0 / bn, m);
+        k_scale_d<<<gv, 256, 0, s>>>(sh, 1.0 / bn, m);
+        FK_LAUNCH();
+        FK_CUDA(cudaMemcpyAsync(Qh + nv * (i + 1), qn, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+        c_prev = c;
+        c = cn / bn;
+        beta = bn;
+        d[i + 1] = c;
+        qw[i + 1] = t3[1] / bn;
+    }
+    // T = L L^T (host), Linv^T
+    std::vector<double> Lm((size_t)kk * kk, 0.0), Li((size_t)kk * kk, 0.0);
+    for (int j = 0; j < kk; ++j) {
+        double sum = T[(size_t)j * k + j];
+        for (int l = 0; l < j; ++l) sum -= Lm[(size_t)j * kk + l] * Lm[(size_t)j * kk + l];
+        if (!(sum > 0.0)) {
+            cudaFreeAsync(buf, s);
+            return FKSKI_E_BREAKDOWN;
+        }
+        Lm[(size_t)j * kk + j] = std::sqrt(sum);
+        for (int r = j + 1; r < kk; ++r) {
+            double v = T[(size_t)r * k + j];
+            for (int l = 0; l < j; ++l) v -= Lm[(size_t)r * kk + l] * Lm[(size_t)j * kk + l];
+            Lm[(size_t)r * kk + j] = v / Lm[(size_t)j * kk + j];
+        }
+    }
+    // Li = L^{-1} (lower); Linv^T[l][j] = Li[j][l]
+    for (int j = 0; j < kk; ++j) {
+        Li[(size_t)j * kk + j] = 1.0 / Lm[(size_t)j * kk + j];
+        for (int r = j + 1; r < kk; ++r) {
+            double v = 0.0;
+            for (int l = j; l < r; ++l) v += Lm[(size_t)r * kk + l] * Li[(size_t)l * kk + j];
+            Li[(size_t)r * kk + j] = -v / Lm[(size_t)r * kk + r];
+        }
+    }
+    std::vector<double> Lt((size_t)kk * kk, 0.0);
+    for (int l = 0; l < kk; ++l)
+        for (int j = 0; j < kk; ++j) Lt[(size_t)l * kk + j] = Li[(size_t)j * kk + l];
+    // G = K (P_hat + W^T b d^T), column-major m x kk (overwrites Q_hat's storage)
+    double *G = Qh;
+    FK_CUDA(cudaMemcpyAsync(G, Ph, sizeof(double) * nv * kk, cudaMemcpyDeviceToDevice, s));
+    for (int j = 0; j < kk; ++j) {
+        k_axpy_d<<<gv, 256, 0, s>>>(G + nv * j, wtb, d[j], m);
+        FK_LAUNCH();
+    }
+    FK_TRY(kgop_apply(kg64, G, Ph, kk, nullptr, 0.0, s));  // Ph <- K G
+    double *dLt = nullptr;
+    FK_TRY(pool_alloc((void **)&dLt, sizeof(double) * kk * kk, s));
+    FK_CUDA(cudaMemcpyAsync(dLt, Lt.data(), sizeof(double) * kk * kk, cudaMemcpyHostToDevice, s));
+    if (st->lowrank) cudaFree(st->lowrank);
+    st->lowrank = nullptr;
+    FK_TRY(dev_alloc((void **)&st->lowrank, sizeof(double) * nv * kk));
+    const unsigned gr = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv((int64_t)nv * kk, 256), 152 * 16));
+    k_lowrank_R<<<gr, 256, 0, s>>>(Ph, dLt, kk, m, st->lowrank);
+    FK_LAUNCH();
+    cudaFreeAsync(dLt, s);
+    cudaFreeAsync(buf, s);
+    FK_CUDA(cudaStreamSynchronize(s));
+    st->lowrank_k = kk;
+    st->lowrank_kreq = k;
+    st->lowrank_kern = *kern;
+    if (info) {
+        info->iters = kk;
+        info->status = FKSKI_OK;
+    }
+    return FKSKI_OK;
+}
+
+static bool same_kernel(const fkski_kernel &a, const fkski_kernel &b, int d) {
+    if (a.type != b.type || a.outputscale != b.outputscale || a.noise_var != b.noise_var) return false;
+    for (int k = 0; k < d; ++k)
+        if (a.lengthscale[k] != b.lengthscale[k]) return false;
+    return true;
+}
+
+template <typename TX>
+static int lowrank_eval(fkski_stats *st, const fkski_kernel *kern, const TX *Xs, int64_t ns, double *cov, cudaStream_t s) {
+    const int64_t m = st->m;
+    const int d = st->d, k = st->lowrank_k;
+    const KeyParams kp = make_key_params(st->grid);
+    const int64_t M1 = st->grid.M[1], M2 = st->grid.M[2];
+    const int64_t s1 = d == 2 ? M1 : M1 * M2, s2 = M2;
+    SolveWork *w;
+    FK_TRY(work_get(st, &w));
+    KgOp *kg64;
+    FK_TRY(work_kg(st, w, FKSKI_F64, &kg64));
+    FK_TRY(kgop_set(kg64, kern, -1, s));
+    double *e = nullptr, *kw = nullptr, *a = nullptr;
+    int *dstatus = nullptr;
+    const size_t nR = (size_t)COV_R * m;
+    FK_TRY(pool_alloc((void **)&e, sizeof(double) * nR, s));
+    FK_TRY(pool_alloc((void **)&kw, sizeof(double) * nR, s));
+    FK_TRY(pool_alloc((void **)&a, sizeof(double) * (size_t)ns * k, s));
+    FK_TRY(pool_alloc((void **)&dstatus, sizeof(int), s));
+    FK_CUDA(cudaMemsetAsync(dstatus, 0, sizeof(int), s));
+    // prior w_i^T K w_j, a block of test points per K_G product
+    for (int64_t j0 = 0; j0 < ns; j0 += COV_R) {
+        const int R = (int)std::min<int64_t>(COV_R, ns - j0);
+        FK_CUDA(cudaMemsetAsync(e, 0, sizeof(double) * R * m, s));
+        if (d == 1) k_scatter_w<TX, 1><<<(R + 63) / 64, 64, 0, s>>>(Xs, ns, j0, R, kp, e, m, s1, s2, dstatus);
+        else if (d == 2) k_scatter_w<TX, 2><<<(R + 63) / 64, 64, 0, s>>>(Xs, ns, j0, R, kp, e, m, s1, s2, dstatus);
+        else k_scatter_w<TX, 3><<<(R + 63) / 64, 64, 0, s>>>(Xs, ns, j0, R, kp, e, m, s1, s2, dstatus);
+        FK_LAUNCH();
+        FK_TRY(kgop_apply(kg64, e, kw, R, nullptr, 0.0, s));
+        const unsigned gg = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(ns * R, 256), 152 * 16));
+        if (d == 1) k_cov_gather<TX, 1><<<gg, 256, 0, s>>>(Xs, ns, kp, kw, R, m, j0, cov, s1, s2);
+        else if (d == 2) k_cov_gather<TX, 2><<<gg, 256, 0, s>>>(Xs, ns, kp, kw, R, m, j0, cov, s1, s2);
+        else k_cov_gather<TX, 3><<<gg, 256, 0, s>>>(Xs, ns, kp, kw, R, m, j0, cov, s1, s2);
+        FK_LAUNCH();
+    }
+    const unsigned ga = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(ns * k, 256), 152 * 16));
+    if (d == 1) k_lowrank_a<TX, 1><<<ga, 256, 0, s>>>(Xs, ns, kp, st->lowrank, k, a, s1, s2, dstatus);
+    else if (d == 2) k_lowrank_a<TX, 2><<<ga, 256, 0, s>>>(Xs, ns, kp, st->lowrank, k, a, s1, s2, dstatus);
+    else k_lowrank_a<TX, 3><<<ga, 256, 0, s>>>(Xs, ns, kp, st->lowrank, k, a, s1, s2, dstatus);
+    FK_LAUNCH();
+    const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(ns * ns, 256), 152 * 16));
+    k_lowrank_sub<<<gs, 256, 0, s>>>(a, k, ns, cov);
+    FK_LAUNCH();
+    int hst = 0;
+    FK_CUDA(cudaMemcpyAsync(&hst, dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(e, s);
+    cudaFreeAsync(kw, s);
+    cudaFreeAsync(a, s);
+    cudaFreeAsync(dstatus, s);
+    FK_CUDA(cudaStreamSynchronize(s));
+    return status_from_bits(hst);
+}
+
+int posterior_cov_lowrank_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, int k, const void *Xs,
+                               int xdtype, int64_t ns, double *cov, fkski_info *info, cudaStream_t s) {
+    (void)opts;
+    if (!st || !kern || k < 1 || ns < 0 || (ns > 0 && (!Xs || !cov))) return FKSKI_E_INVALID_ARG;
+    if (!(kern->noise_var > 0.0) || !std::isfinite(kern->noise_var)) return FKSKI_E_INVALID_ARG;
+    if (xdtype != FKSKI_F32 && xdtype != FKSKI_F64) return FKSKI_E_INVALID_ARG;
+    if (info) memset(info, 0, sizeof(*info));
+    if (!st->lowrank || st->lowrank_kreq != k || !same_kernel(st->lowrank_kern, *kern, st->d)) {
+        const int rc = st->dtype == FKSKI_F32 ? efla_build<float>(st, kern, k, info, s) : efla_build<double>(st, kern, k, info, s);
+        if (rc != FKSKI_OK) return rc;
+    } else if (info) {
+        info->iters = st->lowrank_k;
+    }
+    if (ns == 0) return FKSKI_OK;
+    return xdtype == FKSKI_F32 ? lowrank_eval<float>(st, kern, (const float *)Xs, ns, cov, s)
+                               : lowrank_eval<double>(st, kern, (const double *)Xs, ns, cov, s);
 }
 }  // namespace fk
 

@@ -109,6 +109,18 @@ def sine_1d(n: int = 10_000, seed: int = 0, M: int = 1000) -> Problem:
                    rtol=1e-10, Xstar=xs)
 
 
+def sine_sweep(n: int, m: int, seed: int = 0) -> Problem:
+    """Sec. 5's per-iteration benchmark data: a sine with two periods on [0, 1],
+    y = sin(4 pi x) + N(0, 0.25), x ~ U[0,1] FP32, m grid nodes spanning [0, 1]; RBF l = 0.1,
+    s = 1, sigma^2 = 0.25."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0.0, 1.0, n)
+    y = np.sin(4 * np.pi * x) + rng.normal(0.0, 0.5, n)
+    grid = grid_for_box([0.0], [1.0], (m,))
+    return Problem(f"sine_sweep_{n}_{m}", x[None, :].astype(np.float32), y.astype(np.float32), grid,
+                   Kernel(RBF, (0.1,), 1.0, 0.25), rtol=1e-2, Xstar=None)
+
+
 # ---------------------------------------------------------------- Gaussian mixture (d = 2)
 
 def gmm_2d(n: int = 1_000_000, seed: int = 0, M=(128, 128)) -> Problem:

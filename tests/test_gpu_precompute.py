@@ -139,3 +139,24 @@ def test_band_mvm_matches_oracle(fk, oracle_mod):
     U = fk.band_mvm(st, _tt(V)).cpu().numpy()
     Uref = core.band_matvec(grid, ref["band"], V.astype(np.float64).T).T
     assert rel_fro(U, Uref) <= 2e-6
+
+
+@pytest.mark.parametrize("d,M", [(1, (400,)), (2, (36, 44)), (3, (12, 10, 16)), (3, (9, 8, 10))])
+@pytest.mark.parametrize("R", [1, 2, 5, 9])
+def test_band_mvm_paths(fk, oracle_mod, d, M, R):
+    """Banded W^T W products on every kernel path: the symmetric half-band form (one FP32 rhs,
+    M_last a multiple of 4), the vectorised full-band form (several rhs, groups of <= 8), the
+    generic form (M_last not a multiple of 4) and FP64 vectors."""
+    from oracle import core
+    grid, X, y = problem(d, M, 20000, seed=7)
+    st = fk.precompute(_tt(X), _tt(y), grid)
+    ref = core.precompute(grid, X, y)
+    V = np.random.default_rng(R).normal(size=(R, grid.m))
+    Uref = core.band_matvec(grid, ref["band"], V.T).T
+    U32 = fk.band_mvm(st, _tt(V.astype(np.float32))).cpu().numpy()
+    assert rel_fro(U32, Uref) <= 2e-6
+    U64 = fk.band_mvm(st, _tt(V)).cpu().numpy()
+    assert rel_fro(U64, Uref) <= 2e-6  # FP32 band values (statistics of FP32 inputs)
+    # one rhs alone (half band when eligible) equals the same rhs inside the batch
+    u0 = fk.band_mvm(st, _tt(V[:1].astype(np.float32))).cpu().numpy()
+    assert rel_fro(u0, U32[:1]) <= 1e-6

@@ -1,0 +1,51 @@
+"""Plain SKI baseline (fkski_ski_solve: n-space CG, Alg. 1 from x0 = 0) against the oracle's
+n-space CG and against the factorized solver.
+
+Bars: posterior mean within 1e-4 relative L2 of the oracle at equal rtol (FP64 inputs: also the
+iteration count within max(3, 5%), the same recurrence up to rounding); equal means to 1e-4 with
+the factorized Alg. 3 solve (Prop. 1 / Theorem 1: the same iterates in exact arithmetic)."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import problem, rel_fro
+from paper_2101_11751_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _tt(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("d,M,n,kern,dtype,rtol", [
+    (1, (500,), 8000, synth.Kernel(synth.RBF, (0.05,), 1.0, 0.01), np.float64, 1e-9),
+    (2, (30, 26), 12000, synth.Kernel(synth.RBF, (0.12, 0.15), 1.0, 0.02), np.float64, 1e-8),
+    (2, (24, 25), 9000, synth.Kernel(synth.MATERN52, (0.1, 0.12), 1.0, 0.02), np.float64, 1e-8),
+    (3, (12, 11, 13), 15000, synth.Kernel(synth.RBF, (0.2, 0.25, 0.2), 1.0, 0.05), np.float64, 1e-8),
+    (2, (40, 36), 30000, synth.Kernel(synth.RBF, (0.1, 0.1), 1.0, 0.05), np.float32, 1e-4),
+])
+def test_ski_matches_oracle_cg(fk, oracle_mod, d, M, n, kern, dtype, rtol):
+    from oracle import core
+    grid, X, y = problem(d, M, n, seed=51, dtype=dtype)
+    st = fk.precompute(_tt(X), _tt(y), grid, keep_points=True)
+    a, v, info = fk.ski_solve(st, kern, rtol=rtol, maxiter=6000)
+    a_ref, v_ref, it_ref, _ = core.nspace_mean(grid, kern, X.astype(np.float64), y.astype(np.float64), rtol=rtol,
+                                               x0_mode=0)
+    tol = 1e-6 if dtype == np.float64 else 1e-4
+    assert rel_fro(v.double().cpu().numpy(), v_ref) <= tol
+    assert rel_fro(a.double().cpu().numpy(), a_ref) <= max(tol, 1e-5)
+    if dtype == np.float64:
+        assert abs(info["iters"] - it_ref) <= max(3, 0.05 * it_ref), (info["iters"], it_ref)
+    # the factorized solver gives the same posterior mean
+    _, v_f, _ = fk.solve(st, kern, rtol=rtol, maxiter=6000, x0_mode=0,
+                         precision=fk.DOUBLE if dtype == np.float64 else fk.MIXED)
+    assert rel_fro(v.double().cpu().numpy(), v_f.double().cpu().numpy()) <= (1e-6 if dtype == np.float64 else 3e-4)
+
+
+def test_ski_needs_points(fk):
+    grid, X, y = problem(2, (16, 16), 1000, seed=1)
+    st = fk.precompute(_tt(X), _tt(y), grid)
+    with pytest.raises(fk.FkskiError) as e:
+        fk.ski_solve(st, synth.Kernel(synth.RBF, (0.2, 0.2), 1.0, 0.05))
+    assert e.value.code == fk.E_UNSUPPORTED
