@@ -490,6 +490,18 @@ def slq_logdet(mv, Z: np.ndarray, rtol: float, maxiter: int = 10000):
     return float(np.mean(ests)), np.array(xs), its
 
 
+def slq_logdet_lanczos(mv, Z: np.ndarray, k: int):
+    """Stochastic Lanczos quadrature with k steps of Lanczos with full reorthogonalisation
+    (Alg. 6) per probe, the route the paper's factorized Lanczos (FLA / EFLA, App. B) serves:
+    logdet A ~ mean_j ||z_j||^2 e_1^T log(T_j) e_1.  Returns the estimate and the per-probe terms."""
+    terms = []
+    for j in range(Z.shape[0]):
+        z = np.asarray(Z[j], dtype=np.float64)
+        _, T = lanczos(mv, z, k)
+        terms.append(float(z @ z) * quad_e1(T, np.log))
+    return float(np.mean(terms)), np.array(terms)
+
+
 def theta_names(kernel):
     return [("ell", k) for k in range(len(kernel.lengthscale))] + ["scale", "noise"]
 

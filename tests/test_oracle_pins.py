@@ -318,6 +318,24 @@ def test_lanczos_lowrank_cov_exact_at_full_rank(oracle_mod):
     assert np.all(np.diag(cov5) <= prior + 1e-12) and np.all(np.diag(cov5) >= np.diag(ref) - 1e-9)
 
 
+def test_slq_lanczos_unit_probes_exact(oracle_mod):
+    """SLQ by Lanczos with full reorthogonalisation: probes sqrt(n) e_i run to an invariant
+    Krylov space give the exact log-determinant (Gauss quadrature is exact there); a few Rademacher
+    probes land near it."""
+    from oracle import core
+    grid, X, y = _tiny(2, n=50, seed=14)
+    kern = synth.Kernel(synth.RBF, (0.3, 0.3), 1.0, 0.1)
+    W = core.w_csr(grid, X)
+    mv = core.ski_operator(grid, kern, W)
+    n = X.shape[1]
+    exact = core.ski_inference_dense(grid, kern, X, y, X[:, :2])["logdet"]
+    est, terms = core.slq_logdet_lanczos(mv, math.sqrt(n) * np.eye(n), k=n)
+    assert est == pytest.approx(exact, rel=1e-9)
+    Z = np.stack([core.rademacher(3, p, n) for p in range(64)])
+    est64, _ = core.slq_logdet_lanczos(mv, Z, k=30)
+    assert est64 == pytest.approx(exact, rel=0.05)
+
+
 def test_nspace_cg_mean_matches_dense(oracle_mod):
     from oracle import core
     grid, X, y = _tiny(2, n=150, seed=9)
