@@ -240,6 +240,17 @@ FKSKI_API int fkski_solve(fkski_stats *st, const fkski_kernel *kern, const fkski
 FKSKI_API int fkski_predict(const fkski_stats *st, const void *v, int vdtype, const void *Xstar, int xdtype,
                   int64_t nstar, void *mu_out, void *stream);
 
+/* log det (W K_G W^T + sigma^2 I) by stochastic Lanczos quadrature with the efficiently factorized
+ * Lanczos method (App. B, EFLA; refs [ScalableLD], [GPyTorchBM]): for each of the precompute's
+ * probes z_p, k steps of EFLA started at z_p (FP64, full reorthogonalisation) give T_p, and
+ * logdet ~ mean_p ||z_p||^2 e_1^T log(T_p) e_1 (Ritz values clamped at sigma^2).  The alternative
+ * to the CG-coefficient quadrature inside fkski_loglik_forward, with reorthogonalised Lanczos
+ * vectors.  Needs n_probes >= 1 at precompute time.  logdet_out (host); terms (host, n_probes,
+ * may be NULL) receives each probe's term.  info->iters: the most Lanczos steps taken.  Returns
+ * OK, BREAKDOWN (QL did not converge), INVALID_ARG, OOM, CUDA.  Synchronizes the stream. */
+FKSKI_API int fkski_logdet_lanczos(fkski_stats *st, const fkski_kernel *kern, int k, double *logdet_out,
+                                   double *terms, fkski_info *info, void *stream);
+
 /* Plain SKI posterior mean (Def. 1) by n-space CG (Alg. 1) on W K_G W^T + sigma^2 I from x0 = 0:
  * the O(n + m log m)-per-iteration method the paper's factorized solvers replace (Sec. 5,
  * Fig. 2, Table 1), for comparison.  Needs the points kept by the precompute (opts.keep_points);

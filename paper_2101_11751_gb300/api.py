@@ -84,6 +84,7 @@ SIGNATURES = {
     "fkski_solve": (ctypes.c_int, [P, ctypes.POINTER(CKernel), ctypes.POINTER(COpts), P, P,
                                    ctypes.POINTER(CInfo), P]),
     "fkski_predict": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int64, P, P]),
+    "fkski_logdet_lanczos": (ctypes.c_int, [P, ctypes.POINTER(CKernel), ctypes.c_int, PD, PD, ctypes.POINTER(CInfo), P]),
     "fkski_ski_solve": (ctypes.c_int, [P, ctypes.POINTER(CKernel), ctypes.POINTER(COpts), P, P,
                                        ctypes.POINTER(CInfo), P]),
     "fkski_posterior_cov": (ctypes.c_int, [P, ctypes.POINTER(CKernel), ctypes.POINTER(COpts), P, ctypes.c_int,
@@ -338,6 +339,21 @@ def predict(st: Stats, v: torch.Tensor, Xstar: torch.Tensor, stream=None) -> tor
     _check(_lib.fkski_predict(st.handle, _ptr(v), _dtype_code(v), _ptr(Xstar), _dtype_code(Xstar),
                               Xstar.shape[1], _ptr(mu), _stream(stream)), "fkski_predict")
     return mu
+
+
+def logdet_lanczos(st: Stats, kernel, k: int, stream=None):
+    """fkski_logdet_lanczos: SLQ log-determinant with k EFLA steps per probe; (estimate, terms)."""
+    load()
+    import numpy as np
+    npb = st.info()["n_probes"]
+    L = ctypes.c_double()
+    terms = np.zeros(max(npb, 1))
+    inf = CInfo()
+    k_ = c_kernel(kernel)
+    _check(_lib.fkski_logdet_lanczos(st.handle, ctypes.byref(k_), k, ctypes.byref(L),
+                                     terms.ctypes.data_as(PD), ctypes.byref(inf), _stream(stream)),
+           "fkski_logdet_lanczos")
+    return L.value, terms[:npb], dict(steps=inf.iters)
 
 
 def ski_solve(st: Stats, kernel, rtol: float = 1e-6, maxiter: int = 1000, check_every: int = 16, stream=None,

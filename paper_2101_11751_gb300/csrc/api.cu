@@ -315,6 +315,11 @@ int fkski_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opt
     return solve_impl(st, kern, opts, a_out, v_out, info, S(stream));
 }
 
+int fkski_logdet_lanczos(fkski_stats *st, const fkski_kernel *kern, int k, double *logdet_out, double *terms,
+                         fkski_info *info, void *stream) {
+    return logdet_lanczos_impl(st, kern, k, logdet_out, terms, info, S(stream));
+}
+
 int fkski_ski_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, void *a_out, void *v_out,
                     fkski_info *info, void *stream) {
     return ski_solve_impl(st, kern, opts, a_out, v_out, info, S(stream));

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <vector>
 #include <stdint.h>
 
 #include <cmath>
@@ -152,6 +153,10 @@ int posterior_cov_lowrank_impl(fkski_stats *st, const fkski_kernel *kern, const 
                                const void *Xs, int xdtype, int64_t ns, double *cov, fkski_info *info, cudaStream_t s);
 int ski_solve_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, void *a_out, void *v_out,
                    fkski_info *info, cudaStream_t s);
+int efla_probe_tridiag(fkski_stats *st, const fkski_kernel *kern, int k, int probe, std::vector<double> &dg,
+                       std::vector<double> &of, fkski_info *info, cudaStream_t s);
+int logdet_lanczos_impl(fkski_stats *st, const fkski_kernel *kern, int k, double *logdet, double *terms,
+                        fkski_info *info, cudaStream_t s);
 int solve_batched_impl(int P, fkski_stats *const *sts, const fkski_kernel *kernels, const fkski_opts *opts,
                        void *const *a_out, void *const *v_out, fkski_info *info, cudaStream_t s);
 int predict_batched_impl(int P, const fkski_stats *const *st, const void *const *v, int vdtype, const void *const *Xs,

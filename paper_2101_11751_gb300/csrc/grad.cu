@@ -45,32 +45,12 @@ int spmv_for_grad(fkski_stats *st, const void *x, void *u, int R, int dtype, cud
 // while carrying the first row of the eigenvector matrix.  Output est[p] = rho0 sum_l z_l^2 log lam_l.
 constexpr int SLQ_MAXK = 4096;
 
-// A = W K W^T + sigma^2 I has spectrum in [sigma^2, inf), so a Ritz value below sigma^2 (left by
-// rounding in the FP32 Krylov recurrences) is clamped to sigma^2.
-__global__ void k_slq(const double *__restrict__ ha, const double *__restrict__ hb, const int *__restrict__ iters,
-                      const double *__restrict__ S, int R, double sig2, double *__restrict__ est,
-                      int *__restrict__ status) {
-    extern __shared__ double sm[];
-    const int r = 1 + blockIdx.x;  // probe rhs
-    const int k = iters[r];
-    double *dg = sm;           // diagonal
-    double *of = sm + k + 1;   // off-diagonal (of[i] couples i, i+1)
-    double *z = of + k + 1;    // first eigenvector row
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        const double a = ha[(int64_t)i * R + r];
-        double di = 1.0 / a;
-        if (i > 0) di += hb[(int64_t)(i - 1) * R + r] / ha[(int64_t)(i - 1) * R + r];
-        dg[i] = di;
-        of[i] = (i + 1 < k) ? sqrt(hb[(int64_t)i * R + r]) / a : 0.0;
-        z[i] = (i == 0) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    const double rho0 = S[GF_RHO0 * R + r];
-    if (k == 0) {
-        est[blockIdx.x] = 0.0;
-        return;
-    }
+// e_1^T log(T) e_1 for the symmetric tridiagonal T (diagonal dg[0..k), couplings of[i] between
+// i and i+1, z = e_1 on entry): implicit-shift QL on (dg, of), rotating the first row z of the
+// eigenvector matrix along; Ritz values are clamped at sig2 (the spectrum of A starts there).
+// dg, of and z are overwritten.  Returns the quadrature; *fail when QL did not converge or a
+// Ritz value is not finite.
+__device__ double tridiag_e1_log(double *dg, double *of, double *z, int k, double sig2, int *fail_out) {
     const double eps = 2.220446049250313e-16;
     int fail = 0;
     for (int l = 0; l < k; ++l) {
@@ -119,8 +99,51 @@ __global__ void k_slq(const double *__restrict__ ha, const double *__restrict__ 
         if (!isfinite(dg[i])) fail = 1;
         else acc += z[i] * z[i] * log(fmax(dg[i], sig2));
     }
+    *fail_out = fail;
+    return acc;
+}
+
+// A = W K W^T + sigma^2 I has spectrum in [sigma^2, inf), so a Ritz value below sigma^2 (left by
+// rounding in the FP32 Krylov recurrences) is clamped to sigma^2.
+__global__ void k_slq(const double *__restrict__ ha, const double *__restrict__ hb, const int *__restrict__ iters,
+                      const double *__restrict__ S, int R, double sig2, double *__restrict__ est,
+                      int *__restrict__ status) {
+    extern __shared__ double sm[];
+    const int r = 1 + blockIdx.x;  // probe rhs
+    const int k = iters[r];
+    double *dg = sm;           // diagonal
+    double *of = sm + k + 1;   // off-diagonal (of[i] couples i, i+1)
+    double *z = of + k + 1;    // first eigenvector row
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const double a = ha[(int64_t)i * R + r];
+        double di = 1.0 / a;
+        if (i > 0) di += hb[(int64_t)(i - 1) * R + r] / ha[(int64_t)(i - 1) * R + r];
+        dg[i] = di;
+        of[i] = (i + 1 < k) ? sqrt(hb[(int64_t)i * R + r]) / a : 0.0;
+        z[i] = (i == 0) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double rho0 = S[GF_RHO0 * R + r];
+    if (k == 0) {
+        est[blockIdx.x] = 0.0;
+        return;
+    }
+    int fail = 0;
+    const double acc = tridiag_e1_log(dg, of, z, k, sig2, &fail);
     if (fail) atomicOr(status, ST_BREAKDOWN);
     est[blockIdx.x] = rho0 * acc;
+}
+
+// One tridiagonal's quadrature (single thread: the QL sweep is sequential).
+__global__ void k_tridiag_quad(double *dg, double *of, double *z, int k, double sig2, double scale,
+                               double *__restrict__ out, int *__restrict__ status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = 0; i < k; ++i) z[i] = i == 0 ? 1.0 : 0.0;
+    int fail = 0;
+    const double acc = tridiag_e1_log(dg, of, z, k, sig2, &fail);
+    if (fail) atomicOr(status, ST_BREAKDOWN);
+    *out = scale * acc;
 }
 
 // dots of row pairs: out[r] = sum_i a[r][i] b[r][i]; per-block FP64 partials then a fixed-order sum
@@ -380,4 +403,47 @@ int loglik_backward_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_
                                        : backward_typed<float>(st, kern, &o, grad, info, s);
 }
 
+
+// log det A by stochastic Lanczos quadrature over the precompute's probes, each with k steps of
+// EFLA (App. B) -- the factorized-Lanczos alternative to the CG-coefficient SLQ of the
+// log-likelihood: logdet ~ mean_p ||z_p||^2 e_1^T log(T_p) e_1.
+int logdet_lanczos_impl(fkski_stats *st, const fkski_kernel *kern, int k, double *logdet, double *terms,
+                        fkski_info *info, cudaStream_t s) {
+    if (!st || !kern || !logdet || k < 1) return FKSKI_E_INVALID_ARG;
+    if (st->nprobes < 1) return FKSKI_E_INVALID_ARG;
+    if (!(kern->noise_var > 0.0)) return FKSKI_E_INVALID_ARG;
+    if (info) memset(info, 0, sizeof(*info));
+    double *dbuf = nullptr;
+    int *dstat = nullptr;
+    FK_TRY(pool_alloc((void **)&dbuf, sizeof(double) * (3 * (size_t)(k + 1) + 1), s));
+    FK_TRY(pool_alloc((void **)&dstat, sizeof(int), s));
+    FK_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int), s));
+    double sum = 0.0;
+    int rc = FKSKI_OK;
+    for (int p = 0; p < st->nprobes && rc == FKSKI_OK; ++p) {
+        std::vector<double> dg, of;
+        rc = efla_probe_tridiag(st, kern, k, p, dg, of, info, s);
+        if (rc != FKSKI_OK) break;
+        const int kk = (int)dg.size();
+        double *ddg = dbuf, *dof = dbuf + (k + 1), *dz = dof + (k + 1), *dout = dz + (k + 1);
+        FK_CUDA(cudaMemcpyAsync(ddg, dg.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, s));
+        FK_CUDA(cudaMemcpyAsync(dof, of.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, s));
+        k_tridiag_quad<<<1, 32, 0, s>>>(ddg, dof, dz, kk, kern->noise_var, st->ztz[p], dout, dstat);
+        FK_LAUNCH();
+        double t = 0.0;
+        FK_CUDA(cudaMemcpyAsync(&t, dout, sizeof(double), cudaMemcpyDeviceToHost, s));
+        FK_CUDA(cudaStreamSynchronize(s));
+        if (terms) terms[p] = t;
+        sum += t;
+    }
+    int hst = 0;
+    if (rc == FKSKI_OK) FK_CUDA(cudaMemcpyAsync(&hst, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(dbuf, s);
+    cudaFreeAsync(dstat, s);
+    FK_CUDA(cudaStreamSynchronize(s));
+    if (rc != FKSKI_OK) return rc;
+    *logdet = sum / st->nprobes;
+    if (hst & ST_BREAKDOWN) return FKSKI_E_BREAKDOWN;
+    return FKSKI_OK;
+}
 }  // namespace fk

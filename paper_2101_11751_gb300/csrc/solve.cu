@@ -2281,7 +2281,11 @@ __global__ void k_lowrank_sub(const double *__restrict__ a, int k, int64_t ns, d
 }
 
 template <typename TB>
-static int efla_build(fkski_stats *st, const fkski_kernel *kern, int k, fkski_info *info, cudaStream_t s) {
+// probe < 0: start at y and build the covariance factor R in st.  probe >= 0: start at the probe
+// z_probe (its W^T z and ||z||^2 from the precompute) and return the tridiagonal T (diagonal,
+// couplings) for a Lanczos quadrature instead.
+static int efla_build(fkski_stats *st, const fkski_kernel *kern, int k, fkski_info *info, cudaStream_t s,
+                      int probe = -1, std::vector<double> *tri_dg = nullptr, std::vector<double> *tri_of = nullptr) {
     const int64_t m = st->m;
     const double s2 = kern->noise_var;
     SolveWork *w;
@@ -2300,9 +2304,11 @@ static int efla_build(fkski_stats *st, const fkski_kernel *kern, int k, fkski_in
     double *Qh = buf, *Ph = Qh + nv * (k + 1), *wtb = Ph + nv * (k + 1), *kwb = wtb + nv, *sh = kwb + nv;
     double *qn = sh + nv, *tmp = qn + nv, *tmp2 = tmp + nv, *lam = tmp2 + nv, *dsc = lam + (k + 1);
     double *sums = dsc + 2 * (k + 1);
-    // W^T b = W^T y / ||y|| (FP64), K W^T b
-    const double ynorm = std::sqrt(std::max(st->yty, 1e-300));
-    k_convert<double><<<gv, 256, 0, s>>>(st->wty, st->dtype == FKSKI_F64, wtb, m);
+    // W^T b = W^T b_in / ||b_in|| (FP64), K W^T b
+    const size_t es = st->dtype == FKSKI_F64 ? 8 : 4;
+    const void *src = probe < 0 ? st->wty : (const void *)((const char *)st->wtz + (size_t)probe * m * es);
+    const double ynorm = std::sqrt(std::max(probe < 0 ? st->yty : st->ztz[probe], 1e-300));
+    k_convert<double><<<gv, 256, 0, s>>>(src, st->dtype == FKSKI_F64, wtb, m);
     FK_LAUNCH();
     k_scale_d<<<gv, 256, 0, s>>>(wtb, 1.0 / ynorm, m);
     FK_LAUNCH();
@@ -2387,6 +2393,18 @@ static int efla_build(fkski_stats *st, const fkski_kernel *kern, int k, fkski_in
         d[i + 1] = c;
         qw[i + 1] = t3[1] / bn;
     }
+    if (probe >= 0) {
+        tri_dg->assign(kk, 0.0);
+        tri_of->assign(kk, 0.0);
+        for (int i = 0; i < kk; ++i) {
+            (*tri_dg)[i] = T[(size_t)i * k + i];
+            if (i + 1 < kk) (*tri_of)[i] = T[(size_t)i * k + i + 1];
+        }
+        cudaFreeAsync(buf, s);
+        FK_CUDA(cudaStreamSynchronize(s));
+        if (info) info->iters = std::max(info->iters, kk);
+        return FKSKI_OK;
+    }
     // T = L L^T (host), Linv^T
     std::vector<double> Lm((size_t)kk * kk, 0.0), Li((size_t)kk * kk, 0.0);
     for (int j = 0; j < kk; ++j) {
@@ -2443,6 +2461,14 @@ static int efla_build(fkski_stats *st, const fkski_kernel *kern, int k, fkski_in
         info->status = FKSKI_OK;
     }
     return FKSKI_OK;
+}
+
+// Lanczos tridiagonal of A started at probe z_p (EFLA, k steps, full reorthogonalisation).
+int efla_probe_tridiag(fkski_stats *st, const fkski_kernel *kern, int k, int probe, std::vector<double> &dg,
+                       std::vector<double> &of, fkski_info *info, cudaStream_t s) {
+    if (!st || !kern || k < 1 || probe < 0 || probe >= st->nprobes) return FKSKI_E_INVALID_ARG;
+    return st->dtype == FKSKI_F32 ? efla_build<float>(st, kern, k, info, s, probe, &dg, &of)
+                                  : efla_build<double>(st, kern, k, info, s, probe, &dg, &of);
 }
 
 static bool same_kernel(const fkski_kernel &a, const fkski_kernel &b, int d) {

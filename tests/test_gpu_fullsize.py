@@ -1,0 +1,154 @@
+"""Parity at the full sizes of the benchmarked workloads (the sizes and launch shapes bench.py
+times), on outputs the oracle can compute one by one, and through properties that hold at any size.
+
+- Band / W^T y / W^T z rows at sampled grid nodes: the oracle's precompute over exactly the points
+  whose cells touch those nodes (a node's row only depends on them) must equal the GPU's full-size
+  rows (1e-6 relative, as the small-size tests).
+- Posterior mean: the factorized solve reports ||r|| / ||y|| for the n-space residual r; by the
+  identity (K W^T W + s^2 I) K W^T z = K W^T (y - r) (Claim 6), its m-space residual
+  ||(K B + s^2 I) v - K W^T y|| = ||K W^T r|| must be at most ||K||_2 ||W||_2 ||r||, checked with the
+  oracle's K_G and the GPU band (whose rows were checked above).
+- The sine workload (n = 1e4) is small enough for the oracle's full n-space CG.
+- The serving batch: every problem of the 64 equals its single-problem solve; the smallest ones
+  also match the oracle's n-space CG."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import rel_fro
+from paper_2101_11751_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _tt(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _digits(keys, grid):
+    nc = [int(grid.M[k]) - 3 for k in range(grid.d)]
+    out = np.empty((grid.d, keys.size), np.int64)
+    r = keys.astype(np.int64)
+    for k in range(grid.d - 1, -1, -1):
+        out[k] = r % nc[k]
+        r //= nc[k]
+    return out
+
+
+def _check_sampled_rows(fk, st, X, y, grid, keys, n_nodes, seed, nprobe=0, probe_seed=0):
+    """Oracle rows at sampled nodes from the points of the cells around them."""
+    from oracle import core
+    rng = np.random.default_rng(seed)
+    d = grid.d
+    M = [int(grid.M[k]) for k in range(d)]
+    nodes = np.stack([rng.integers(0, M[k], n_nodes) for k in range(d)])
+    dig = _digits(keys, grid)
+    sel = np.zeros(keys.size, bool)
+    for j in range(n_nodes):
+        inside = np.ones(keys.size, bool)
+        for k in range(d):
+            inside &= (dig[k] >= nodes[k, j] - 3) & (dig[k] <= nodes[k, j])
+        sel |= inside
+    idx = np.nonzero(sel)[0]
+    Xs, ys = np.ascontiguousarray(X[:, idx]), np.ascontiguousarray(y[idx])
+    ref = core.precompute(grid, Xs, ys, nprobe=0)
+    ex = fk.stats_export(st)
+    flat = np.ravel_multi_index(tuple(nodes), tuple(M))
+    gb, rb = ex["band"][:, flat], ref["band"][:, flat]
+    assert rel_fro(gb, rb) <= 1e-6, rel_fro(gb, rb)
+    assert np.max(np.abs(gb - rb)) <= 1e-6 * np.max(np.abs(rb))
+    assert rel_fro(ex["wty"][flat], ref["wty"][flat]) <= 1e-6
+    if nprobe:
+        # W^T z over the same points: the probe signs depend on the global point index
+        Z = np.stack([core.rademacher(probe_seed, p, X.shape[1])[idx] for p in range(nprobe)])
+        W = core.w_csr(grid, Xs)
+        wtz = (W.T @ Z.T).T
+        assert rel_fro(ex["wtz"][:, flat], wtz[:, flat]) <= 1e-6
+    return ex
+
+
+def _check_mean_residual(fk, ex, grid, kern, v, rel_res, yty):
+    """||(K B + s^2 I) v - K W^T y|| <= ||K|| ||W|| ||r||  (||r|| = rel_res ||y||)."""
+    from oracle import core
+    v = v.double().cpu().numpy()
+    Bv = core.band_matvec(grid, ex["band"], v)
+    lhs = core.kg_matvec(grid, kern, Bv) + kern.noise_var * v - core.kg_matvec(grid, kern, ex["wty"])
+    # ||K||_2 <= max row sum of |K| (symmetric); ||W||_2^2 = ||W^T W||_2 <= max row sum of the band
+    ones = np.ones(grid.m)
+    kmax = float(np.max(np.abs(core.kg_matvec(grid, kern, ones))))
+    wmax = float(np.sqrt(np.max(np.abs(ex["band"]).sum(axis=0))))
+    bound = kmax * wmax * rel_res * np.sqrt(yty)
+    assert np.linalg.norm(lhs) <= 1.05 * bound + 1e-12 * np.linalg.norm(core.kg_matvec(grid, kern, ex["wty"])), \
+        (np.linalg.norm(lhs), bound)
+
+
+def test_sine_full(fk, oracle_mod):
+    """c1: n = 1e4 FP64, M = 1000, rtol 1e-10 -- full precompute and mean against the oracle."""
+    from oracle import core
+    pr = synth.sine_1d()
+    st = fk.precompute(_tt(pr.X), _tt(pr.y), pr.grid, keep_sort=True)
+    ex = fk.stats_export(st)
+    ref = core.precompute(pr.grid, pr.X, pr.y)
+    assert rel_fro(ex["band"], ref["band"]) <= 1e-6 and rel_fro(ex["wty"], ref["wty"]) <= 1e-6
+    srt = fk.stats_export_sort(st)
+    np.testing.assert_array_equal(srt["perm"], ref["perm"])
+    a, v, info = fk.solve(st, pr.kernel, rtol=pr.rtol, maxiter=20000, precision=fk.DOUBLE)
+    _, v_ref, it_ref, _ = core.nspace_mean(pr.grid, pr.kernel, pr.X, pr.y, rtol=pr.rtol, x0_mode=1)
+    assert rel_fro(v.cpu().numpy(), v_ref) <= 1e-4
+    assert abs(info["iters"] - it_ref) <= max(3, 0.05 * it_ref)
+    mu = fk.predict(st, v, _tt(pr.Xstar)).cpu().numpy()
+    assert rel_fro(mu, core.predict(pr.grid, v_ref, pr.Xstar)) <= 1e-4
+
+
+def test_gmm_full(fk, oracle_mod):
+    """c2: n = 1e6 clustered 2-D, grid 128^2, Matern-5/2, rtol 1e-6."""
+    pr = synth.gmm_2d()
+    st = fk.precompute(_tt(pr.X), _tt(pr.y), pr.grid, keep_sort=True)
+    keys = fk.stats_export_sort(st)["keys"]
+    ex = _check_sampled_rows(fk, st, pr.X, pr.y, pr.grid, keys, 24, seed=1)
+    a, v, info = fk.solve(st, pr.kernel, rtol=pr.rtol, maxiter=6000, allow_not_converged=True)
+    _check_mean_residual(fk, ex, pr.grid, pr.kernel, v, info["rel_residual"], ex["yty"])
+
+
+def test_grf_full(fk, oracle_mod):
+    """c3: n = 1e7 uniform 3-D, grid 64^3, 16 probes."""
+    pr = synth.grf_3d()
+    st = fk.precompute(_tt(pr.X), _tt(pr.y), pr.grid, n_probes=pr.n_probes, probe_seed=pr.probe_seed,
+                       keep_sort=True)
+    keys = fk.stats_export_sort(st)["keys"]
+    ex = _check_sampled_rows(fk, st, pr.X, pr.y, pr.grid, keys, 12, seed=2, nprobe=2, probe_seed=pr.probe_seed)
+    a, v, info = fk.solve(st, pr.kernel, rtol=1e-4, maxiter=4000, allow_not_converged=True)
+    _check_mean_residual(fk, ex, pr.grid, pr.kernel, v, info["rel_residual"], ex["yty"])
+
+
+def test_radar_full(fk, oracle_mod):
+    """c4: n = 119,548,800 radar points, grid 128 x 128 x 32, rtol 1e-5 (the benchmarked step)."""
+    pr = synth.radar_3d(device="cuda")
+    st = fk.precompute(_tt(pr.X), _tt(pr.y), pr.grid, keep_sort=True)
+    keys = fk.stats_export_sort(st)["keys"]
+    ex = _check_sampled_rows(fk, st, pr.X, pr.y, pr.grid, keys, 16, seed=3)
+    a, v, info = fk.solve(st, pr.kernel, rtol=pr.rtol, maxiter=4000, check_every=16, allow_not_converged=True)
+    _check_mean_residual(fk, ex, pr.grid, pr.kernel, v, info["rel_residual"], ex["yty"])
+
+
+def test_batch_full(fk, oracle_mod):
+    """c5: 64 uneven problems under one graph; each equals its single-problem solve, and the
+    smallest match the oracle's n-space CG."""
+    from oracle import core
+    probs = synth.batch_2d()
+    sts = fk.precompute_batched([_tt(p.X) for p in probs], [_tt(p.y) for p in probs], [p.grid for p in probs])
+    a_b, v_b, info_b = fk.solve_batched(sts, [p.kernel for p in probs], rtol=1e-4, maxiter=4000,
+                                        allow_not_converged=True)
+    mus = fk.predict_batched(sts, v_b, [_tt(p.Xstar) for p in probs])
+    for i, p in enumerate(probs):
+        a, v, info = fk.solve(sts[i], p.kernel, rtol=1e-4, maxiter=4000, allow_not_converged=True)
+        assert info_b[i]["iters"] == info["iters"]
+        assert rel_fro(v_b[i].double().cpu().numpy(), v.double().cpu().numpy()) <= 1e-6
+    small = sorted(range(len(probs)), key=lambda i: probs[i].X.shape[1])[:3]
+    for i in small:
+        p = probs[i]
+        _, v_ref, _, _ = core.nspace_mean(p.grid, p.kernel, p.X.astype(np.float64), p.y.astype(np.float64),
+                                          rtol=1e-4, x0_mode=1)
+        assert rel_fro(v_b[i].double().cpu().numpy(), v_ref) <= 1e-3
+        mu_ref = core.predict(p.grid, v_ref, p.Xstar[:, :2000].astype(np.float64))
+        assert rel_fro(mus[i][:2000].double().cpu().numpy(), mu_ref) <= 1e-3

@@ -72,3 +72,33 @@ def test_autograd_function_and_budget_recompute(fk, oracle_mod):
     Lg, gg, _ = fk.grad(st, kern, rtol=1e-4)
     assert Lg == L1.item()
     np.testing.assert_array_equal(np.array(gg), g1.numpy())
+
+
+@pytest.mark.parametrize("d,M,n,kern", [
+    (2, (20, 22), 4000, synth.Kernel(synth.RBF, (0.15, 0.2), 1.0, 0.05)),
+    (3, (9, 10, 8), 5000, synth.Kernel(synth.RBF, (0.25, 0.3, 0.2), 1.0, 0.05)),
+])
+def test_logdet_lanczos_matches_oracle(fk, oracle_mod, d, M, n, kern):
+    """EFLA-based SLQ vs the oracle's n-space Lanczos (full reorthogonalisation, same probes, same
+    k): the same Krylov spaces, so the per-probe quadratures agree to 1e-8 (FP64 both sides)."""
+    from oracle import core
+    grid, X, y = problem(d, M, n, seed=61, dtype=np.float64)
+    T, seed, k = 4, 9, 40
+    st = fk.precompute(_tt(X), _tt(y), grid, n_probes=T, probe_seed=seed)
+    L, terms, info = fk.logdet_lanczos(st, kern, k)
+    Z = np.stack([core.rademacher(seed, p, n) for p in range(T)])
+    mv = core.ski_operator(grid, kern, core.w_csr(grid, X))
+    ref, rterms = core.slq_logdet_lanczos(mv, Z, k)
+    np.testing.assert_allclose(terms, rterms, rtol=1e-8)
+    assert L == pytest.approx(ref, rel=1e-8)
+
+
+def test_logdet_lanczos_exact_with_unit_probes(fk, oracle_mod):
+    from oracle import core
+    grid, X, y = problem(2, (8, 9), 40, seed=3, dtype=np.float64)
+    kern = synth.Kernel(synth.RBF, (0.3, 0.25), 1.3, 0.05)
+    n = X.shape[1]
+    st = fk.precompute(_tt(X), _tt(y), grid, Z=_tt(math.sqrt(n) * np.eye(n)))
+    L, _, _ = fk.logdet_lanczos(st, kern, n + 5)
+    exact = core.ski_inference_dense(grid, kern, X, y, X[:, :2])["logdet"]
+    assert L == pytest.approx(exact, rel=1e-8)
