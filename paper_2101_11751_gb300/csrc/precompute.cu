@@ -823,45 +823,24 @@ __global__ void __launch_bounds__(MOM_WARPS * 32) k_moments(const uint32_t *__re
 // ------------------------------------------------------------------ FP32 3-D moments, point-balanced
 // The same per-cell sums as k_moments<float, 3>, with the work of a column tile split evenly by
 // points instead of by cells: warp w takes the w-th eighth of the tile's sorted point range,
-// walks it cell by cell in chunks of at most 16 points of one cell, and keeps 49 + 8 FP32 sums
+// walks it cell by cell in chunks of at most 32 points of one cell, and keeps 49 + 8 FP32 sums
 // per lane (4 sub-groups x 8 roles, as in cell_moments_d3).  Every M3_FLUSH chunks and at the
 // end of its part of a cell it folds the sub-groups together and adds the sums to shared
 // memory: straight into the cell's slot when the warp owns the whole cell, else into one of its
 // two edge buffers (first / last cell, shared with the neighbouring warps).  The edge buffers
 // are added to the slots in warp order afterwards, so the result does not depend on timing.
-// Records of the next chunk are loaded before the current one is computed.  The 49 moment sums
-// of a role are kept as packed FP32 pairs over p2 and updated with fma.rn.f32x2 (two FMAs per
-// instruction; each element is rounded as a scalar FMA would be).
+// Records of the next chunk are loaded before the current one is computed.
 constexpr int M3_WARPS = 8;
-constexpr int M3_PS = 44;     // staged floats per point: B1[7], y | B2[7], 0 | B3[p] twice each (14), 0, 0 |
-                              // w1[4] | w2[4] | w3[4]  (44 / 4 odd: conflict-free 16-byte rows)
+constexpr int M3_PS = 36;     // staged floats per point: B1[7], y | B2[7], 0 | B3[7], 0 | w1[4] | w2[4] | w3[4]
 constexpr int M3_SLOT = 409;  // 343 moments + 64 y-moments + 2 pad (odd stride: the contraction's
                               // threads read slots of consecutive cells without bank conflicts)
-constexpr int M3_CH = 16;     // points per chunk (staged by lanes 0..15)
-constexpr int M3_FLUSH = 16;  // chunks between folds of the register sums
+constexpr int M3_FLUSH = 8;   // chunks between folds of the register sums
 constexpr int M3_NCT = 64;    // cells per tile
 
 static size_t moments3f_smem(int nct) {
-    return sizeof(float) * ((size_t)M3_WARPS * M3_CH * M3_PS + (size_t)nct * M3_SLOT + (size_t)M3_WARPS * 2 * M3_SLOT) +
+    return sizeof(float) * ((size_t)M3_WARPS * 32 * M3_PS + (size_t)nct * M3_SLOT + (size_t)M3_WARPS * 2 * M3_SLOT) +
            sizeof(uint32_t) * (size_t)(nct + 1) + sizeof(int) * 2 * M3_WARPS;
 }
-
-// Packed FP32 pairs (fma.rn.f32x2 / mul.rn.f32x2): two lanes of a 64-bit register, low half first.
-__device__ __forceinline__ unsigned long long f2_dup(float a) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
-    return r;
-}
-__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
-    unsigned long long r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ void f2_fma(unsigned long long &acc, unsigned long long a, unsigned long long b) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
-}
-__device__ __forceinline__ float f2_lo(unsigned long long a) { return __uint_as_float((unsigned)(a & 0xFFFFFFFFull)); }
-__device__ __forceinline__ float f2_hi(unsigned long long a) { return __uint_as_float((unsigned)(a >> 32)); }
 
 __device__ __forceinline__ int m3_find_cell(const uint32_t *coff, int nct, uint32_t p) {
     int lo = 0, hi = nct - 1;  // largest i with coff[i] <= p
@@ -872,7 +851,7 @@ __device__ __forceinline__ int m3_find_cell(const uint32_t *coff, int nct, uint3
     return lo;
 }
 
-__global__ void __launch_bounds__(M3_WARPS * 32, 2) k_moments3f(const uint32_t *__restrict__ perm, const Rec4<float> *__restrict__ rec,
+__global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__restrict__ perm, const Rec4<float> *__restrict__ rec,
                                                               const uint32_t *__restrict__ offsets, ColTiling tl, ETab<float> E,
                                                               float *__restrict__ outM, float *__restrict__ outY) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -886,7 +865,7 @@ __global__ void __launch_bounds__(M3_WARPS * 32, 2) k_moments3f(const uint32_t *
     const int cend = min(je, tl.C);
     const int nct = cend - cfirst;
     float *stage = reinterpret_cast<float *>(smraw);
-    float *slots = stage + M3_WARPS * M3_CH * M3_PS;
+    float *slots = stage + M3_WARPS * 32 * M3_PS;
     float *edge = slots + nct * M3_SLOT;
     uint32_t *coff = reinterpret_cast<uint32_t *>(edge + M3_WARPS * 2 * M3_SLOT);
     int *ecell = reinterpret_cast<int *>(coff + nct + 1);
@@ -908,19 +887,15 @@ __global__ void __launch_bounds__(M3_WARPS * 32, 2) k_moments3f(const uint32_t *
         ecell[2 * warp] = e0;
         ecell[2 * warp + 1] = e1;
     }
-    float *pb = stage + warp * M3_CH * M3_PS;
-    // m2[p3][pp] = (M[a][2pp][p3], M[a][2pp + 1][p3]) for role a = r (pp = 3: p2 = 6 and padding)
-    unsigned long long m2[7][4];
-    float yacc[8];
+    float *pb = stage + warp * 32 * M3_PS;
+    float m[49], yacc[8];
 #pragma unroll
-    for (int i = 0; i < 7; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) m2[i][j] = 0ull;
+    for (int i = 0; i < 49; ++i) m[i] = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i) yacc[i] = 0.f;
     uint32_t p = ws;
     int c = ws < we ? m3_find_cell(coff, nct, ws) : 0;
-    int nh = ws < we ? (int)min((uint32_t)M3_CH, min(coff[c + 1], we) - p) : 0;
+    int nh = ws < we ? (int)min(32u, min(coff[c + 1], we) - p) : 0;
     Rec4<float> my;
     my.t[0] = my.t[1] = my.t[2] = my.y = 0.f;
     if (lane < nh) my = rec[perm[p + lane]];
@@ -939,13 +914,13 @@ __global__ void __launch_bounds__(M3_WARPS * 32, 2) k_moments3f(const uint32_t *
             q[15] = 0.f;
             bern6<float>(my.t[2], b);
 #pragma unroll
-            for (int i = 0; i < 7; ++i) q[16 + 2 * i] = q[17 + 2 * i] = b[i];
-            q[30] = q[31] = 0.f;
+            for (int i = 0; i < 7; ++i) q[16 + i] = b[i];
+            q[23] = 0.f;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 keys_weights<float>(my.t[k], w);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) q[32 + 4 * k + i] = w[i];
+                for (int i = 0; i < 4; ++i) q[24 + 4 * k + i] = w[i];
             }
             float4 *dst = reinterpret_cast<float4 *>(pb + lane * M3_PS);
 #pragma unroll
@@ -958,32 +933,28 @@ __global__ void __launch_bounds__(M3_WARPS * 32, 2) k_moments3f(const uint32_t *
         int nhn = 0;
         if (pn < we) {
             while (coff[cn + 1] <= pn) ++cn;
-            nhn = (int)min((uint32_t)M3_CH, min(coff[cn + 1], we) - pn);
+            nhn = (int)min(32u, min(coff[cn + 1], we) - pn);
             if (lane < nhn) my = rec[perm[pn + lane]];
         }
         __syncwarp();
+#pragma unroll 2
         for (int k = sg; k < nh; k += 4) {
             const float *q = pb + k * M3_PS;
             const float alpha = r < 7 ? q[r] : 0.f;
             const float yv = q[7];
-            const ulonglong2 b2a = *reinterpret_cast<const ulonglong2 *>(q + 8);
-            const ulonglong2 b2b = *reinterpret_cast<const ulonglong2 *>(q + 12);
-            const unsigned long long aa = f2_dup(alpha);
-            const unsigned long long ab[4] = {f2_mul(aa, b2a.x), f2_mul(aa, b2a.y), f2_mul(aa, b2b.x), f2_mul(aa, b2b.y)};
-            const ulonglong2 *b3 = reinterpret_cast<const ulonglong2 *>(q + 16);
+            const float4 b2a = *reinterpret_cast<const float4 *>(q + 8), b2b = *reinterpret_cast<const float4 *>(q + 12);
+            const float4 b3a = *reinterpret_cast<const float4 *>(q + 16), b3b = *reinterpret_cast<const float4 *>(q + 20);
+            const float b2[7] = {b2a.x, b2a.y, b2a.z, b2a.w, b2b.x, b2b.y, b2b.z};
+            const float b3[7] = {b3a.x, b3a.y, b3a.z, b3a.w, b3b.x, b3b.y, b3b.z};
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const ulonglong2 bb = b3[h];
+            for (int p2 = 0; p2 < 7; ++p2) {
+                const float ab = alpha * b2[p2];
 #pragma unroll
-                for (int pp = 0; pp < 4; ++pp) f2_fma(m2[2 * h][pp], ab[pp], bb.x);
-                if (h < 3) {
-#pragma unroll
-                    for (int pp = 0; pp < 4; ++pp) f2_fma(m2[2 * h + 1][pp], ab[pp], bb.y);
-                }
+                for (int p3 = 0; p3 < 7; ++p3) m[p2 * 7 + p3] = fmaf(ab, b3[p3], m[p2 * 7 + p3]);
             }
-            const float ywa = yv * q[32 + (r >> 1)];
-            const float2 w2 = *reinterpret_cast<const float2 *>(q + 36 + 2 * (r & 1));
-            const float4 w3 = *reinterpret_cast<const float4 *>(q + 40);
+            const float ywa = yv * q[24 + (r >> 1)];
+            const float2 w2 = *reinterpret_cast<const float2 *>(q + 28 + 2 * (r & 1));
+            const float4 w3 = *reinterpret_cast<const float4 *>(q + 32);
             const float q0 = ywa * w2.x, q1 = ywa * w2.y;
             yacc[0] = fmaf(q0, w3.x, yacc[0]);
             yacc[1] = fmaf(q0, w3.y, yacc[1]);
@@ -996,14 +967,6 @@ __global__ void __launch_bounds__(M3_WARPS * 32, 2) k_moments3f(const uint32_t *
         }
         __syncwarp();
         if (cell_done || ++nacc == M3_FLUSH) {
-            float m[49];
-#pragma unroll
-            for (int p3 = 0; p3 < 7; ++p3)
-#pragma unroll
-                for (int pp = 0; pp < 4; ++pp) {
-                    m[(2 * pp) * 7 + p3] = f2_lo(m2[p3][pp]);
-                    if (pp < 3) m[(2 * pp + 1) * 7 + p3] = f2_hi(m2[p3][pp]);
-                }
 #pragma unroll
             for (int i = 0; i < 49; ++i) {
                 m[i] += __shfl_xor_sync(0xFFFFFFFFu, m[i], 8);
@@ -1030,9 +993,7 @@ __global__ void __launch_bounds__(M3_WARPS * 32, 2) k_moments3f(const uint32_t *
             }
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < 7; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) m2[i][j] = 0ull;
+            for (int i = 0; i < 49; ++i) m[i] = 0.f;
 #pragma unroll
             for (int i = 0; i < 8; ++i) yacc[i] = 0.f;
             nacc = 0;
