@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstdio>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -53,6 +54,20 @@ static cudaError_t pool_for(int dev, cudaMemPool_t *out) {
     }
     *out = g_pool[dev];
     return cudaSuccess;
+}
+
+static std::mutex g_attr_mu;
+static std::map<std::pair<int, const void *>, size_t> g_attr;
+
+int raise_smem_limit(const void *func, size_t bytes) {
+    int dev = 0;
+    FK_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    size_t &cur = g_attr[std::make_pair(dev, func)];
+    if (bytes <= cur) return FKSKI_OK;
+    FK_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+    return FKSKI_OK;
 }
 
 int pool_alloc(void **p, size_t bytes, cudaStream_t s) {

@@ -16,6 +16,10 @@ namespace fk {
 int note_cuda_error(cudaError_t e, const char *file, int line);
 // Stream-ordered temporary from the library's per-device caching pool (free with cudaFreeAsync).
 int pool_alloc(void **p, size_t bytes, cudaStream_t s);
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the current device, never
+// lowering it: kernel nodes captured in a CUDA graph keep their sizes, and a later smaller limit
+// would make their launches fail.
+int raise_smem_limit(const void *func, size_t bytes);
 }  // namespace fk
 
 #define FK_CUDA(call)                                                  \

@@ -280,7 +280,7 @@ static int forward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_
     for (int r = 1; r < R; ++r) kmax = std::max(kmax, it[r]);
     if (kmax > SLQ_MAXK) return FKSKI_E_UNSUPPORTED;
     const size_t slq_sm = sizeof(double) * 3 * (size_t)(kmax + 1);
-    if (slq_sm > 48 * 1024) FK_CUDA(cudaFuncSetAttribute(k_slq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slq_sm));
+    if (slq_sm > 48 * 1024) FK_TRY(raise_smem_limit((const void *)k_slq, slq_sm));
     k_slq<<<R - 1, 128, slq_sm, s>>>(gv.hist_a, gv.hist_b, gv.iters, gv.S, R, kern->noise_var, est, dstat);
     FK_LAUNCH();
     k_loglik_assemble<<<1, 32, 0, s>>>(gv.S, sl.zx, est, R, (double)st->n, sl.fs);

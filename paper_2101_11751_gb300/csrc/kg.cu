@@ -521,13 +521,13 @@ static int launch_cplx(const typename Cx<T>::t *in, typename Cx<T>::t *out, Cplx
     const size_t sm = sizeof(C) * ((size_t)p.L / 2 + (size_t)p.Q * p.L);
     const unsigned nb = (unsigned)cdiv(p.nlines, p.Q);
     if (mode == 0) {
-        FK_CUDA(cudaFuncSetAttribute(k_cplx_pass<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        FK_TRY(raise_smem_limit((const void *)k_cplx_pass<T, 0>, sm));
         k_cplx_pass<T, 0><<<nb, FFT_T, sm, s>>>(in, out, p, lam, gate);
     } else if (mode == 1) {
-        FK_CUDA(cudaFuncSetAttribute(k_cplx_pass<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        FK_TRY(raise_smem_limit((const void *)k_cplx_pass<T, 1>, sm));
         k_cplx_pass<T, 1><<<nb, FFT_T, sm, s>>>(in, out, p, lam, gate);
     } else {
-        FK_CUDA(cudaFuncSetAttribute(k_cplx_pass<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        FK_TRY(raise_smem_limit((const void *)k_cplx_pass<T, 2>, sm));
         k_cplx_pass<T, 2><<<nb, FFT_T, sm, s>>>(in, out, p, lam, gate);
     }
     FK_LAUNCH();
@@ -594,11 +594,11 @@ int kgop_set(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s) {
             const int deriv = (param == a) ? 1 : 0;
             const size_t sm = sizeof(double2) * ((size_t)op->L[a] / 2 + (size_t)op->L[a]);
             if (op->dtype == FKSKI_F32) {
-                FK_CUDA(cudaFuncSetAttribute(k_spectrum_1d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                FK_TRY(raise_smem_limit((const void *)k_spectrum_1d<float>, sm));
                 k_spectrum_1d<float><<<1, FFT_T, sm, s>>>((float *)op->lam[a], (int)op->g.M[a], op->L[a], op->g.h[a],
                                                           kern->lengthscale[a], deriv, scale);
             } else {
-                FK_CUDA(cudaFuncSetAttribute(k_spectrum_1d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                FK_TRY(raise_smem_limit((const void *)k_spectrum_1d<double>, sm));
                 k_spectrum_1d<double><<<1, FFT_T, sm, s>>>((double *)op->lam[a], (int)op->g.M[a], op->L[a], op->g.h[a],
                                                            kern->lengthscale[a], deriv, scale);
             }
@@ -669,7 +669,7 @@ static int launch_kron(const T *src, T *dst, RealPass p, const PassCfg &cfg, con
     const unsigned nb = (unsigned)cdiv(p.nlines, p.Q);
 #define FK_KRON(EPIV, RADV)                                                                                      \
     do {                                                                                                         \
-        FK_CUDA(cudaFuncSetAttribute(k_kron_pass<T, EPIV, RADV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+        FK_TRY(raise_smem_limit((const void *)k_kron_pass<T, EPIV, RADV>, sm)); \
         k_kron_pass<T, EPIV, RADV><<<nb, cfg.threads, sm, s>>>(src, dst, p, lam, addv, alpha_dev, alpha, gate); \
     } while (0)
     if (addv) {

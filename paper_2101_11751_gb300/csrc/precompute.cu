@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint32_t *__restrict_
 
 // Scatter one tile stably.  gscan = exclusive scan of ghist in digit-major order.
 template <bool FIRST, bool WRITE_KEYS>
-__global__ void __launch_bounds__(RS_T) k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+__global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                         uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                         int64_t n, int shift, int bits,
                                                         const uint32_t *__restrict__ gscan, int64_t ntiles) {
@@ -442,14 +442,12 @@ static int radix_sort_perm(const uint32_t *keys, int64_t n, int keybits, uint32_
     keybits = std::max(keybits, 1);
     const int npass = (int)cdiv(keybits, RS_MAXBITS);
     const int bits = (int)cdiv(keybits, npass);
-    static bool attr_done = false;
-    if (!attr_done) {
-        const int mx = (int)radix_scatter_smem(RS_MAXBITS);
-        FK_CUDA(cudaFuncSetAttribute(k_radix_scatter<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        FK_CUDA(cudaFuncSetAttribute(k_radix_scatter<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        FK_CUDA(cudaFuncSetAttribute(k_radix_scatter<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        FK_CUDA(cudaFuncSetAttribute(k_radix_scatter<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        attr_done = true;
+    {
+        const size_t mx = radix_scatter_smem(RS_MAXBITS);
+        FK_TRY(raise_smem_limit((const void *)k_radix_scatter<true, true>, mx));
+        FK_TRY(raise_smem_limit((const void *)k_radix_scatter<true, false>, mx));
+        FK_TRY(raise_smem_limit((const void *)k_radix_scatter<false, true>, mx));
+        FK_TRY(raise_smem_limit((const void *)k_radix_scatter<false, false>, mx));
     }
     const uint32_t *kin = keys;
     const uint32_t *vin = nullptr;
@@ -1332,12 +1330,12 @@ static int reduce_and_assemble(fkski_stats *st, const uint32_t *perm, const Rec4
         ColTiling t3;
         make_tiling<T, D>(g, M3_NCT, t3);
         const size_t smem = moments3f_smem(t3.nct);
-        FK_CUDA(cudaFuncSetAttribute(k_moments3f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FK_TRY(raise_smem_limit((const void *)k_moments3f, smem));
         k_moments3f<<<(unsigned)(t3.ncol * t3.ntile), M3_WARPS * 32, smem, s>>>(perm, rec, offsets, t3, E, t1, t1y);
     } else {
         const size_t smem = sizeof(T) * ((size_t)(L::PSTRIDE > 0 ? MOM_WARPS * 32 * L::PSTRIDE : 0) +
                                          (size_t)tl.nct * L::SLOT);
-        FK_CUDA(cudaFuncSetAttribute(k_moments<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FK_TRY(raise_smem_limit((const void *)k_moments<T, D>, smem));
         k_moments<T, D><<<(unsigned)(tl.ncol * tl.ntile), MOM_WARPS * 32, smem, s>>>(perm, rec, offsets, tl, E, t1, t1y);
     }
     FK_LAUNCH();
@@ -1376,7 +1374,7 @@ static int reduce_and_assemble(fkski_stats *st, const uint32_t *perm, const Rec4
             FK_TRY(sc.get(&z1, sizeof(T) * (size_t)(st->nprobes * NL * SP)));
         }
         const size_t psm = sizeof(T) * ((size_t)MOM_WARPS * 32 * 16 + (size_t)tp.nct * PL::SLOT);
-        FK_CUDA(cudaFuncSetAttribute(k_probe_moments<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+        FK_TRY(raise_smem_limit((const void *)k_probe_moments<T, D>, psm));
         for (int t0 = 0; t0 < st->nprobes; t0 += PG) {
             k_probe_moments<T, D><<<(unsigned)(tp.ncol * tp.ntile), MOM_WARPS * 32, psm, s>>>(
                 perm, rec, offsets, tp, Z, st->n, st->nprobes, t0, st->probe_seed, z1);

@@ -63,7 +63,7 @@ def _check_sampled_rows(fk, st, X, y, grid, keys, n_nodes, seed, nprobe=0, probe
         Z = np.stack([core.rademacher(probe_seed, p, X.shape[1])[idx] for p in range(nprobe)])
         W = core.w_csr(grid, Xs)
         wtz = (W.T @ Z.T).T
-        assert rel_fro(ex["wtz"][:, flat], wtz[:, flat]) <= 1e-6
+        assert rel_fro(ex["wtz"][:nprobe][:, flat], wtz[:, flat]) <= 1e-6
     return ex
 
 
