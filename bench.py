@@ -45,7 +45,7 @@ def measured_peaks():
     return HBM_FALLBACK, "fallback"
 
 
-SPMV_KERNEL = "k_band_spmv4h<49>"  # one rhs: the symmetric half band
+SPMV_KERNEL = "k_band_spmv4h<49, 0>"  # one rhs: the symmetric half band
 
 
 def profiled_traffic(kernel: str):

@@ -87,11 +87,13 @@ __device__ __forceinline__ void bf_dit(C &u, C &v, const C w) {
 
 // In-place DIF over `nl` lines of length L stored contiguously (line stride L), natural order in,
 // bit-reversed out.  RADIX 4 runs two radix-2 stages (spans h, h/2) per pass over shared memory:
-// each thread keeps 4 values in registers, halving the passes and barriers.
+// each thread keeps 4 values in registers, halving the passes and barriers.  The stages run from
+// span h0 down to 1 (h0 = L/2 for a whole transform; a caller that has already done the larger
+// spans passes the next one).
 template <typename T, int RADIX>
-__device__ __forceinline__ void fft_dif(typename Cx<T>::t *x, int nl, int L, const typename Cx<T>::t *tw) {
+__device__ __forceinline__ void fft_dif(typename Cx<T>::t *x, int nl, int L, const typename Cx<T>::t *tw, int h0 = 0) {
     using C = typename Cx<T>::t;
-    int h = L >> 1;
+    int h = h0 > 0 ? h0 : (L >> 1);
     if (RADIX == 4) {
         const int ng = nl * (L >> 2);
         const int lq = __ffs(L) - 3;  // log2(L/4)
@@ -135,15 +137,20 @@ __device__ __forceinline__ void fft_dif(typename Cx<T>::t *x, int nl, int L, con
 }
 
 // In-place DIT inverse (conjugate twiddles, no 1/L: folded into the spectrum), bit-reversed in,
-// natural out.  RADIX 4 groups the spans (h, 2h) from h = 1 upwards.
+// natural out.  RADIX 4 groups the spans (h, 2h) from h = 1 upwards.  Only the spans below htop
+// run (htop = L for a whole transform; a caller that finishes the largest span itself passes L/2).
+// With `lam`, the inputs of the first stage are first multiplied by lam[position in the line]
+// (the pointwise spectrum product, rounded exactly as a separate pass would round it).
 template <typename T, int RADIX>
-__device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L, const typename Cx<T>::t *tw) {
+__device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L, const typename Cx<T>::t *tw,
+                                            int htop = 0, const T *__restrict__ lam = nullptr) {
     using C = typename Cx<T>::t;
+    if (htop <= 0) htop = L;
     int h = 1;
     if (RADIX == 4) {
         const int ng = nl * (L >> 2);
         const int lq = __ffs(L) - 3;  // log2(L/4)
-        for (; 4 * h <= L; h <<= 2) {
+        for (; 4 * h <= htop; h <<= 2) {
             const int lh = __ffs(h) - 1;
             const int tA = L / (2 * h), tB = L / (4 * h);
             for (int b = threadIdx.x; b < ng; b += blockDim.x) {
@@ -151,6 +158,14 @@ __device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L,
                 const int j = k & (h - 1), blk = k >> lh;
                 C *xl = x + line * L + blk * 4 * h;
                 C a0 = xl[j], a1 = xl[j + h], a2 = xl[j + 2 * h], a3 = xl[j + 3 * h];
+                if (lam && h == 1) {
+                    const T *lb = lam + blk * 4;
+                    const T l0 = lb[0], l1 = lb[1], l2 = lb[2], l3 = lb[3];
+                    a0.x = r_mul(a0.x, l0); a0.y = r_mul(a0.y, l0);
+                    a1.x = r_mul(a1.x, l1); a1.y = r_mul(a1.y, l1);
+                    a2.x = r_mul(a2.x, l2); a2.y = r_mul(a2.y, l2);
+                    a3.x = r_mul(a3.x, l3); a3.y = r_mul(a3.y, l3);
+                }
                 const C wa = tw[j * tA];
                 bf_dit(a0, a1, wa);
                 bf_dit(a2, a3, wa);
@@ -166,7 +181,7 @@ __device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L,
     }
     const int nbf = nl * (L >> 1);
     const int lhalf = __ffs(L) - 2;  // log2(L/2)
-    for (; h < L; h <<= 1) {
+    for (; h < htop; h <<= 1) {
         const int tstep = L / (2 * h);
         const int lh = __ffs(h) - 1;
         for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
@@ -174,6 +189,11 @@ __device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L,
             const int j = k & (h - 1), blk = k >> lh;
             C *xl = x + line * L + blk * 2 * h;
             C u = xl[j], v = xl[j + h];
+            if (lam && h == 1) {
+                const T lu = lam[blk * 2], lv = lam[blk * 2 + 1];
+                u.x = r_mul(u.x, lu); u.y = r_mul(u.y, lu);
+                v.x = r_mul(v.x, lv); v.y = r_mul(v.y, lv);
+            }
             bf_dit(u, v, tw[j * tstep]);
             xl[j] = u;
             xl[j + h] = v;
@@ -200,60 +220,333 @@ struct RealPass {
 
 constexpr int FFT_TMAX = 512;
 
+// One CTA transforms Q real lines (Q/2 complex lines).  Shared memory: the twiddles (copied from
+// a table computed once per operator), the Q line base addresses (the only 64-bit index
+// arithmetic, once per line), then the lines.  Two stages are folded into the global-memory
+// phases: the upper half of every embedded line is zero (M <= L/2), so the first DIF stage (span
+// L/2) is one complex multiply at load time, and only the first M outputs are kept, so the last
+// DIT stage (span L/2) is one complex multiply-add at store time.  The spectrum product is folded
+// into the first DIT stage.
 template <typename T, bool EPI, int RADIX>
 __global__ void __launch_bounds__(FFT_TMAX) k_kron_pass(const T *__restrict__ in, T *__restrict__ out, RealPass p,
-                                                      const T *__restrict__ lam_br, const T *__restrict__ addv,
+                                                      const T *__restrict__ lam_br,
+                                                      const typename Cx<T>::t *__restrict__ tw_g,
+                                                      const T *__restrict__ addv,
                                                       const double *__restrict__ alpha_dev, double alpha_host,
                                                       const int *__restrict__ gate) {
     if (gate && *gate) return;
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
+    const int L = p.L, M = p.M, Q = p.Q, H = L >> 1;
+    const int nc = Q >> 1;
     C *tw = reinterpret_cast<C *>(smraw);
-    C *x = tw + p.L / 2;
-    const int L = p.L, M = p.M, Q = p.Q;
-    const int nc = Q / 2;
-    make_twiddles<T>(tw, L);
+    long long *la = reinterpret_cast<long long *>(tw + H);
+    C *x = reinterpret_cast<C *>(la + Q);
+    for (int k = threadIdx.x; k < H; k += blockDim.x) tw[k] = tw_g[k];
     const int64_t l0 = (int64_t)blockIdx.x * Q;
-    const int nq = (int)min((int64_t)Q, p.nlines - l0);
-    // zero padding region and odd partner
-    for (int e = threadIdx.x; e < nc * L; e += blockDim.x) {
-        x[e].x = T(0);
-        x[e].y = T(0);
+    for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+        // real line slot -> base address of its first element (-1: padding slot or past the end)
+        const int64_t slot = l0 + q;
+        long long a = -1;
+        if (slot < p.nlines) {
+            const int64_t lr = slot % p.lpr2;
+            if (lr < p.lpr) {
+                const int64_t l = (slot / p.lpr2) * p.lpr + lr;
+                a = (l / p.S) * (int64_t)M * p.S + (l % p.S);
+            }
+        }
+        la[q] = a;
     }
     __syncthreads();
-    // load: element (q, i), address base(line) + i*S (padding slots stay zero)
     const int64_t S = p.S;
-    for (int e = threadIdx.x; e < nq * M; e += blockDim.x) {
-        int q, i;
-        if (S == 1) { q = e / M; i = e % M; } else { q = e % nq; i = e / nq; }
-        const int64_t slot = l0 + q, lr = slot % p.lpr2;
-        if (lr >= p.lpr) continue;
-        const int64_t l = (slot / p.lpr2) * p.lpr + lr;
-        const int64_t base = (l / S) * (int64_t)M * S + (l % S);
-        const T v = in[base + (int64_t)i * S];
-        if (q & 1) x[(q >> 1) * L + i].y = v; else x[(q >> 1) * L + i].x = v;
+    const int lc = __ffs(nc) - 1;  // nc is a power of two
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // load complex line c, element i < L/2 (real parts: line 2c, imaginary: line 2c+1), and apply
+    // the first DIF stage against the zero upper half: (u, 0) -> (u, u w_i)
+    auto load_one = [&](int c, int i) {
+        const long long a0 = la[2 * c], a1 = la[2 * c + 1];
+        C u;
+        u.x = T(0);
+        u.y = T(0);
+        if (i < M) {
+            if (a0 >= 0) u.x = in[a0 + (int64_t)i * S];
+            if (a1 >= 0) u.y = in[a1 + (int64_t)i * S];
+        }
+        const C w = tw[i];
+        C v;
+        v.x = r_fma(u.x, w.x, -r_mul(u.y, w.y));
+        v.y = r_fma(u.x, w.y, r_mul(u.y, w.x));
+        x[c * L + i] = u;
+        x[c * L + i + H] = v;
+    };
+    if (S == 1) {  // lines are contiguous: lanes along the line
+        for (int c = warp; c < nc; c += nw)
+            for (int i = lane; i < H; i += 32) load_one(c, i);
+    } else {  // lines are neighbours in memory: lanes across lines
+        for (int e = threadIdx.x; e < nc * H; e += blockDim.x) load_one(e & (nc - 1), e >> lc);
     }
     __syncthreads();
-    fft_dif<T, RADIX>(x, nc, L, tw);
-    for (int e = threadIdx.x; e < nc * L; e += blockDim.x) {
-        const T lm = lam_br[e % L];
-        x[e].x *= lm;
-        x[e].y *= lm;
-    }
-    __syncthreads();
-    fft_dit_inv<T, RADIX>(x, nc, L, tw);
+    fft_dif<T, RADIX>(x, nc, L, tw, H >> 1);
+    fft_dit_inv<T, RADIX>(x, nc, L, tw, H, lam_br);
     const T alpha = EPI ? (alpha_dev ? (T)(*alpha_dev) : (T)alpha_host) : T(0);
-    for (int e = threadIdx.x; e < nq * M; e += blockDim.x) {
-        int q, i;
-        if (S == 1) { q = e / M; i = e % M; } else { q = e % nq; i = e / nq; }
-        const int64_t slot = l0 + q, lr = slot % p.lpr2;
-        if (lr >= p.lpr) continue;
-        const int64_t l = (slot / p.lpr2) * p.lpr + lr;
-        const int64_t a = (l / S) * (int64_t)M * S + (l % S) + (int64_t)i * S;
-        T v = (q & 1) ? x[(q >> 1) * L + i].y : x[(q >> 1) * L + i].x;
-        if (EPI) v = fma(alpha, addv[a], v);
-        out[a] = v;
+    // last DIT stage (span L/2) for the kept outputs i < M: u + v conj(w_i)
+    auto store_one = [&](int c, int i) {
+        const C u = x[c * L + i], v = x[c * L + i + H], w = tw[i];
+        const T tx = r_fma(v.x, w.x, r_mul(v.y, w.y));
+        const T ty = r_fma(v.y, w.x, -r_mul(v.x, w.y));
+        const long long a0 = la[2 * c], a1 = la[2 * c + 1];
+        if (a0 >= 0) {
+            const int64_t a = a0 + (int64_t)i * S;
+            T r = r_add(u.x, tx);
+            if (EPI) r = fma(alpha, addv[a], r);
+            out[a] = r;
+        }
+        if (a1 >= 0) {
+            const int64_t a = a1 + (int64_t)i * S;
+            T r = r_add(u.y, ty);
+            if (EPI) r = fma(alpha, addv[a], r);
+            out[a] = r;
+        }
+    };
+    if (S == 1) {
+        for (int c = warp; c < nc; c += nw)
+            for (int i = lane; i < M; i += 32) store_one(c, i);
+    } else {
+        for (int e = threadIdx.x; e < nc * M; e += blockDim.x) store_one(e & (nc - 1), e >> lc);
     }
+}
+
+// ------------------------------------------------------------------ register FFT pass (L <= 256)
+// The same embedded Toeplitz product along one axis, with each complex line's transform held in
+// registers: L = L1 * L2 (L2 <= L1 <= 16) and the four-step decomposition
+//   X[k1 + L1 k2] = sum_{n2} W_L2^{n2 k2} W_L^{n2 k1} sum_{n1} x[L2 n1 + n2] W_L1^{n1 k1}:
+// L1 threads per line; thread n2 runs the L1-point DFT of its column, applies W_L^{n2 k1}, and
+// the line's threads exchange through shared memory (one warp-synchronous transpose) so that
+// thread k1 holds X[k1 + L1 k2] for all k2 after its L2-point DFT.  The spectrum product and the
+// inverse run the same steps backwards, so a line needs two transposes and no block barrier;
+// the block only synchronises around the coalesced load and store of its lines.  The exchange
+// rows are padded to L2 + 1 complex values (conflict-free transposes).  Lines never interact,
+// so results do not depend on how many lines a CTA holds (the tuner's only choice here).
+template <typename C>
+__device__ __forceinline__ C cmul(const C a, const C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename C>
+__device__ __forceinline__ C cmulc(const C a, const C b) {  // a * conj(b)
+    C r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.y * b.x - a.x * b.y;
+    return r;
+}
+
+// In-register DFT of size N (natural order in and out): radix-2 DIF, then the bit-reversal
+// permutation as register renaming.  W_N^t = tw[t * (L / N)] (tw: exp(-2 pi i k / L), k < L/2);
+// INV uses conjugate twiddles.
+template <typename T, int N, int L, bool INV>
+__device__ __forceinline__ void reg_dft(typename Cx<T>::t (&v)[N], const typename Cx<T>::t *tw) {
+    using C = typename Cx<T>::t;
+#pragma unroll
+    for (int h = N / 2; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int b0 = 0; b0 < N; b0 += 2 * h) {
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                const C a = v[b0 + j], b = v[b0 + j + h];
+                C sum, dif;
+                sum.x = a.x + b.x; sum.y = a.y + b.y;
+                dif.x = a.x - b.x; dif.y = a.y - b.y;
+                v[b0 + j] = sum;
+                const int t = j * (N / (2 * h));  // W_N^t
+                if (t == 0) {
+                    v[b0 + j + h] = dif;
+                } else if (4 * t == N) {  // W = -i (forward) or +i (inverse)
+                    C r;
+                    if (INV) { r.x = -dif.y; r.y = dif.x; } else { r.x = dif.y; r.y = -dif.x; }
+                    v[b0 + j + h] = r;
+                } else {
+                    const C w = tw[t * (L / N)];
+                    v[b0 + j + h] = INV ? cmulc(dif, w) : cmul(dif, w);
+                }
+            }
+        }
+    }
+    // bit-reversed -> natural
+    C o[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        int r = 0;
+#pragma unroll
+        for (int b = 1, q = k; b < N; b <<= 1, q >>= 1) r = (r << 1) | (q & 1);
+        o[r] = v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = o[k];
+}
+
+// W_L^e for any integer e >= 0 from the half table (W_L^{e + L/2} = -W_L^e); conjugated for INV.
+template <typename T, int L, bool INV>
+__device__ __forceinline__ typename Cx<T>::t tw_any(const typename Cx<T>::t *tw, int e) {
+    e &= L - 1;
+    typename Cx<T>::t w = tw[e & (L / 2 - 1)];
+    if (e >= L / 2) { w.x = -w.x; w.y = -w.y; }
+    if (INV) w.y = -w.y;
+    return w;
+}
+
+template <typename T, bool EPI, int L1, int L2>
+__global__ void __launch_bounds__(256) k_kron_pass_reg(const T *__restrict__ in, T *__restrict__ out, RealPass p,
+                                                        const T *__restrict__ lam_br,
+                                                        const typename Cx<T>::t *__restrict__ tw_g,
+                                                        const T *__restrict__ addv,
+                                                        const double *__restrict__ alpha_dev, double alpha_host,
+                                                        const int *__restrict__ gate) {
+    if (gate && *gate) return;
+    using C = typename Cx<T>::t;
+    constexpr int L = L1 * L2, H = L / 2;
+    constexpr int LS = L + L1;  // per-line shared stride (complex): exchange rows of L2 + 1
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int M = p.M, Q = p.Q;
+    const int nc = Q >> 1;
+    C *tw = reinterpret_cast<C *>(smraw);
+    T *lam = reinterpret_cast<T *>(tw + H);
+    long long *la = reinterpret_cast<long long *>(lam + L + (L & 1));
+    C *x = reinterpret_cast<C *>(la + Q);
+    for (int k = threadIdx.x; k < H; k += blockDim.x) tw[k] = tw_g[k];
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        // natural-order spectrum from the bit-reversed table
+        constexpr int LB = (L1 == 16 ? 4 : (L1 == 8 ? 3 : (L1 == 4 ? 2 : 1))) + (L2 == 16 ? 4 : (L2 == 8 ? 3 : (L2 == 4 ? 2 : 1)));
+        lam[k] = lam_br[__brev((unsigned)k) >> (32 - LB)];
+    }
+    const int64_t l0 = (int64_t)blockIdx.x * Q;
+    for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+        const int64_t slot = l0 + q;
+        long long a = -1;
+        if (slot < p.nlines) {
+            const int64_t lr = slot % p.lpr2;
+            if (lr < p.lpr) {
+                const int64_t l = (slot / p.lpr2) * p.lpr + lr;
+                a = (l / p.S) * (int64_t)M * p.S + (l % p.S);
+            }
+        }
+        la[q] = a;
+    }
+    __syncthreads();
+    const int64_t S = p.S;
+    const int lc = __ffs(nc) - 1;  // nc is a power of two
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // coalesced load of the data part (i < M) of every line: real parts line 2c, imaginary 2c+1
+    auto load_one = [&](int c, int i) {
+        const long long a0 = la[2 * c], a1 = la[2 * c + 1];
+        C u;
+        u.x = a0 >= 0 ? in[a0 + (int64_t)i * S] : T(0);
+        u.y = a1 >= 0 ? in[a1 + (int64_t)i * S] : T(0);
+        x[c * LS + i] = u;
+    };
+    if (S == 1) {
+        for (int c = warp; c < nc; c += nw)
+            for (int i = lane; i < M; i += 32) load_one(c, i);
+    } else {
+        for (int e = threadIdx.x; e < nc * M; e += blockDim.x) load_one(e & (nc - 1), e >> lc);
+    }
+    __syncthreads();
+    // one line per group of L1 lanes; the loop over a warp's lines is warp-uniform (the
+    // exchanges synchronise the whole warp), idle groups only take part in the syncs
+    constexpr int GPW = 32 / L1;
+    const int j = lane % L1;
+    for (int cb = warp * GPW; cb < nc; cb += nw * GPW) {
+        const int c = cb + lane / L1;
+        const bool act = c < nc;
+        C *xl = x + (act ? c : 0) * LS;
+        const bool col = act && j < L2;  // thread owns column n2 = j in the outer steps
+        // forward, step 1: DFT over n1 of x[L2 n1 + j] (zero beyond M), then W_L^{j k1}
+        C v[L1];
+        if (col) {
+#pragma unroll
+            for (int n1 = 0; n1 < L1; ++n1) {
+                const int n = L2 * n1 + j;
+                if (n < M) v[n1] = xl[n];
+                else { v[n1].x = T(0); v[n1].y = T(0); }
+            }
+            reg_dft<T, L1, L, false>(v, tw);
+#pragma unroll
+            for (int k1 = 1; k1 < L1; ++k1) v[k1] = cmul(v[k1], tw_any<T, L, false>(tw, j * k1));
+        }
+        __syncwarp();
+        if (col) {
+#pragma unroll
+            for (int k1 = 0; k1 < L1; ++k1) xl[k1 * (L2 + 1) + j] = v[k1];
+        }
+        __syncwarp();
+        // step 2: thread k1 = j: DFT over n2 -> X[k1 + L1 k2]; spectrum; inverse over k2;
+        // then W_L^{-n2 k1}
+        if (act) {
+            C u[L2];
+#pragma unroll
+            for (int n2 = 0; n2 < L2; ++n2) u[n2] = xl[j * (L2 + 1) + n2];
+            reg_dft<T, L2, L, false>(u, tw);
+#pragma unroll
+            for (int k2 = 0; k2 < L2; ++k2) {
+                const T lm = lam[j + L1 * k2];
+                u[k2].x *= lm;
+                u[k2].y *= lm;
+            }
+            reg_dft<T, L2, L, true>(u, tw);
+#pragma unroll
+            for (int n2 = 1; n2 < L2; ++n2) u[n2] = cmul(u[n2], tw_any<T, L, true>(tw, n2 * j));
+#pragma unroll
+            for (int n2 = 0; n2 < L2; ++n2) xl[j * (L2 + 1) + n2] = u[n2];
+        }
+        __syncwarp();
+        // inverse, step 1 backwards: thread n2 = j: inverse DFT over k1 -> y[L2 n1 + j]
+        if (col) {
+#pragma unroll
+            for (int k1 = 0; k1 < L1; ++k1) v[k1] = xl[k1 * (L2 + 1) + j];
+            reg_dft<T, L1, L, true>(v, tw);
+        }
+        __syncwarp();
+        if (col) {
+#pragma unroll
+            for (int n1 = 0; n1 < L1; ++n1) {
+                const int n = L2 * n1 + j;
+                if (n < M) xl[n] = v[n1];
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    const T alpha = EPI ? (alpha_dev ? (T)(*alpha_dev) : (T)alpha_host) : T(0);
+    auto store_one = [&](int c, int i) {
+        const C u = x[c * LS + i];
+        const long long a0 = la[2 * c], a1 = la[2 * c + 1];
+        if (a0 >= 0) {
+            const int64_t a = a0 + (int64_t)i * S;
+            T r = u.x;
+            if (EPI) r = fma(alpha, addv[a], r);
+            out[a] = r;
+        }
+        if (a1 >= 0) {
+            const int64_t a = a1 + (int64_t)i * S;
+            T r = u.y;
+            if (EPI) r = fma(alpha, addv[a], r);
+            out[a] = r;
+        }
+    };
+    if (S == 1) {
+        for (int c = warp; c < nc; c += nw)
+            for (int i = lane; i < M; i += 32) store_one(c, i);
+    } else {
+        for (int e = threadIdx.x; e < nc * M; e += blockDim.x) store_one(e & (nc - 1), e >> lc);
+    }
+}
+
+// Twiddle table exp(-2 pi i k / L), k < L/2, for the Kronecker passes (same formula as the
+// per-CTA tables, computed once per operator).
+template <typename T>
+__global__ void __launch_bounds__(FFT_T) k_twiddles(typename Cx<T>::t *__restrict__ tw, int L) {
+    make_twiddles<T>(tw, L);
 }
 
 // ------------------------------------------------------------------ complex axis pass (BTTB)
@@ -438,6 +731,8 @@ struct KgOp {
     int kind;           // FKSKI_RBF / FKSKI_MATERN52
     int param;
     void *lam[3];       // Kronecker spectra (bit-reversed), L_k each
+    void *tw[3];        // Kronecker pass twiddles, L_k / 2 complex each
+    bool tw_ok[3];      // twiddle table written
     void *lamN;         // BTTB spectrum over the L-box (bit-reversed per axis)
     int64_t N;          // prod L_k
     void *scratch;      // work buffer
@@ -476,8 +771,10 @@ int kgop_create(const fkski_grid *grid, int dtype, KgOp **op) {
 
 void kgop_destroy(KgOp *op) {
     if (!op) return;
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) {
         if (op->lam[a]) cudaFree(op->lam[a]);
+        if (op->tw[a]) cudaFree(op->tw[a]);
+    }
     if (op->lamN) cudaFree(op->lamN);
     if (op->scratch) cudaFree(op->scratch);
     delete op;
@@ -590,6 +887,18 @@ int kgop_set(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s) {
         for (int a = 0; a < op->d; ++a) {
             size_t have = 0;
             if (!op->lam[a]) FK_TRY(ensure(&op->lam[a], have, es * op->L[a]));
+            if (!op->tw[a]) {
+                size_t have_tw = 0;
+                FK_TRY(ensure(&op->tw[a], have_tw, es * op->L[a]));  // L/2 complex
+            }
+            if (!op->tw_ok[a]) {
+                if (op->dtype == FKSKI_F32)
+                    k_twiddles<float><<<1, FFT_T, 0, s>>>((float2 *)op->tw[a], op->L[a]);
+                else
+                    k_twiddles<double><<<1, FFT_T, 0, s>>>((double2 *)op->tw[a], op->L[a]);
+                FK_LAUNCH();
+                op->tw_ok[a] = true;
+            }
             const double scale = (a == 0) ? (param == op->d ? 1.0 : kern->outputscale) : 1.0;
             const int deriv = (param == a) ? 1 : 0;
             const size_t sm = sizeof(double2) * ((size_t)op->L[a] / 2 + (size_t)op->L[a]);
@@ -616,9 +925,12 @@ int kgop_set(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s) {
 // graph capture: the solver calls kgop_tune before capturing) and keeps the fastest; untuned shapes get a default that
 // puts at least ~4 CTAs on every SM.
 struct PassCfg {
-    int radix, cl, threads;
+    int radix, cl, threads;  // radix 0: the register kernel (k_kron_pass_reg)
     float ms;  // tuned time per launch (0: default, not tuned)
 };
+
+// Axis lengths whose embedding the register kernel covers (L = L1 * L2, L1 <= 16).
+static bool reg_fft_ok(int L) { return L >= 8 && L <= 256; }
 
 struct PassKey {
     int dtype, L, M;
@@ -649,9 +961,22 @@ static int device_sms() {
 
 static PassCfg default_cfg(const RealPass &p) {
     const int64_t ncl = p.nlines / 2;  // complex lines
+    if (reg_fft_ok(p.L)) {
+        int cl = 16;
+        while (cl > 1 && cdiv(ncl, cl) < 4 * device_sms()) cl >>= 1;
+        return PassCfg{0, cl, 128, 0.f};
+    }
     int cl = std::max(1, FFT_SMEM_CPLX / p.L);
     while (cl > 1 && cdiv(ncl, cl) < 4 * device_sms()) cl >>= 1;
     return PassCfg{4, cl, 256, 0.f};
+}
+
+// Register-kernel shared memory: twiddles, natural-order spectrum, line addresses, padded lines.
+template <typename T>
+static size_t reg_pass_smem(int L, int cl) {
+    const int L1 = L >= 128 ? 16 : (L >= 32 ? 8 : 4);
+    return sizeof(typename Cx<T>::t) * ((size_t)L / 2 + (size_t)cl * (L + L1)) + sizeof(T) * (size_t)L +
+           sizeof(long long) * 2 * (size_t)cl;
 }
 
 static PassCfg pass_config(int dtype, const RealPass &p, int nrhs) {
@@ -662,15 +987,39 @@ static PassCfg pass_config(int dtype, const RealPass &p, int nrhs) {
 }
 
 template <typename T>
-static int launch_kron(const T *src, T *dst, RealPass p, const PassCfg &cfg, const T *lam, const T *addv,
-                       const double *alpha_dev, double alpha, const int *gate, cudaStream_t s) {
+static int launch_kron(const T *src, T *dst, RealPass p, const PassCfg &cfg, const T *lam,
+                       const typename Cx<T>::t *tw, const T *addv, const double *alpha_dev, double alpha,
+                       const int *gate, cudaStream_t s) {
     p.Q = 2 * cfg.cl;
-    const size_t sm = sizeof(typename Cx<T>::t) * ((size_t)p.L / 2 + (size_t)cfg.cl * p.L);
     const unsigned nb = (unsigned)cdiv(p.nlines, p.Q);
+    if (cfg.radix == 0) {
+        const size_t smr = reg_pass_smem<T>(p.L, cfg.cl);
+#define FK_KRONR(EPIV, A, B)                                                                                     \
+    do {                                                                                                         \
+        FK_TRY(raise_smem_limit((const void *)k_kron_pass_reg<T, EPIV, A, B>, smr));                           \
+        k_kron_pass_reg<T, EPIV, A, B><<<nb, cfg.threads, smr, s>>>(src, dst, p, lam, tw, addv, alpha_dev, alpha, gate); \
+    } while (0)
+#define FK_KRONR_L(EPIV)                                     \
+    switch (p.L) {                                           \
+        case 8: FK_KRONR(EPIV, 4, 2); break;                 \
+        case 16: FK_KRONR(EPIV, 4, 4); break;                \
+        case 32: FK_KRONR(EPIV, 8, 4); break;                \
+        case 64: FK_KRONR(EPIV, 8, 8); break;                \
+        case 128: FK_KRONR(EPIV, 16, 8); break;              \
+        case 256: FK_KRONR(EPIV, 16, 16); break;             \
+        default: return FKSKI_E_UNSUPPORTED;                 \
+    }
+        if (addv) { FK_KRONR_L(true); } else { FK_KRONR_L(false); }
+#undef FK_KRONR_L
+#undef FK_KRONR
+        FK_LAUNCH();
+        return FKSKI_OK;
+    }
+    const size_t sm = sizeof(typename Cx<T>::t) * ((size_t)p.L / 2 + (size_t)cfg.cl * p.L) + sizeof(long long) * p.Q;
 #define FK_KRON(EPIV, RADV)                                                                                      \
     do {                                                                                                         \
         FK_TRY(raise_smem_limit((const void *)k_kron_pass<T, EPIV, RADV>, sm)); \
-        k_kron_pass<T, EPIV, RADV><<<nb, cfg.threads, sm, s>>>(src, dst, p, lam, addv, alpha_dev, alpha, gate); \
+        k_kron_pass<T, EPIV, RADV><<<nb, cfg.threads, sm, s>>>(src, dst, p, lam, tw, addv, alpha_dev, alpha, gate); \
     } while (0)
     if (addv) {
         if (cfg.radix == 4) FK_KRON(true, 4); else FK_KRON(true, 2);
@@ -684,41 +1033,84 @@ static int launch_kron(const T *src, T *dst, RealPass p, const PassCfg &cfg, con
 
 // Time the candidates of one pass shape on scratch data and record the fastest.
 template <typename T>
-static int tune_pass(int dtype, RealPass p, const T *lam, T *buf_in, T *buf_out, cudaStream_t s) {
+static int tune_pass(int dtype, RealPass p, const T *lam, const typename Cx<T>::t *tw, T *buf_in, T *buf_out,
+                     cudaStream_t s) {
     const PassKey key{dtype, p.L, p.M, p.S, p.nlines};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         if (g_tune.count(key)) return FKSKI_OK;
     }
-    cudaEvent_t e0, e1;
-    FK_CUDA(cudaEventCreate(&e0));
-    FK_CUDA(cudaEventCreate(&e1));
+    // Candidates are timed as a captured graph of TUNE_REPS launches on a private stream (the
+    // per-launch host overhead would otherwise hide the kernels' differences).
+    constexpr int TUNE_REPS = 10;
+    cudaStream_t ts = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, ej = nullptr;
+    FK_CUDA(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ej, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ej, s);  // buffers were prepared on s
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ts, ej, 0);
+    int rc = ce == cudaSuccess ? FKSKI_OK : note_cuda_error(ce, __FILE__, __LINE__);
     PassCfg best = default_cfg(p);
     best.ms = 1e30f;
-    const int clmax = std::max(1, FFT_SMEM_CPLX / p.L);
     const int64_t ncl = std::max<int64_t>(1, p.nlines / 2);
-    int rc = FKSKI_OK;
-    for (int radix : {4, 2}) {
-        for (int threads : {128, 256, 512}) {
-            for (int cl = 1; cl <= clmax && rc == FKSKI_OK; cl <<= 1) {
-                if (cl > 1 && cl / 2 >= ncl) break;  // more lines per CTA than there are lines
-                const PassCfg c{radix, cl, threads, 0.f};
-                rc = launch_kron<T>(buf_in, buf_out, p, c, lam, nullptr, nullptr, 0.0, nullptr, s);  // warm-up
-                if (rc) break;
-                const int reps = 3;
-                cudaError_t e = cudaEventRecord(e0, s);
-                for (int r = 0; r < reps && rc == FKSKI_OK; ++r)
-                    rc = launch_kron<T>(buf_in, buf_out, p, c, lam, nullptr, nullptr, 0.0, nullptr, s);
-                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                float ms = 0.f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                if (e != cudaSuccess) { rc = note_cuda_error(e, __FILE__, __LINE__); break; }
-                ms /= reps;
-                if (ms < best.ms) best = PassCfg{radix, cl, threads, ms};
+    auto time_cfg = [&](const PassCfg &c) -> int {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal);
+        int r = e == cudaSuccess ? FKSKI_OK : note_cuda_error(e, __FILE__, __LINE__);
+        for (int k = 0; k < TUNE_REPS && r == FKSKI_OK; ++k)
+            r = launch_kron<T>(buf_in, buf_out, p, c, lam, tw, nullptr, nullptr, 0.0, nullptr, ts);
+        const cudaError_t ee = cudaStreamEndCapture(ts, &g);
+        if (r != FKSKI_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        e = ee;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge, ts);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, ts);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge, ts);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ts);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) return note_cuda_error(e, __FILE__, __LINE__);
+        ms /= TUNE_REPS;
+        if (ms < best.ms) best = PassCfg{c.radix, c.cl, c.threads, ms};
+        return FKSKI_OK;
+    };
+    if (reg_fft_ok(p.L)) {
+        // register kernel only (its configurations are bit-identical to each other)
+        for (int threads : {64, 128, 256}) {
+            for (int cl = 1; cl <= 64 && rc == FKSKI_OK; cl <<= 1) {
+                if (cl > 1 && cl / 2 >= ncl) break;
+                if (reg_pass_smem<T>(p.L, cl) > 96 * 1024) break;
+                rc = time_cfg(PassCfg{0, cl, threads, 0.f});
+            }
+        }
+    } else {
+        const int clmax = std::max(1, FFT_SMEM_CPLX / p.L);
+        for (int radix : {4, 2}) {
+            for (int threads : {128, 256, 512}) {
+                for (int cl = 1; cl <= clmax && rc == FKSKI_OK; cl <<= 1) {
+                    if (cl > 1 && cl / 2 >= ncl) break;  // more lines per CTA than there are lines
+                    rc = time_cfg(PassCfg{radix, cl, threads, 0.f});
+                }
             }
         }
     }
+    if (rc == FKSKI_OK) {
+        ce = cudaEventRecord(ej, ts);  // s continues after the tuning launches
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, ej, 0);
+        if (ce != cudaSuccess) rc = note_cuda_error(ce, __FILE__, __LINE__);
+    }
+    cudaStreamSynchronize(ts);
+    cudaStreamDestroy(ts);
+    if (ej) cudaEventDestroy(ej);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
@@ -744,7 +1136,8 @@ static int kron_tune(KgOp *op, int nrhs, cudaStream_t s) {
         p.lpr2 = p.lpr + (p.lpr & 1);
         p.nlines = (int64_t)nrhs * p.lpr2;
         p.Q = 2;
-        rc = tune_pass<T>(op->dtype, p, (const T *)op->lam[a], buf, buf + (size_t)nrhs * m, s);
+        rc = tune_pass<T>(op->dtype, p, (const T *)op->lam[a], (const typename Cx<T>::t *)op->tw[a], buf,
+                          buf + (size_t)nrhs * m, s);
     }
     cudaFreeAsync(buf, s);
     return rc;
@@ -753,7 +1146,7 @@ static int kron_tune(KgOp *op, int nrhs, cudaStream_t s) {
 int kgop_tune(KgOp *op, int nrhs, cudaStream_t s) {
     if (op->kind != FKSKI_RBF || nrhs < 1) return FKSKI_OK;
     for (int a = 0; a < op->d; ++a)
-        if (!op->lam[a]) return FKSKI_E_INVALID_ARG;  // spectra first (kgop_set)
+        if (!op->lam[a] || !op->tw[a]) return FKSKI_E_INVALID_ARG;  // spectra first (kgop_set)
     return op->dtype == FKSKI_F32 ? kron_tune<float>(op, nrhs, s) : kron_tune<double>(op, nrhs, s);
 }
 
@@ -804,7 +1197,8 @@ static int kron_apply(KgOp *op, const T *v, T *out, int nrhs, const T *addv, con
         const PassCfg cfg = pass_config(op->dtype, p, nrhs);
         p.Q = 2 * cfg.cl;
         const bool last = step == d - 1;
-        FK_TRY((launch_kron<T>(src, dst, p, cfg, (const T *)op->lam[a], last ? addv : nullptr, alpha_dev, alpha,
+        FK_TRY((launch_kron<T>(src, dst, p, cfg, (const T *)op->lam[a], (const typename Cx<T>::t *)op->tw[a],
+                               last ? addv : nullptr, alpha_dev, alpha,
                                op->gate, s)));
         src = dst;
     }
@@ -927,8 +1321,8 @@ int kg_mvm_impl(const fkski_grid *grid, const fkski_kernel *kern, int param, con
 // each other's data and give wrong results.
 static __device__ __align__(256) unsigned char g_kg_noalloc_scratch[FKSKI_NOALLOC_SCRATCH_BYTES];
 
-constexpr size_t NOALLOC_LAM_BYTES = sizeof(double) * FFT_SMEM_CPLX;  // one axis spectrum, FP32 or FP64
-constexpr size_t NOALLOC_BUF_OFFSET = 3 * NOALLOC_LAM_BYTES;
+constexpr size_t NOALLOC_LAM_BYTES = sizeof(double) * FFT_SMEM_CPLX;  // one axis spectrum (or twiddle table), FP32 or FP64
+constexpr size_t NOALLOC_BUF_OFFSET = 6 * NOALLOC_LAM_BYTES;              // 3 spectra, 3 twiddle tables
 constexpr int NOALLOC_MAX_DEVICES = 64;
 static_assert(NOALLOC_BUF_OFFSET % 256 == 0, "intermediate must stay 256-byte aligned");
 static_assert(FKSKI_NOALLOC_SCRATCH_BYTES > NOALLOC_BUF_OFFSET, "scratch smaller than its spectra");
@@ -983,10 +1377,13 @@ int kg_mvm_noalloc_impl(const fkski_grid *grid, const fkski_kernel *kern, int pa
     void *base = nullptr;
     FK_TRY(noalloc_scratch(&base));
     unsigned char *b = static_cast<unsigned char *>(base);
-    for (int a = 0; a < op.d; ++a) op.lam[a] = b + (size_t)a * NOALLOC_LAM_BYTES;
+    for (int a = 0; a < op.d; ++a) {
+        op.lam[a] = b + (size_t)a * NOALLOC_LAM_BYTES;
+        op.tw[a] = b + (size_t)(3 + a) * NOALLOC_LAM_BYTES;
+    }
     op.scratch = b + NOALLOC_BUF_OFFSET;
     op.scratch_bytes = FKSKI_NOALLOC_SCRATCH_BYTES - NOALLOC_BUF_OFFSET;
-    // with the spectra and the intermediate already in place, neither step below allocates
+    // with the spectra, twiddles and the intermediate already in place, neither step below allocates
     FK_TRY(kgop_set(&op, kern, param, s));
     return kgop_apply(&op, v, out, nrhs, nullptr, 0.0, s);
 }

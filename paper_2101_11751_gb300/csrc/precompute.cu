@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 namespace fk {
@@ -61,25 +62,45 @@ struct ETab {
     T e[4][7][7];
 };
 
+// One entry of the table as a constexpr function: with compile-time arguments (the unrolled
+// contraction loops) it folds to a literal, and the kernels skip the 64 of its 112 on-stencil
+// entries that are zero.
+__host__ __device__ constexpr double etab_coef(int a, int dl, int p) {
+    constexpr double beta[4][4] = {{0, -1.0 / 6, 0, 0}, {1, 1, 1.0 / 6, 0}, {0, 1.0 / 6, 1, 1}, {0, 0, -1.0 / 6, 0}};
+    constexpr double c3[4] = {1, 3, 3, 1};
+    constexpr double c6[7] = {1, 6, 15, 20, 15, 6, 1};
+    const int b = a + dl - 3;
+    double v = 0.0;
+    if (b >= 0 && b < 4)
+        for (int q = 0; q < 4; ++q) {
+            const int r = p - q;
+            if (r >= 0 && r < 4) v += beta[a][q] * beta[b][r] * c3[q] * c3[r] / c6[p];
+        }
+    return v;
+}
+
+// acc[dl] += sum_p E[A][dl][p] v[p] for every dl, p in increasing order, the entries as
+// compile-time constants (zero entries, including the off-stencil dl, emit nothing).
+template <int A, int DL, int P, typename T>
+__device__ __forceinline__ void etab_term(T &acc, T v) {
+    constexpr double c = etab_coef(A, DL, P);
+    if constexpr (c != 0.0) acc = fma((T)c, v, acc);
+}
+template <int A, typename T, int... I>
+__device__ __forceinline__ void etab_accumulate_seq(T (&acc)[7], const T *v, std::integer_sequence<int, I...>) {
+    (etab_term<A, I / 7, I % 7>(acc[I / 7], v[I % 7]), ...);
+}
+template <int A, typename T>
+__device__ __forceinline__ void etab_accumulate(T (&acc)[7], const T *v) {
+    etab_accumulate_seq<A>(acc, v, std::make_integer_sequence<int, 49>{});
+}
+
 template <typename T>
 static ETab<T> make_etab() {
-    const double beta[4][4] = {{0, -1.0 / 6, 0, 0}, {1, 1, 1.0 / 6, 0}, {0, 1.0 / 6, 1, 1}, {0, 0, -1.0 / 6, 0}};
-    const double c3[4] = {1, 3, 3, 1};
-    const double c6[7] = {1, 6, 15, 20, 15, 6, 1};
     ETab<T> E;
     for (int a = 0; a < 4; ++a)
-        for (int dl = 0; dl < 7; ++dl) {
-            const int b = a + dl - 3;
-            for (int p = 0; p < 7; ++p) {
-                double v = 0.0;
-                if (b >= 0 && b < 4)
-                    for (int q = 0; q < 4; ++q) {
-                        const int r = p - q;
-                        if (r >= 0 && r < 4) v += beta[a][q] * beta[b][r] * c3[q] * c3[r] / c6[p];
-                    }
-                E.e[a][dl][p] = (T)v;
-            }
-        }
+        for (int dl = 0; dl < 7; ++dl)
+            for (int p = 0; p < 7; ++p) E.e[a][dl][p] = (T)etab_coef(a, dl, p);
     return E;
 }
 
@@ -100,56 +121,83 @@ __global__ void k_gather_points(const uint32_t *__restrict__ perm, const uint32_
 // One thread per point (uniform trip count per block so warp collectives stay converged).
 // Writes key[i], rec[i] = (t_1..t_d, y_i), adds to the per-cell counts (warp-aggregated
 // integer atomics: exact) and accumulates y^2 (FP32 runs of 8, FP64 across) per block.
+// Blocks walk whole radix tiles (RS_TILE consecutive points) so that the first radix pass's
+// per-tile digit histogram (digit = key & (2^hbits - 1)) is counted here too and written in the
+// layout k_radix_hist would write (digit-major, ghist[digit * ntiles + tile]).  A point that
+// fails its checks is written with key 0 and counted under digit 0, as the sort will see it.
+constexpr int RS_T = 256;
+constexpr int RS_ITEMS = 32;
+constexpr int RS_TILE = RS_T * RS_ITEMS;  // 8192; each warp owns 1024 contiguous keys
+constexpr int RS_MAXBITS = 10;
+
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_keys(const T *__restrict__ X, const T *__restrict__ y, int64_t n,
-                                              KeyParams kp, uint32_t *__restrict__ keys,
-                                              Rec4<T> *__restrict__ rec, uint32_t *__restrict__ counts,
-                                              double *__restrict__ ypart, int *__restrict__ status) {
+__global__ void __launch_bounds__(RS_T) k_keys(const T *__restrict__ X, const T *__restrict__ y, int64_t n,
+                                               KeyParams kp, uint32_t *__restrict__ keys,
+                                               Rec4<T> *__restrict__ rec, uint32_t *__restrict__ counts,
+                                               double *__restrict__ ypart, int *__restrict__ status,
+                                               uint32_t *__restrict__ ghist, int hbits, int64_t ntiles) {
+    __shared__ uint32_t hist[1 << RS_MAXBITS];
     const int lane = threadIdx.x & 31;
+    const int nb = 1 << hbits;
+    const uint32_t hmask = (uint32_t)nb - 1u;
     double ysq = 0.0;
     float run = 0.f;
     int nrun = 0;
     int bad = 0;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        uint32_t key = 0xFFFFFFFFu;
-        if (i < n) {
-            Rec4<T> r;
-            r.t[0] = r.t[1] = r.t[2] = T(0);
-            int64_t kk = 0;
-            int st = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int i = threadIdx.x; i < nb; i += RS_T) hist[i] = 0u;
+        __syncthreads();
+        for (int k = 0; k < RS_ITEMS; ++k) {
+            const int64_t i = tile * RS_TILE + (int64_t)k * RS_T + threadIdx.x;
+            uint32_t key = 0xFFFFFFFFu;
+            bool failed = false;
+            if (i < n) {
+                Rec4<T> r;
+                r.t[0] = r.t[1] = r.t[2] = T(0);
+                int64_t kk = 0;
+                int st = 0;
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                int c = 1;
-                T t = T(0);
-                const int sk = axis_cell<T>(X[(int64_t)k * n + i], kp, k, c, t);
-                st |= sk;
-                kk += (int64_t)(c - 1) * kp.cstride[k];
-                r.t[k] = t;
-            }
-            const T yi = y[i];
-            if (!isfinite((double)yi)) st |= 2;
-            if (st == 0) {
-                key = (uint32_t)kk;
-                r.y = yi;
-                rec[i] = r;
-                keys[i] = key;
-                if (sizeof(T) == 4) {
-                    const float yf = (float)yi;
-                    run = fmaf(yf, yf, run);
-                    if (++nrun == 8) { ysq += (double)run; run = 0.f; nrun = 0; }
-                } else {
-                    ysq += (double)yi * (double)yi;
+                for (int a = 0; a < D; ++a) {
+                    int c = 1;
+                    T t = T(0);
+                    const int sk = axis_cell<T>(X[(int64_t)a * n + i], kp, a, c, t);
+                    st |= sk;
+                    kk += (int64_t)(c - 1) * kp.cstride[a];
+                    r.t[a] = t;
                 }
-            } else {
-                bad |= (st & 2) ? ST_NONFINITE : ST_OUT_OF_GRID;
-                keys[i] = 0;
-                r.y = T(0);
-                rec[i] = r;
+                const T yi = y[i];
+                if (!isfinite((double)yi)) st |= 2;
+                if (st == 0) {
+                    key = (uint32_t)kk;
+                    r.y = yi;
+                    rec[i] = r;
+                    keys[i] = key;
+                    if (sizeof(T) == 4) {
+                        const float yf = (float)yi;
+                        run = fmaf(yf, yf, run);
+                        if (++nrun == 8) { ysq += (double)run; run = 0.f; nrun = 0; }
+                    } else {
+                        ysq += (double)yi * (double)yi;
+                    }
+                } else {
+                    bad |= (st & 2) ? ST_NONFINITE : ST_OUT_OF_GRID;
+                    failed = true;
+                    keys[i] = 0;
+                    r.y = T(0);
+                    rec[i] = r;
+                }
             }
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+            if (key != 0xFFFFFFFFu && lane == __ffs(peers) - 1) {
+                atomicAdd(&counts[key], (uint32_t)__popc(peers));
+                if (ghist) atomicAdd(&hist[key & hmask], (uint32_t)__popc(peers));
+            }
+            if (failed && ghist) atomicAdd(&hist[0], 1u);
         }
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
-        if (key != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&counts[key], (uint32_t)__popc(peers));
+        __syncthreads();
+        if (ghist)
+            for (int d = threadIdx.x; d < nb; d += RS_T) ghist[(int64_t)d * ntiles + tile] = hist[d];
+        __syncthreads();
     }
     ysq += (double)run;
     if (bad) atomicOr(status, bad);
@@ -309,10 +357,6 @@ static int exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, bool
 }
 
 // ------------------------------------------------------------------ stable LSD radix sort
-constexpr int RS_T = 256;
-constexpr int RS_ITEMS = 32;
-constexpr int RS_TILE = RS_T * RS_ITEMS;  // 8192; each warp owns 1024 contiguous keys
-constexpr int RS_MAXBITS = 10;
 
 // Lanes of the warp holding the same digit (lanes outside `valid_mask` never match).
 __device__ __forceinline__ unsigned digit_peers(uint32_t dg, int bits, unsigned valid_mask) {
@@ -436,8 +480,17 @@ static size_t radix_scatter_smem(int bits) {
 
 // Stable sort of `keys` (values < 2^keybits); writes the permutation to perm_out.
 // Scratch: k2 (n), v1 (n), ghist (2^10 * ntiles), bsum.
+// Digit width of the first pass (the others use the same width).
+static int radix_pass_bits(int keybits) {
+    keybits = std::max(keybits, 1);
+    const int npass = (int)cdiv(keybits, RS_MAXBITS);
+    return (int)cdiv(keybits, npass);
+}
+
+// With first_hist, ghist already holds the first pass's per-tile histogram (from k_keys).
 static int radix_sort_perm(const uint32_t *keys, int64_t n, int keybits, uint32_t *perm_out, uint32_t *k2a,
-                           uint32_t *k2b, uint32_t *v1, uint32_t *ghist, uint32_t *bsum, cudaStream_t s) {
+                           uint32_t *k2b, uint32_t *v1, uint32_t *ghist, uint32_t *bsum, bool first_hist,
+                           cudaStream_t s) {
     const int64_t ntiles = cdiv(n, RS_TILE);
     keybits = std::max(keybits, 1);
     const int npass = (int)cdiv(keybits, RS_MAXBITS);
@@ -459,8 +512,10 @@ static int radix_sort_perm(const uint32_t *keys, int64_t n, int keybits, uint32_
         const int shift = p * bits;
         const int b = std::min(bits, keybits - shift);
         const bool first = p == 0, last = p == npass - 1;
-        k_radix_hist<<<(unsigned)ntiles, RS_T, 0, s>>>(kin, n, shift, b, ghist, ntiles);
-        FK_LAUNCH();
+        if (!(first && first_hist)) {
+            k_radix_hist<<<(unsigned)ntiles, RS_T, 0, s>>>(kin, n, shift, b, ghist, ntiles);
+            FK_LAUNCH();
+        }
         FK_TRY(exclusive_scan_u32(ghist, ghist, ((int64_t)1 << b) * ntiles, false, bsum, s));
         uint32_t *kout = kbufs[p % 2];
         uint32_t *vout = vbufs[vsel];
@@ -783,24 +838,21 @@ __global__ void __launch_bounds__(MOM_WARPS * 32) k_moments(const uint32_t *__re
         T acc[7];
 #pragma unroll
         for (int dl = 0; dl < 7; ++dl) acc[dl] = T(0);
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        auto cell = [&](auto a_) {
+            constexpr int a = decltype(a_)::value;
             const int c = j - a;
             if (c >= cfirst && c < cend) {
                 const T *sl = slots + (int64_t)(c - cfirst) * L::SLOT + pp * 7;
                 T v[7];
 #pragma unroll
                 for (int p = 0; p < 7; ++p) v[p] = sl[p];
-#pragma unroll
-                for (int dl = 0; dl < 7; ++dl) {
-                    const int b = a + dl - 3;
-                    if (b >= 0 && b < 4) {
-#pragma unroll
-                        for (int p = 0; p < 7; ++p) acc[dl] = fma(E.e[a][dl][p], v[p], acc[dl]);
-                    }
-                }
+                etab_accumulate<a>(acc, v);
             }
-        }
+        };
+        cell(std::integral_constant<int, 0>{});
+        cell(std::integral_constant<int, 1>{});
+        cell(std::integral_constant<int, 2>{});
+        cell(std::integral_constant<int, 3>{});
         const int64_t sp = col * tl.Ml + j;
 #pragma unroll
         for (int dl = 0; dl < 7; ++dl) outM[(int64_t)(pp * 7 + dl) * S1 + sp] = acc[dl];
@@ -886,11 +938,22 @@ __global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__r
         ecell[2 * warp + 1] = e1;
     }
     float *pb = stage + warp * 32 * M3_PS;
-    float m[49], yacc[8];
+    // moment sums of this lane's row a = r: (b, c) for b in pairs {0,1}, {2,3}, {4,5} as packed
+    // float2 (updated with the paired fma.rn.f32x2, each component rounded exactly as a scalar
+    // fmaf), b = 6 scalar; y sums in pairs
+    float2 mp[3][7];
+    float m6[7];
+    float2 yp[4];
 #pragma unroll
-    for (int i = 0; i < 49; ++i) m[i] = 0.f;
+    for (int c = 0; c < 7; ++c) {
+        mp[0][c] = mp[1][c] = mp[2][c] = make_float2(0.f, 0.f);
+        m6[c] = 0.f;
+    }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) yacc[i] = 0.f;
+    for (int i = 0; i < 4; ++i) yp[i] = make_float2(0.f, 0.f);
+    // component (b, c) of the lane's sums
+    auto mref = [&](int b, int c) -> float & { return b == 6 ? m6[c] : ((b & 1) ? mp[b >> 1][c].y : mp[b >> 1][c].x); };
+    auto yref = [&](int i) -> float & { return (i & 1) ? yp[i >> 1].y : yp[i >> 1].x; };
     uint32_t p = ws;
     int c = ws < we ? m3_find_cell(coff, nct, ws) : 0;
     int nh = ws < we ? (int)min(32u, min(coff[c + 1], we) - p) : 0;
@@ -942,58 +1005,72 @@ __global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__r
             const float yv = q[7];
             const float4 b2a = *reinterpret_cast<const float4 *>(q + 8), b2b = *reinterpret_cast<const float4 *>(q + 12);
             const float4 b3a = *reinterpret_cast<const float4 *>(q + 16), b3b = *reinterpret_cast<const float4 *>(q + 20);
-            const float b2[7] = {b2a.x, b2a.y, b2a.z, b2a.w, b2b.x, b2b.y, b2b.z};
             const float b3[7] = {b3a.x, b3a.y, b3a.z, b3a.w, b3b.x, b3b.y, b3b.z};
+            // ab_b = alpha * B2_b (rounded), then sum_c += ab_b * B3_c
+            const float2 aa = make_float2(alpha, alpha);
+            const float2 ab01 = __fmul2_rn(aa, make_float2(b2a.x, b2a.y));
+            const float2 ab23 = __fmul2_rn(aa, make_float2(b2a.z, b2a.w));
+            const float2 ab45 = __fmul2_rn(aa, make_float2(b2b.x, b2b.y));
+            const float ab6 = alpha * b2b.z;
 #pragma unroll
-            for (int p2 = 0; p2 < 7; ++p2) {
-                const float ab = alpha * b2[p2];
-#pragma unroll
-                for (int p3 = 0; p3 < 7; ++p3) m[p2 * 7 + p3] = fmaf(ab, b3[p3], m[p2 * 7 + p3]);
+            for (int c = 0; c < 7; ++c) {
+                const float2 zz = make_float2(b3[c], b3[c]);
+                mp[0][c] = __ffma2_rn(ab01, zz, mp[0][c]);
+                mp[1][c] = __ffma2_rn(ab23, zz, mp[1][c]);
+                mp[2][c] = __ffma2_rn(ab45, zz, mp[2][c]);
+                m6[c] = fmaf(ab6, b3[c], m6[c]);
             }
             const float ywa = yv * q[24 + (r >> 1)];
             const float2 w2 = *reinterpret_cast<const float2 *>(q + 28 + 2 * (r & 1));
             const float4 w3 = *reinterpret_cast<const float4 *>(q + 32);
-            const float q0 = ywa * w2.x, q1 = ywa * w2.y;
-            yacc[0] = fmaf(q0, w3.x, yacc[0]);
-            yacc[1] = fmaf(q0, w3.y, yacc[1]);
-            yacc[2] = fmaf(q0, w3.z, yacc[2]);
-            yacc[3] = fmaf(q0, w3.w, yacc[3]);
-            yacc[4] = fmaf(q1, w3.x, yacc[4]);
-            yacc[5] = fmaf(q1, w3.y, yacc[5]);
-            yacc[6] = fmaf(q1, w3.z, yacc[6]);
-            yacc[7] = fmaf(q1, w3.w, yacc[7]);
+            const float2 qq = __fmul2_rn(make_float2(ywa, ywa), w2);
+            const float2 q0 = make_float2(qq.x, qq.x), q1 = make_float2(qq.y, qq.y);
+            const float2 w3a = make_float2(w3.x, w3.y), w3b = make_float2(w3.z, w3.w);
+            yp[0] = __ffma2_rn(q0, w3a, yp[0]);
+            yp[1] = __ffma2_rn(q0, w3b, yp[1]);
+            yp[2] = __ffma2_rn(q1, w3a, yp[2]);
+            yp[3] = __ffma2_rn(q1, w3b, yp[3]);
         }
         __syncwarp();
         if (cell_done || ++nacc == M3_FLUSH) {
 #pragma unroll
-            for (int i = 0; i < 49; ++i) {
-                m[i] += __shfl_xor_sync(0xFFFFFFFFu, m[i], 8);
-                m[i] += __shfl_xor_sync(0xFFFFFFFFu, m[i], 16);
-            }
+            for (int b = 0; b < 7; ++b)
+#pragma unroll
+                for (int c = 0; c < 7; ++c) {
+                    float &v = mref(b, c);
+                    v += __shfl_xor_sync(0xFFFFFFFFu, v, 8);
+                    v += __shfl_xor_sync(0xFFFFFFFFu, v, 16);
+                }
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                yacc[i] += __shfl_xor_sync(0xFFFFFFFFu, yacc[i], 8);
-                yacc[i] += __shfl_xor_sync(0xFFFFFFFFu, yacc[i], 16);
+                float &v = yref(i);
+                v += __shfl_xor_sync(0xFFFFFFFFu, v, 8);
+                v += __shfl_xor_sync(0xFFFFFFFFu, v, 16);
             }
             if (sg == 0) {
                 float *dst = c == e0 ? edge + (warp * 2) * M3_SLOT
                                      : (c == e1 ? edge + (warp * 2 + 1) * M3_SLOT : slots + c * M3_SLOT);
                 if (r < 7) {
 #pragma unroll
-                    for (int i = 0; i < 49; ++i) dst[r * 49 + i] += m[i];
+                    for (int b = 0; b < 7; ++b)
+#pragma unroll
+                        for (int c = 0; c < 7; ++c) dst[r * 49 + b * 7 + c] += mref(b, c);
                 }
                 const int a1 = r >> 1, a2 = 2 * (r & 1);
 #pragma unroll
                 for (int a3 = 0; a3 < 4; ++a3) {
-                    dst[343 + a1 * 16 + a2 * 4 + a3] += yacc[a3];
-                    dst[343 + a1 * 16 + (a2 + 1) * 4 + a3] += yacc[4 + a3];
+                    dst[343 + a1 * 16 + a2 * 4 + a3] += yref(a3);
+                    dst[343 + a1 * 16 + (a2 + 1) * 4 + a3] += yref(4 + a3);
                 }
             }
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < 49; ++i) m[i] = 0.f;
+            for (int c = 0; c < 7; ++c) {
+                mp[0][c] = mp[1][c] = mp[2][c] = make_float2(0.f, 0.f);
+                m6[c] = 0.f;
+            }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) yacc[i] = 0.f;
+            for (int i = 0; i < 4; ++i) yp[i] = make_float2(0.f, 0.f);
             nacc = 0;
         }
         p = pn;
@@ -1019,24 +1096,21 @@ __global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__r
         float acc[7];
 #pragma unroll
         for (int dl = 0; dl < 7; ++dl) acc[dl] = 0.f;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        auto cell = [&](auto a_) {
+            constexpr int a = decltype(a_)::value;
             const int cc = j - a;
             if (cc >= cfirst && cc < cend) {
                 const float *sl = slots + (cc - cfirst) * M3_SLOT + pp * 7;
                 float v[7];
 #pragma unroll
                 for (int q = 0; q < 7; ++q) v[q] = sl[q];
-#pragma unroll
-                for (int dl = 0; dl < 7; ++dl) {
-                    const int b = a + dl - 3;
-                    if (b >= 0 && b < 4) {
-#pragma unroll
-                        for (int q = 0; q < 7; ++q) acc[dl] = fmaf(E.e[a][dl][q], v[q], acc[dl]);
-                    }
-                }
+                etab_accumulate<a>(acc, v);
             }
-        }
+        };
+        cell(std::integral_constant<int, 0>{});
+        cell(std::integral_constant<int, 1>{});
+        cell(std::integral_constant<int, 2>{});
+        cell(std::integral_constant<int, 3>{});
         const int64_t sp = col * tl.Ml + j;
 #pragma unroll
         for (int dl = 0; dl < 7; ++dl) outM[(int64_t)(pp * 7 + dl) * S1 + sp] = acc[dl];
@@ -1212,15 +1286,18 @@ __global__ void __launch_bounds__(256) k_axis_pass(const T *__restrict__ in, T *
         const int64_t co = r / ap.n_ci;
         const int j0 = jr * AXJ;
         const int jn = min(AXJ, ap.S_out - j0);
+        // component p of cell c at src[p * pstr + c * n_si]; output dl of node j at dst[dl * dstr + j * n_si]
+        const int64_t pstr = ap.n_ci * Sin_tot, dstr = ap.n_ci * Sout_tot;
+        const T *src = in + (co * P * ap.n_ci + ci) * Sin_tot + so * ap.S_in * ap.n_si + si;
+        T *dst = out + (co * DO * ap.n_ci + ci) * Sout_tot + so * ap.S_out * ap.n_si + si;
         // win[3 - a] holds cell j - a; the window shifts by one cell per output
         T win[4][P];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int c = j0 - 3 + k;
+            const T *q = src + (int64_t)c * ap.n_si;
 #pragma unroll
-            for (int p = 0; p < P; ++p)
-                win[k + 1][p] = (c >= 0 && c < ap.S_in) ? in[((co * P + p) * ap.n_ci + ci) * Sin_tot + (so * ap.S_in + c) * ap.n_si + si]
-                                                         : T(0);
+            for (int p = 0; p < P; ++p) win[k + 1][p] = (c >= 0 && c < ap.S_in) ? q[p * pstr] : T(0);
         }
 #pragma unroll 1
         for (int jj = 0; jj < jn; ++jj) {
@@ -1229,31 +1306,25 @@ __global__ void __launch_bounds__(256) k_axis_pass(const T *__restrict__ in, T *
             for (int k = 0; k < 3; ++k)
 #pragma unroll
                 for (int p = 0; p < P; ++p) win[k][p] = win[k + 1][p];
+            const T *q = src + (int64_t)j * ap.n_si;
 #pragma unroll
-            for (int p = 0; p < P; ++p)
-                win[3][p] = (j < ap.S_in) ? in[((co * P + p) * ap.n_ci + ci) * Sin_tot + (so * ap.S_in + j) * ap.n_si + si] : T(0);
+            for (int p = 0; p < P; ++p) win[3][p] = (j < ap.S_in) ? q[p * pstr] : T(0);
             T acc[DO];
 #pragma unroll
             for (int dl = 0; dl < DO; ++dl) acc[dl] = T(0);
+            if constexpr (MPART) {
+                // cell j - a is win[3 - a]
+                etab_accumulate<0>(acc, win[3]);
+                etab_accumulate<1>(acc, win[2]);
+                etab_accumulate<2>(acc, win[1]);
+                etab_accumulate<3>(acc, win[0]);
+            } else {
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const T *v = win[3 - a];  // cell j - a
-                if (MPART) {
-#pragma unroll
-                    for (int dl = 0; dl < DO; ++dl) {
-                        const int b = a + dl - 3;
-                        if (b >= 0 && b < 4) {
-#pragma unroll
-                            for (int p = 0; p < 7; ++p) acc[dl] = fma(E.e[a][dl][p], v[p], acc[dl]);
-                        }
-                    }
-                } else {
-                    acc[0] += v[a];
-                }
+                for (int a = 0; a < 4; ++a) acc[0] += win[3 - a][a];
             }
-            const int64_t spo = (so * ap.S_out + j) * ap.n_si + si;
+            T *o = dst + (int64_t)j * ap.n_si;
 #pragma unroll
-            for (int dl = 0; dl < DO; ++dl) out[((co * DO + dl) * ap.n_ci + ci) * Sout_tot + spo] = acc[dl];
+            for (int dl = 0; dl < DO; ++dl) o[dl * dstr] = acc[dl];
         }
     }
 }
@@ -1420,19 +1491,20 @@ static int precompute_typed(fkski_stats *st, const T *X, const T *y, const T *Z,
     FK_TRY(sc.get(&ghist, sizeof(uint32_t) * ((int64_t)1 << RS_MAXBITS) * ntiles));
     FK_TRY(sc.get(&bsum, sizeof(uint32_t) * (cdiv(maxscan, SCAN_TILE) + 1)));
     FK_TRY(sc.get(&dstatus, sizeof(int) * 4));
-    const int kblocks = (int)std::min<int64_t>(cdiv(n, 256), 152 * 8);
+    const int kblocks = (int)std::min<int64_t>(ntiles, 152 * 8);
     FK_TRY(sc.get(&ypart, sizeof(double) * (kblocks + 64 * 1216)));
     FK_TRY(sc.get(&dyty, sizeof(double) * (1 + kMaxProbes)));
     FK_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (ncell + 1), s));
     FK_CUDA(cudaMemsetAsync(dstatus, 0, sizeof(int) * 4, s));
-    k_keys<T, D><<<kblocks, 256, 0, s>>>(X, y, n, kp, keys, rec, counts, ypart, dstatus);
+    int keybits = 1;
+    while (((int64_t)1 << keybits) < ncell) ++keybits;
+    k_keys<T, D><<<kblocks, RS_T, 0, s>>>(X, y, n, kp, keys, rec, counts, ypart, dstatus, ghist,
+                                         radix_pass_bits(keybits), ntiles);
     FK_LAUNCH();
     k_sum_partials<<<1, 32, 0, s>>>(ypart, kblocks, 1, dyty);
     FK_LAUNCH();
     FK_TRY(exclusive_scan_u32(counts, offsets, ncell, true, bsum, s));
-    int keybits = 1;
-    while (((int64_t)1 << keybits) < ncell) ++keybits;
-    FK_TRY(radix_sort_perm(keys, n, keybits, perm, k2a, k2b, v1, ghist, bsum, s));
+    FK_TRY(radix_sort_perm(keys, n, keybits, perm, k2a, k2b, v1, ghist, bsum, true, s));
     FK_TRY((reduce_and_assemble<T, D>(st, perm, rec, offsets, Z, sc, s)));
     if (st->nprobes > 0) {
         if (Z) {

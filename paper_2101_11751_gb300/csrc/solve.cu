@@ -54,7 +54,44 @@ struct CgCtl {
     int replace;   // MIXED: reliable updates on; DOUBLE: off
     double sig2;
     double delta2; // replacement trigger: gamma < delta2 * gamma at the last replacement
+    unsigned int fin_cnt[2];  // blocks done in the launch whose last block finalises (gamma, delta)
 };
+
+// Last-block finalisation: every block of a reducing kernel writes its partials, then counts
+// itself done; the last block to finish (it sees every other block's partials after the fence)
+// runs the scalar step that would otherwise be a separate one-block launch, and re-arms the
+// counter for the next launch.  Call with the whole block; returns true in the last block.
+__device__ __forceinline__ bool last_block(unsigned int *counter) {
+    __shared__ unsigned int s_last;
+    __threadfence();  // every thread's partial writes, before the block counts itself done
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1 ? 1u : 0u;
+    }
+    __syncthreads();
+    const bool last = s_last != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// Arguments of the CG scalar steps when a reducing kernel finalises them in its last block.
+struct CgFin {
+    double *S;
+    int *state, *want, *iters;
+    double *hist;
+    CgCtl *ctl;
+    int mode;
+};
+
+template <bool GEN>
+__device__ void fin_gamma_dev(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ state,
+                              int *__restrict__ want, int *__restrict__ iters, double *__restrict__ hist_beta,
+                              CgCtl *__restrict__ ctl, int mode);
+template <bool GEN>
+__device__ void fin_delta_dev(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ state,
+                              const int *__restrict__ want, int *__restrict__ iters, double *__restrict__ hist_alpha,
+                              CgCtl *__restrict__ ctl, int mode);
 
 struct BandOffs {
     int off[343];
@@ -258,16 +295,23 @@ __global__ void __launch_bounds__(CG_T, Spmv4Occ<RB>::blocks) k_band_spmv4(const
 // reads, per upper row, its 7 direct quads at i0 and two quads around i0 - rowbase per
 // diagonal for the mirrored term; the mirrored quads are the direct quads of the thread
 // rowbase/4 positions back, read at about the same time, so they come from L2.
-template <int NROW>
-__global__ void __launch_bounds__(CG_T, 3) k_band_spmv4h(const float *__restrict__ hb, const float *__restrict__ x,
+// FIN 1 / 2: the last block to finish takes the CG gamma step (fin_gamma_dev, plain / GEN) from
+// all blocks' partials (R = 1 layout).
+template <int NROW, int FIN>
+__global__ void __launch_bounds__(CG_T, 2) k_band_spmv4h(const float *__restrict__ hb, const float *__restrict__ x,
                                                           float *__restrict__ u, int64_t m, RowOffs rows,
                                                           double *__restrict__ part, int NQ, const float *__restrict__ g,
-                                                          const int *__restrict__ gate, int Rtot, int r0, int nwork) {
+                                                          const int *__restrict__ gate, int Rtot, int r0, int nwork,
+                                                          CgFin fin) {
     if (gate && *gate) return;
     __shared__ double sh[CG_T / 32];
     if ((int)blockIdx.x >= nwork) {
         if (part && threadIdx.x == 0)
             for (int q = 0; q < NQ && q < 2; ++q) part[(int64_t)blockIdx.x * NQ * Rtot + r0 * NQ + q] = 0.0;
+        if (FIN && last_block(&fin.ctl->fin_cnt[0])) {
+            fin_gamma_dev<FIN == 2>(part, gridDim.x, fin.S, fin.state, fin.want, fin.iters, fin.hist, fin.ctl, fin.mode);
+            if (threadIdx.x == 0) fin.ctl->fin_cnt[0] = 0;
+        }
         return;
     }
     constexpr int C = NROW / 2;  // centre row
@@ -315,7 +359,7 @@ __global__ void __launch_bounds__(CG_T, 3) k_band_spmv4h(const float *__restrict
                     }
                 }
         }
-#pragma unroll 1
+#pragma unroll 2
         for (int u_ = 0; u_ < C; ++u_) {
             const int row = C + 1 + u_;
             const int64_t rb = rows.base[row];
@@ -371,6 +415,10 @@ __global__ void __launch_bounds__(CG_T, 3) k_band_spmv4h(const float *__restrict
     if (NQ > 1) {
         const double s1 = block_sum<float>(dq1, sh);
         if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ * Rtot + r0 * NQ + 1] = s1;
+    }
+    if (FIN && last_block(&fin.ctl->fin_cnt[0])) {
+        fin_gamma_dev<FIN == 2>(part, gridDim.x, fin.S, fin.state, fin.want, fin.iters, fin.hist, fin.ctl, fin.mode);
+        if (threadIdx.x == 0) fin.ctl->fin_cnt[0] = 0;
     }
 }
 
@@ -563,10 +611,10 @@ static int launch_spmv(const TB *band, const fkski_grid &g, const TX *x, TX *u, 
                 // one rhs: symmetric half (the stored band from the centre row's dx = 0 onwards)
                 const int nrow = g.d == 3 ? 49 : (g.d == 2 ? 7 : 1);
                 const float *hb = band + (int64_t)((nrow / 2) * 7 + 3) * m;
-                const int nwork = std::min(nblocks, num_sms() * 3);
-                if (g.d == 3) k_band_spmv4h<49><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork);
-                else if (g.d == 2) k_band_spmv4h<7><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork);
-                else k_band_spmv4h<1><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork);
+                const int nwork = std::min(nblocks, num_sms() * 2);
+                if (g.d == 3) k_band_spmv4h<49, 0><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork, CgFin{});
+                else if (g.d == 2) k_band_spmv4h<7, 0><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork, CgFin{});
+                else k_band_spmv4h<1, 0><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork, CgFin{});
                 FK_LAUNCH();
                 return FKSKI_OK;
             }
@@ -632,6 +680,26 @@ static int launch_spmv(const TB *band, const fkski_grid &g, const TX *x, TX *u, 
 #undef FK_SPMV
         FK_LAUNCH();
     }
+    return FKSKI_OK;
+}
+
+// One FP32 rhs: the half-band product with the CG gamma step taken by its last block (returns
+// FKSKI_E_UNSUPPORTED, launching nothing, where the half-band kernel does not apply).
+template <bool GEN>
+static int launch_spmvh_fin(const float *band, const fkski_grid &g, const float *x, float *u, int64_t m,
+                            double *part, int NQ, const float *gv, const int *gate, int nblocks, const CgFin &fin,
+                            cudaStream_t s) {
+    if (!spmv4_ok(g, m, band, x, u, gv)) return FKSKI_E_UNSUPPORTED;
+    const RowOffs ro = make_rows(g);
+    const int nrow = g.d == 3 ? 49 : (g.d == 2 ? 7 : 1);
+    const float *hb = band + (int64_t)((nrow / 2) * 7 + 3) * m;
+    const int nwork = std::min(nblocks, num_sms() * 2);
+    constexpr int F = GEN ? 2 : 1;
+    if (g.d == 3) k_band_spmv4h<49, F><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork, fin);
+    else if (g.d == 2) k_band_spmv4h<7, F><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork, fin);
+    else k_band_spmv4h<1, F><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork, fin);
+
+    FK_LAUNCH();
     return FKSKI_OK;
 }
 
@@ -726,13 +794,16 @@ __global__ void __launch_bounds__(CG_T) k_cg_xr(int64_t m, int R, double *__rest
     }
 }
 
-// p = r + beta p; s = u + beta s; z = v + beta z; partial dots s.z, s.kg, p.g, z.g (layout NQ = 4)
+// p = r + beta p; s = u + beta s; z = v + beta z; partial dots s.z, s.kg, p.g, z.g (layout NQ = 4);
+// the last block then takes the alpha step (fin_delta_dev) from all blocks' partials.
 template <typename T, bool GEN>
 __global__ void __launch_bounds__(CG_T) k_cg_psz(int64_t m, int R, const T *__restrict__ r, const T *__restrict__ u,
                                                   const T *__restrict__ v, T *__restrict__ p, T *__restrict__ s, T *__restrict__ z,
                                                   const T *__restrict__ g, const T *__restrict__ kg,
-                                                  const double *__restrict__ S, const int *__restrict__ state,
-                                                  double *__restrict__ part, const CgCtl *__restrict__ ctl) {
+                                                  double *__restrict__ part, CgFin fin) {
+    const CgCtl *ctl = fin.ctl;
+    const double *S = fin.S;
+    const int *state = fin.state;
     if (ctl->all_done) return;
     __shared__ double sh[CG_T / 32];
     for (int rr = 0; rr < R; ++rr) {
@@ -767,15 +838,19 @@ __global__ void __launch_bounds__(CG_T) k_cg_psz(int64_t m, int R, const T *__re
             pp[0] = t0; pp[1] = t1; pp[2] = t2; pp[3] = t3;
         }
     }
+    if (last_block(&fin.ctl->fin_cnt[1])) {
+        fin_delta_dev<GEN>(part, gridDim.x, fin.S, fin.state, fin.want, fin.iters, fin.hist, fin.ctl, fin.mode);
+        if (threadIdx.x == 0) fin.ctl->fin_cnt[1] = 0;
+    }
 }
 
 // gamma = <r, r> from u.r (q0) and r.g (q1) (Claim 4), after this iteration's x/r step
 // (GEN: c^x, c^r follow the step first).  mode 0: iterate; 1: init (no step taken).
 // Converged rhs become final (DOUBLE) or tentative, awaiting the true residual (MIXED).
 template <bool GEN>
-__global__ void k_cg_fin_gamma(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ state,
-                               int *__restrict__ want, int *__restrict__ iters, double *__restrict__ hist_beta,
-                               CgCtl *__restrict__ ctl, int mode) {
+__device__ void fin_gamma_dev(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ state,
+                              int *__restrict__ want, int *__restrict__ iters, double *__restrict__ hist_beta,
+                              CgCtl *__restrict__ ctl, int mode) {
     if (ctl->all_done) return;
     const int R = ctl->R;
     const double s2 = ctl->sig2;
@@ -832,12 +907,19 @@ __global__ void k_cg_fin_gamma(const double *__restrict__ part, int nparts, doub
     }
 }
 
+template <bool GEN>
+__global__ void k_cg_fin_gamma(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ state,
+                               int *__restrict__ want, int *__restrict__ iters, double *__restrict__ hist_beta,
+                               CgCtl *__restrict__ ctl, int mode) {
+    fin_gamma_dev<GEN>(part, nparts, S, state, want, iters, hist_beta, ctl, mode);
+}
+
 // alpha = gamma / <p, A p> (Claim 4 terms for GEN) for the next step.  mode 0: after an
 // iteration (records the next alpha, advances the counter); 1: init.
 template <bool GEN>
-__global__ void k_cg_fin_delta(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ state,
-                               const int *__restrict__ want, int *__restrict__ iters, double *__restrict__ hist_alpha,
-                               CgCtl *__restrict__ ctl, int mode) {
+__device__ void fin_delta_dev(const double *__restrict__ part, int nparts, double *__restrict__ S, int *__restrict__ state,
+                              const int *__restrict__ want, int *__restrict__ iters, double *__restrict__ hist_alpha,
+                              CgCtl *__restrict__ ctl, int mode) {
     if (ctl->all_done) return;
     const int R = ctl->R;
     const double s2 = ctl->sig2;
@@ -893,6 +975,7 @@ __global__ void k_cg_fin_delta(const double *__restrict__ part, int nparts, doub
         ctl->any_rep = rep;
     }
 }
+
 
 // After a residual replacement (MIXED): gamma from the true residual for the flagged rhs;
 // finish those that meet the tolerance, resume the others with alpha = gamma / <p, A p>
@@ -1378,14 +1461,27 @@ static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_op
         k_convert_t<double, T><<<gv, 256, 0, s>>>(V.r0, V.r, m, 1.0);
         FK_LAUNCH();
     }
+    // u = W^T W r with its partials, then the gamma step (taken by the product's last block when
+    // the half-band kernel applies, else by its own one-block launch)
+    auto spmv_gamma = [&](const int *gate, int mode, cudaStream_t st_) -> int {
+        if constexpr (std::is_same<T, float>::value) {
+            if (R == 1) {
+                const int rc0 = launch_spmvh_fin<GEN>(band, st->grid, V.r, V.u, m, w->part, NQ, GEN ? V.g : nullptr, gate,
+                                                      (int)gb, CgFin{w->S, w->state, w->want, w->iters, hb, w->ctl, mode},
+                                                      st_);
+                if (rc0 != FKSKI_E_UNSUPPORTED) return rc0;
+            }
+        }
+        FK_TRY((launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, gate, gb, st_)));
+        k_cg_fin_gamma<GEN><<<1, 256, 0, st_>>>(w->part, gb, w->S, w->state, w->want, w->iters, hb, w->ctl, mode);
+        FK_LAUNCH();
+        return FKSKI_OK;
+    };
     // init pass: gamma_0, s_0 = u_0, z_0 = v_0, p_0 = r_0, alpha_0
-    FK_TRY((launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, nullptr, gb, s)));
-    k_cg_fin_gamma<GEN><<<1, 256, 0, s>>>(w->part, gb, w->S, w->state, w->want, w->iters, hb, w->ctl, 1);
-    FK_LAUNCH();
+    FK_TRY(spmv_gamma(nullptr, 1, s));
     FK_TRY(kgop_apply_dev(kg, V.u, V.v, R, V.r, sig2_dev, s));
-    k_cg_psz<T, GEN><<<gb, CG_T, 0, s>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->S, w->state, w->part, w->ctl);
-    FK_LAUNCH();
-    k_cg_fin_delta<GEN><<<1, 256, 0, s>>>(w->part, gb, w->S, w->state, w->want, w->iters, ha, w->ctl, 1);
+    k_cg_psz<T, GEN><<<gb, CG_T, 0, s>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->part,
+                                         CgFin{w->S, w->state, w->want, w->iters, ha, w->ctl, 1});
     FK_LAUNCH();
     FK_TRY(kgop_reserve(kg, R));
     FK_TRY(kgop_reserve(kg64, R));
@@ -1401,13 +1497,12 @@ static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_op
     kgop_set_gate(kg, gate_done);  // finished solves skip their K_G passes too
     for (int it = 0; it < check && rc == FKSKI_OK; ++it) {
         k_cg_xr<T, GEN><<<gv, CG_T, 0, cs>>>(m, R, V.x, V.r, V.p, V.z, V.kg, w->S, w->state, w->ctl);
-        rc = launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, gate_done, gb, cs);
+        rc = spmv_gamma(gate_done, 0, cs);
         if (rc) break;
-        k_cg_fin_gamma<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->want, w->iters, hb, w->ctl, 0);
         rc = kgop_apply_dev(kg, V.u, V.v, R, V.r, sig2_dev, cs);
         if (rc) break;
-        k_cg_psz<T, GEN><<<gb, CG_T, 0, cs>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->S, w->state, w->part, w->ctl);
-        k_cg_fin_delta<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->want, w->iters, ha, w->ctl, 0);
+        k_cg_psz<T, GEN><<<gb, CG_T, 0, cs>>>(m, R, V.r, V.u, V.v, V.p, V.s, V.z, V.g, V.kg, w->part,
+                                              CgFin{w->S, w->state, w->want, w->iters, ha, w->ctl, 0});
     }
     cudaError_t ce = cudaStreamEndCapture(cs, &gbody);
     kgop_set_gate(kg, nullptr);

@@ -12,7 +12,8 @@ from paper_2101_11751_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 GRIDS = [((7,), (0.2,)), ((1000,), (0.05,)), ((128, 128), (0.04, 0.06)), ((33, 20), (0.3, 0.1)),
-         ((12, 10, 11), (0.2, 0.3, 0.25)), ((64, 64, 64), (0.1, 0.1, 0.1)), ((5, 130, 6), (0.3, 0.05, 0.4))]
+         ((12, 10, 11), (0.2, 0.3, 0.25)), ((64, 64, 64), (0.1, 0.1, 0.1)), ((5, 130, 6), (0.3, 0.05, 0.4)),
+         ((4, 9), (0.5, 0.3)), ((300,), (0.02,))]  # L = 8 and 32; L = 1024 (shared-memory transform)
 
 
 @pytest.mark.parametrize("M,ell", GRIDS)

@@ -160,3 +160,20 @@ def test_band_mvm_paths(fk, oracle_mod, d, M, R):
     # one rhs alone (half band when eligible) equals the same rhs inside the batch
     u0 = fk.band_mvm(st, _tt(V[:1].astype(np.float32))).cpu().numpy()
     assert rel_fro(u0, U32[:1]) <= 1e-6
+
+
+def test_band_mvm_half_many_tiles(fk, oracle_mod):
+    """The symmetric half-band product on a grid with more row tiles than SMs, so that each
+    persistent CTA walks several tiles and the mirrored windows (up to ~10 tiles back) cross tile
+    and CTA boundaries; one FP32 rhs, compared with the oracle's band product."""
+    from oracle import core
+    grid, X, y = problem(3, (48, 44, 40), 20000, seed=11)
+    st = fk.precompute(_tt(X), _tt(y), grid)
+    ref = core.precompute(grid, X, y)
+    v = np.random.default_rng(5).normal(size=(1, grid.m))
+    uref = core.band_matvec(grid, ref["band"], v.T).T
+    u = fk.band_mvm(st, _tt(v.astype(np.float32))).cpu().numpy()
+    assert rel_fro(u, uref) <= 2e-6
+    # repeated launches give identical bits (fixed summation order)
+    u2 = fk.band_mvm(st, _tt(v.astype(np.float32))).cpu().numpy()
+    np.testing.assert_array_equal(u, u2)
