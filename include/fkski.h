@@ -128,16 +128,18 @@ FKSKI_API const char *fkski_last_error_detail(void);
 
 /* The launch configurations the K_G autotuner has chosen so far in this process, one line per
  * pass shape ("f32 L=256 M=128 S=32 lines=4096 -> radix 4, 4 lines/CTA, 256 threads, 0.0123 ms").
- * The paper has no counterpart: the tuner picks, per Kronecker pass shape, the FFT stage radix
- * (2 or 4), the lines per CTA and the threads per CTA by timing each candidate once (before the
- * solver captures its graphs); the choices give bit-identical results.  Writes at most len bytes
+ * The paper has no counterpart: the tuner picks, per Kronecker pass shape, the lines per CTA and
+ * threads per CTA (and, for the shared-memory transform used above L = 256 in FP32 / L = 64 in
+ * FP64, the FFT stage radix 2 or 4; radix 0 denotes the register transform) by timing each
+ * candidate once (before the solver captures its graphs); the choices give bit-identical results.  Writes at most len bytes
  * (NUL-terminated) to buf (may be NULL) and returns the size needed. */
 FKSKI_API size_t fkski_tuning_table(char *buf, size_t len);
 
-/* Stream-ordered temporaries (precompute scratch, covariance blocks, tuner buffers) come from a
- * library memory pool per device that keeps freed blocks cached, so repeated calls map no new
- * memory.  This returns the cached blocks to the device (the paper has no counterpart).  Call
- * it with no library call in flight.  Returns OK or CUDA. */
+/* Stream-ordered temporaries (precompute scratch, covariance blocks, tuner buffers) and the
+ * statistics' band, W^T y and W^T z come from a library memory pool per device that keeps freed
+ * blocks cached, so repeated calls map no new memory.  This returns the cached blocks to the
+ * device (the paper has no counterpart).  Call it with no library call in flight.  Returns OK or
+ * CUDA. */
 FKSKI_API int fkski_trim_memory(void);
 
 /* Number of kernel launches this library has issued in the process so far (a replayed CUDA graph
@@ -151,7 +153,11 @@ FKSKI_API long long fkski_kernel_launches(void);
  *   and z_p^T z_p.
  * Points are sorted by grid cell with a stable sort (ties by input index) and reduced per cell
  * in that order, so the result is deterministic.
- *   grid   host; X device d x n (dtype); y device n (dtype); Z device n_probes x n (dtype) or NULL
+ *   grid   host; X d x n (dtype); y n (dtype); Z n_probes x n (dtype) or NULL.  X, y and Z are
+ *          read once, by the first kernel: they may be device memory or page-locked host memory
+ *          mapped into the device address space (e.g. cudaHostAlloc), which the kernel then reads
+ *          over the host link without a separate copy; memory the CUDA runtime reports without a
+ *          device mapping (pageable host memory on most systems) is INVALID_ARG.
  *   dtype  FKSKI_F32 or FKSKI_F64 (points and targets).  F32: per-cell sums in FP32 (runs of
  *          32 points per lane, then a second FP32 level) and FP32 statistics; F64: FP64 throughout.
  *   out    receives a new fkski_stats on success (NULL on failure).
@@ -181,7 +187,8 @@ FKSKI_API int fkski_stats_export_sort(const fkski_stats *st, uint32_t *keys, int
 FKSKI_API int fkski_stats_save(const fkski_stats *st, const char *path, void *stream);
 FKSKI_API int fkski_stats_load(const char *path, fkski_stats **out, void *stream);
 
-/* Release a stats object and all its device memory (NULL is a no-op). */
+/* Release a stats object and all its device memory (NULL is a no-op).  Synchronizes the device;
+ * the pool-backed buffers go back to the library pool (see fkski_trim_memory). */
 FKSKI_API void fkski_destroy(fkski_stats *st);
 
 /* ------------------------------------------------------------------ operators (Sec. 2.2, 3.2)

@@ -134,11 +134,11 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _ptr(t: Optional[torch.Tensor]):
+def _ptr(t: Optional[torch.Tensor], allow_pinned: bool = False):
     if t is None:
         return None
-    if not t.is_cuda:
-        raise ValueError("expected a CUDA tensor")
+    if not t.is_cuda and not (allow_pinned and t.is_pinned()):
+        raise ValueError("expected a CUDA tensor" + (" or a pinned host tensor" if allow_pinned else ""))
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
     return ctypes.c_void_p(t.data_ptr())
@@ -213,14 +213,15 @@ class Stats:
 
 def precompute(X: torch.Tensor, y: torch.Tensor, grid, Z: Optional[torch.Tensor] = None, n_probes: int = 0,
                probe_seed: int = 0, keep_sort: bool = False, keep_points: bool = False, stream=None) -> Stats:
-    """fkski_precompute: X (d, n) and y (n) CUDA tensors of one dtype; Z optional (T, n)."""
+    """fkski_precompute: X (d, n) and y (n) of one dtype, CUDA tensors or pinned host tensors (read
+    once by the key kernel over the host link); Z optional (T, n)."""
     load()
     if Z is not None:
         n_probes = Z.shape[0]
     o = opts(n_probes=n_probes, probe_seed=probe_seed, keep_sort=int(keep_sort), keep_points=int(keep_points))
     h = ctypes.c_void_p()
     g = c_grid(grid)
-    code = _lib.fkski_precompute(ctypes.byref(g), _ptr(X), _ptr(y), _ptr(Z), X.shape[1], _dtype_code(X),
+    code = _lib.fkski_precompute(ctypes.byref(g), _ptr(X, True), _ptr(y, True), _ptr(Z, True), X.shape[1], _dtype_code(X),
                                  ctypes.byref(o), ctypes.byref(h), _stream(stream))
     _check(code, "fkski_precompute")
     return Stats(h, grid, X.shape[1])

@@ -16,10 +16,16 @@ void destroy_stats(fkski_stats *st) {
     cudaGetDevice(&cur);
     if (st->device != cur) cudaSetDevice(st->device);
     free_solve_work(st->work);
-    void *ptrs[] = {st->band, st->wty, st->wtz, st->band_alt, st->wty_alt, st->wtz_alt, st->keys, st->perm, st->offsets,
-                    st->lowrank, st->pts, st->pkeys};
+    void *ptrs[] = {st->band_alt, st->wty_alt, st->wtz_alt, st->keys, st->perm, st->offsets, st->lowrank, st->pts,
+                    st->pkeys};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    // pool blocks: once the device is idle (cudaFree above already waited for it when it ran),
+    // hand them back to the pool
+    cudaDeviceSynchronize();
+    void *pooled[] = {st->band, st->wty, st->wtz};
+    for (void *p : pooled)
+        if (p) cudaFreeAsync(p, 0);
     if (st->device != cur) cudaSetDevice(cur);
     delete st;
 }
@@ -288,11 +294,9 @@ int fkski_stats_load(const char *path, fkski_stats **out, void *stream) {
     for (int p = 0; p < kMaxProbes; ++p) st->ztz[p] = h.ztz[p];
     cudaGetDevice(&st->device);
     int rc = FKSKI_OK;
-    if (cudaMalloc(&st->band, es * nb) != cudaSuccess || cudaMalloc(&st->wty, es * h.m) != cudaSuccess ||
-        (h.nprobes && cudaMalloc(&st->wtz, es * h.nprobes * h.m) != cudaSuccess)) {
-        cudaGetLastError();
+    if (pool_alloc(&st->band, es * nb, s) != FKSKI_OK || pool_alloc(&st->wty, es * h.m, s) != FKSKI_OK ||
+        (h.nprobes && pool_alloc(&st->wtz, es * h.nprobes * h.m, s) != FKSKI_OK))
         rc = FKSKI_E_OOM;
-    }
     if (rc == FKSKI_OK) {
         if (cudaMemcpyAsync(st->band, buf.data(), es * nb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(st->wty, buf.data() + es * nb, es * h.m, cudaMemcpyHostToDevice, s) != cudaSuccess ||

@@ -111,7 +111,8 @@ struct fkski_stats {
     double yty;
     double ztz[fk::kMaxProbes];
     int device;
-    // sufficient statistics, in `dtype`
+    // sufficient statistics, in `dtype`; from the library's memory pool (returned to it by
+    // fkski_destroy, so that repeated precomputes map no new memory)
     void *band;     // 7^d x m
     void *wty;      // m
     void *wtz;      // nprobes x m

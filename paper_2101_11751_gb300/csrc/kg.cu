@@ -260,7 +260,6 @@ __global__ void __launch_bounds__(FFT_TMAX) k_kron_pass(const T *__restrict__ in
     __syncthreads();
     const int64_t S = p.S;
     const int lc = __ffs(nc) - 1;  // nc is a power of two
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     // load complex line c, element i < L/2 (real parts: line 2c, imaginary: line 2c+1), and apply
     // the first DIF stage against the zero upper half: (u, 0) -> (u, u w_i)
     auto load_one = [&](int c, int i) {
@@ -279,10 +278,10 @@ __global__ void __launch_bounds__(FFT_TMAX) k_kron_pass(const T *__restrict__ in
         x[c * L + i] = u;
         x[c * L + i + H] = v;
     };
-    if (S == 1) {  // lines are contiguous: lanes along the line
-        for (int c = warp; c < nc; c += nw)
-            for (int i = lane; i < H; i += 32) load_one(c, i);
-    } else {  // lines are neighbours in memory: lanes across lines
+    if (S == 1) {  // lines are contiguous: consecutive threads along the line (H is a power of two)
+        const int lh = __ffs(H) - 1;
+        for (int e = threadIdx.x; e < nc * H; e += blockDim.x) load_one(e >> lh, e & (H - 1));
+    } else {  // lines are neighbours in memory: consecutive threads across lines
         for (int e = threadIdx.x; e < nc * H; e += blockDim.x) load_one(e & (nc - 1), e >> lc);
     }
     __syncthreads();
@@ -309,8 +308,9 @@ __global__ void __launch_bounds__(FFT_TMAX) k_kron_pass(const T *__restrict__ in
         }
     };
     if (S == 1) {
-        for (int c = warp; c < nc; c += nw)
-            for (int i = lane; i < M; i += 32) store_one(c, i);
+        const int lh = __ffs(H) - 1;
+        for (int e = threadIdx.x; e < nc * H; e += blockDim.x)
+            if ((e & (H - 1)) < M) store_one(e >> lh, e & (H - 1));
     } else {
         for (int e = threadIdx.x; e < nc * M; e += blockDim.x) store_one(e & (nc - 1), e >> lc);
     }
@@ -445,9 +445,9 @@ __global__ void __launch_bounds__(256) k_kron_pass_reg(const T *__restrict__ in,
         u.y = a1 >= 0 ? in[a1 + (int64_t)i * S] : T(0);
         x[c * LS + i] = u;
     };
-    if (S == 1) {
-        for (int c = warp; c < nc; c += nw)
-            for (int i = lane; i < M; i += 32) load_one(c, i);
+    if (S == 1) {  // consecutive threads along the line (H = L / 2 >= M, a power of two)
+        for (int e = threadIdx.x; e < nc * H; e += blockDim.x)
+            if ((e & (H - 1)) < M) load_one(e / H, e & (H - 1));
     } else {
         for (int e = threadIdx.x; e < nc * M; e += blockDim.x) load_one(e & (nc - 1), e >> lc);
     }
@@ -535,8 +535,8 @@ __global__ void __launch_bounds__(256) k_kron_pass_reg(const T *__restrict__ in,
         }
     };
     if (S == 1) {
-        for (int c = warp; c < nc; c += nw)
-            for (int i = lane; i < M; i += 32) store_one(c, i);
+        for (int e = threadIdx.x; e < nc * H; e += blockDim.x)
+            if ((e & (H - 1)) < M) store_one(e / H, e & (H - 1));
     } else {
         for (int e = threadIdx.x; e < nc * M; e += blockDim.x) store_one(e & (nc - 1), e >> lc);
     }
@@ -929,8 +929,10 @@ struct PassCfg {
     float ms;  // tuned time per launch (0: default, not tuned)
 };
 
-// Axis lengths whose embedding the register kernel covers (L = L1 * L2, L1 <= 16).
-static bool reg_fft_ok(int L) { return L >= 8 && L <= 256; }
+// Passes that run the register kernel (L = L1 * L2, L1 <= 16): FP32 up to L = 256; FP64 up to
+// L = 64 (its 16-value columns need twice the registers, and for L = 128, 256 the
+// shared-memory kernel is as fast or faster).  The rule depends on the shape only.
+static bool reg_fft_ok(int dtype, int L) { return L >= 8 && L <= (dtype == FKSKI_F32 ? 256 : 64); }
 
 struct PassKey {
     int dtype, L, M;
@@ -959,9 +961,9 @@ static int device_sms() {
     return n;
 }
 
-static PassCfg default_cfg(const RealPass &p) {
+static PassCfg default_cfg(int dtype, const RealPass &p) {
     const int64_t ncl = p.nlines / 2;  // complex lines
-    if (reg_fft_ok(p.L)) {
+    if (reg_fft_ok(dtype, p.L)) {
         int cl = 16;
         while (cl > 1 && cdiv(ncl, cl) < 4 * device_sms()) cl >>= 1;
         return PassCfg{0, cl, 128, 0.f};
@@ -983,7 +985,7 @@ static PassCfg pass_config(int dtype, const RealPass &p, int nrhs) {
     (void)nrhs;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     const auto it = g_tune.find(PassKey{dtype, p.L, p.M, p.S, p.nlines});
-    return it != g_tune.end() ? it->second : default_cfg(p);
+    return it != g_tune.end() ? it->second : default_cfg(dtype, p);
 }
 
 template <typename T>
@@ -1052,7 +1054,7 @@ static int tune_pass(int dtype, RealPass p, const T *lam, const typename Cx<T>::
     if (ce == cudaSuccess) ce = cudaEventRecord(ej, s);  // buffers were prepared on s
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ts, ej, 0);
     int rc = ce == cudaSuccess ? FKSKI_OK : note_cuda_error(ce, __FILE__, __LINE__);
-    PassCfg best = default_cfg(p);
+    PassCfg best = default_cfg(dtype, p);
     best.ms = 1e30f;
     const int64_t ncl = std::max<int64_t>(1, p.nlines / 2);
     auto time_cfg = [&](const PassCfg &c) -> int {
@@ -1083,7 +1085,7 @@ static int tune_pass(int dtype, RealPass p, const T *lam, const typename Cx<T>::
         if (ms < best.ms) best = PassCfg{c.radix, c.cl, c.threads, ms};
         return FKSKI_OK;
     };
-    if (reg_fft_ok(p.L)) {
+    if (reg_fft_ok(dtype, p.L)) {
         // register kernel only (its configurations are bit-identical to each other)
         for (int threads : {64, 128, 256}) {
             for (int cl = 1; cl <= 64 && rc == FKSKI_OK; cl <<= 1) {

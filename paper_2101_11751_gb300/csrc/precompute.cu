@@ -1544,12 +1544,36 @@ static int precompute_typed(fkski_stats *st, const T *X, const T *y, const T *Z,
 
 void destroy_stats(fkski_stats *st);
 
+// Device address of an input array: device (or managed) memory as is; page-locked host memory
+// through its device mapping; anything else (pageable host memory) is rejected.
+static int device_view(const void *p, const void **dp) {
+    *dp = nullptr;
+    if (!p) return FKSKI_OK;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return FKSKI_E_INVALID_ARG;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        *dp = p;
+        return FKSKI_OK;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *dp = a.devicePointer;
+        return FKSKI_OK;
+    }
+    return FKSKI_E_INVALID_ARG;
+}
+
 int precompute_impl(const fkski_grid *grid, const void *X, const void *y, const void *Z, int64_t n, int dtype,
                     const fkski_opts *opts, fkski_stats **out, cudaStream_t s) {
     if (!out) return FKSKI_E_INVALID_ARG;
     *out = nullptr;
     if (!grid || !X || !y || n < 1) return FKSKI_E_INVALID_ARG;
     if (dtype != FKSKI_F32 && dtype != FKSKI_F64) return FKSKI_E_INVALID_ARG;
+    FK_TRY(device_view(X, &X));
+    FK_TRY(device_view(y, &y));
+    FK_TRY(device_view(Z, &Z));
     const int d = grid->d;
     if (d < 1 || d > 3) return FKSKI_E_INVALID_ARG;
     int64_t m = 1, ncell = 1;
@@ -1580,11 +1604,9 @@ int precompute_impl(const fkski_grid *grid, const void *X, const void *y, const 
     const size_t es = dtype == FKSKI_F32 ? 4 : 8;
     const int64_t nb = ipow(7, d);
     int rc = FKSKI_OK;
-    if (cudaMalloc(&st->band, es * nb * m) != cudaSuccess || cudaMalloc(&st->wty, es * m) != cudaSuccess ||
-        (np > 0 && cudaMalloc(&st->wtz, es * np * m) != cudaSuccess)) {
-        cudaGetLastError();
+    if (pool_alloc(&st->band, es * nb * m, s) != FKSKI_OK || pool_alloc(&st->wty, es * m, s) != FKSKI_OK ||
+        (np > 0 && pool_alloc(&st->wtz, es * np * m, s) != FKSKI_OK))
         rc = FKSKI_E_OOM;
-    }
     if (rc == FKSKI_OK) {
         if (dtype == FKSKI_F32) {
             const float *Xf = (const float *)X, *yf = (const float *)y, *Zf = (const float *)Z;

@@ -317,8 +317,16 @@ __global__ void __launch_bounds__(CG_T, 2) k_band_spmv4h(const float *__restrict
     constexpr int C = NROW / 2;  // centre row
     float dq0 = 0.f, dq1 = 0.f;
     const int64_t nquad = m >> 2;
-    auto ld4 = [&](const float *base, int64_t j) -> float4 {  // quad at j (multiple of 4), zero off the ends
-        if (j >= 0 && j + 4 <= m) return __ldcs(reinterpret_cast<const float4 *>(base + j));
+    // quad at j (multiple of 4), zero off the ends; read-only loads that ask L2 to fetch the
+    // surrounding 256 B (a warp's band quads are contiguous, so DRAM sees larger bursts)
+    auto ld4 = [&](const float *base, int64_t j) -> float4 {
+        if (j >= 0 && j + 4 <= m) {
+            float4 r;
+            asm volatile("ld.global.nc.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                         : "l"(base + j));
+            return r;
+        }
         return make_float4(0.f, 0.f, 0.f, 0.f);
     };
     auto xwin = [&](int64_t w0, float v[12]) {  // x[w0 .. w0 + 11], zero off the ends

@@ -177,3 +177,31 @@ def test_band_mvm_half_many_tiles(fk, oracle_mod):
     # repeated launches give identical bits (fixed summation order)
     u2 = fk.band_mvm(st, _tt(v.astype(np.float32))).cpu().numpy()
     np.testing.assert_array_equal(u, u2)
+
+
+def test_pinned_host_inputs(fk, oracle_mod):
+    """X and y in page-locked host memory, read in place by the key kernel, give the same
+    statistics as device copies, bit for bit.  Pageable host memory is rejected by the binding;
+    the library rejects memory the CUDA runtime reports without a device mapping before any
+    device work (a platform that maps pageable memory must then give the same statistics)."""
+    import ctypes
+    grid, X, y = problem(3, (12, 10, 16), 30000, seed=13)
+    st_d = fk.precompute(_tt(X), _tt(y), grid, keep_sort=True)
+    Xh, yh = torch.from_numpy(X).pin_memory(), torch.from_numpy(y).pin_memory()
+    st_h = fk.precompute(Xh, yh, grid, keep_sort=True)
+    a, b = fk.stats_export(st_d), fk.stats_export(st_h)
+    for k in ("band", "wty"):
+        np.testing.assert_array_equal(a[k], b[k])
+    assert a["yty"] == b["yty"]
+    np.testing.assert_array_equal(fk.stats_export_sort(st_d)["perm"], fk.stats_export_sort(st_h)["perm"])
+    with pytest.raises(ValueError):
+        fk.precompute(torch.from_numpy(X), torch.from_numpy(y), grid)
+    h = ctypes.c_void_p()
+    code = fk.load().fkski_precompute(ctypes.byref(fk.c_grid(grid)), ctypes.c_void_p(X.ctypes.data),
+                                      ctypes.c_void_p(y.ctypes.data), None, X.shape[1], fk.F32,
+                                      ctypes.byref(fk.opts()), ctypes.byref(h), None)
+    if code == fk.OK:
+        st_p = fk.Stats(h, grid, X.shape[1])
+        np.testing.assert_array_equal(fk.stats_export(st_p)["band"], a["band"])
+    else:
+        assert code == fk.E_INVALID_ARG and not h.value
