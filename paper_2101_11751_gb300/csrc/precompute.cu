@@ -56,15 +56,9 @@ KeyParams make_key_params(const fkski_grid &g) {
 
 // Bernstein coefficients of the products w_a w_b (a, b = 0..3) in the degree-6 basis:
 // with w_a = sum_q beta_a[q] B3_q, B3_q B3_r = C(3,q) C(3,r) / C(6,q+r) B6_{q+r}.
-// Table E[a][delta+3][p] = coefficient of B6_p in w_a w_{a+delta} (0 if a+delta is off-stencil).
-template <typename T>
-struct ETab {
-    T e[4][7][7];
-};
-
-// One entry of the table as a constexpr function: with compile-time arguments (the unrolled
-// contraction loops) it folds to a literal, and the kernels skip the 64 of its 112 on-stencil
-// entries that are zero.
+// Table E[a][delta+3][p] = coefficient of B6_p in w_a w_{a+delta} (0 if a+delta is off-stencil),
+// as a constexpr function: with compile-time arguments (the contraction helpers below) it folds
+// to a literal, and the kernels skip the 64 of its 112 on-stencil entries that are zero.
 __host__ __device__ constexpr double etab_coef(int a, int dl, int p) {
     constexpr double beta[4][4] = {{0, -1.0 / 6, 0, 0}, {1, 1, 1.0 / 6, 0}, {0, 1.0 / 6, 1, 1}, {0, 0, -1.0 / 6, 0}};
     constexpr double c3[4] = {1, 3, 3, 1};
@@ -93,15 +87,6 @@ __device__ __forceinline__ void etab_accumulate_seq(T (&acc)[7], const T *v, std
 template <int A, typename T>
 __device__ __forceinline__ void etab_accumulate(T (&acc)[7], const T *v) {
     etab_accumulate_seq<A>(acc, v, std::make_integer_sequence<int, 49>{});
-}
-
-template <typename T>
-static ETab<T> make_etab() {
-    ETab<T> E;
-    for (int a = 0; a < 4; ++a)
-        for (int dl = 0; dl < 7; ++dl)
-            for (int p = 0; p < 7; ++p) E.e[a][dl][p] = (T)etab_coef(a, dl, p);
-    return E;
 }
 
 
@@ -803,7 +788,7 @@ __device__ void cell_moments_d1(const uint32_t *__restrict__ perm, const Rec4<T>
 template <typename T, int D>
 __global__ void __launch_bounds__(MOM_WARPS * 32) k_moments(const uint32_t *__restrict__ perm, const Rec4<T> *__restrict__ rec,
                                                              const uint32_t *__restrict__ offsets, ColTiling tl,
-                                                             ETab<T> E, T *__restrict__ outM, T *__restrict__ outY) {
+                                                             T *__restrict__ outM, T *__restrict__ outY) {
     using L = MomLayout<D>;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *pbuf = reinterpret_cast<T *>(smraw);
@@ -902,7 +887,7 @@ __device__ __forceinline__ int m3_find_cell(const uint32_t *coff, int nct, uint3
 }
 
 __global__ void __launch_bounds__(M3_WARPS * 32) k_moments3f(const uint32_t *__restrict__ perm, const Rec4<float> *__restrict__ rec,
-                                                              const uint32_t *__restrict__ offsets, ColTiling tl, ETab<float> E,
+                                                              const uint32_t *__restrict__ offsets, ColTiling tl,
                                                               float *__restrict__ outM, float *__restrict__ outY) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1270,7 +1255,7 @@ struct AxisPass {
 constexpr int AXJ = 8;
 
 template <typename T, bool MPART>
-__global__ void __launch_bounds__(256) k_axis_pass(const T *__restrict__ in, T *__restrict__ out, AxisPass ap, ETab<T> E) {
+__global__ void __launch_bounds__(256) k_axis_pass(const T *__restrict__ in, T *__restrict__ out, AxisPass ap) {
     constexpr int P = MPART ? 7 : 4;
     constexpr int DO = MPART ? 7 : 1;
     const int64_t Sin_tot = ap.n_so * ap.S_in * ap.n_si;
@@ -1330,10 +1315,10 @@ __global__ void __launch_bounds__(256) k_axis_pass(const T *__restrict__ in, T *
 }
 
 template <typename T, bool MPART>
-static int launch_axis_pass(const T *in, T *out, AxisPass ap, const ETab<T> &E, cudaStream_t s) {
+static int launch_axis_pass(const T *in, T *out, AxisPass ap, cudaStream_t s) {
     const int64_t total = ap.n_co * ap.n_ci * ap.n_so * ((ap.S_out + AXJ - 1) / AXJ) * ap.n_si;
     const int64_t nb = std::min<int64_t>(cdiv(total, 256), 152 * 16);
-    k_axis_pass<T, MPART><<<(unsigned)std::max<int64_t>(nb, 1), 256, 0, s>>>(in, out, ap, E);
+    k_axis_pass<T, MPART><<<(unsigned)std::max<int64_t>(nb, 1), 256, 0, s>>>(in, out, ap);
     FK_LAUNCH();
     return FKSKI_OK;
 }
@@ -1382,7 +1367,6 @@ static int reduce_and_assemble(fkski_stats *st, const uint32_t *perm, const Rec4
                                const T *Z, Scratch &sc, cudaStream_t s) {
     const fkski_grid &g = st->grid;
     using L = MomLayout<D>;
-    const ETab<T> E = make_etab<T>();
     ColTiling tl;
     make_tiling<T, D>(g, MomCap<T, D>::NCT, tl);
     const int64_t S1 = tl.ncol * tl.Ml;
@@ -1402,12 +1386,12 @@ static int reduce_and_assemble(fkski_stats *st, const uint32_t *perm, const Rec4
         make_tiling<T, D>(g, M3_NCT, t3);
         const size_t smem = moments3f_smem(t3.nct);
         FK_TRY(raise_smem_limit((const void *)k_moments3f, smem));
-        k_moments3f<<<(unsigned)(t3.ncol * t3.ntile), M3_WARPS * 32, smem, s>>>(perm, rec, offsets, t3, E, t1, t1y);
+        k_moments3f<<<(unsigned)(t3.ncol * t3.ntile), M3_WARPS * 32, smem, s>>>(perm, rec, offsets, t3, t1, t1y);
     } else {
         const size_t smem = sizeof(T) * ((size_t)(L::PSTRIDE > 0 ? MOM_WARPS * 32 * L::PSTRIDE : 0) +
                                          (size_t)tl.nct * L::SLOT);
         FK_TRY(raise_smem_limit((const void *)k_moments<T, D>, smem));
-        k_moments<T, D><<<(unsigned)(tl.ncol * tl.ntile), MOM_WARPS * 32, smem, s>>>(perm, rec, offsets, tl, E, t1, t1y);
+        k_moments<T, D><<<(unsigned)(tl.ncol * tl.ntile), MOM_WARPS * 32, smem, s>>>(perm, rec, offsets, tl, t1, t1y);
     }
     FK_LAUNCH();
     const int64_t M0 = g.M[0];
@@ -1416,19 +1400,19 @@ static int reduce_and_assemble(fkski_stats *st, const uint32_t *perm, const Rec4
         FK_TRY(sc.get(&t2, sizeof(T) * (size_t)(343 * (M0 - 3) * M1 * M2)));
         FK_TRY(sc.get(&t2y, sizeof(T) * (size_t)(4 * (M0 - 3) * M1 * M2)));
         AxisPass a1{7, 7, M0 - 3, M2, (int)(M1 - 3), (int)M1};
-        FK_TRY((launch_axis_pass<T, true>(t1, t2, a1, E, s)));
+        FK_TRY((launch_axis_pass<T, true>(t1, t2, a1, s)));
         AxisPass a0{1, 49, 1, M1 * M2, (int)(M0 - 3), (int)M0};
-        FK_TRY((launch_axis_pass<T, true>(t2, band, a0, E, s)));
+        FK_TRY((launch_axis_pass<T, true>(t2, band, a0, s)));
         AxisPass y1{4, 1, M0 - 3, M2, (int)(M1 - 3), (int)M1};
-        FK_TRY((launch_axis_pass<T, false>(t1y, t2y, y1, E, s)));
+        FK_TRY((launch_axis_pass<T, false>(t1y, t2y, y1, s)));
         AxisPass y0{1, 1, 1, M1 * M2, (int)(M0 - 3), (int)M0};
-        FK_TRY((launch_axis_pass<T, false>(t2y, wty, y0, E, s)));
+        FK_TRY((launch_axis_pass<T, false>(t2y, wty, y0, s)));
     } else if (D == 2) {
         const int64_t M1 = g.M[1];
         AxisPass a0{1, 7, 1, M1, (int)(M0 - 3), (int)M0};
-        FK_TRY((launch_axis_pass<T, true>(t1, band, a0, E, s)));
+        FK_TRY((launch_axis_pass<T, true>(t1, band, a0, s)));
         AxisPass y0{1, 1, 1, M1, (int)(M0 - 3), (int)M0};
-        FK_TRY((launch_axis_pass<T, false>(t1y, wty, y0, E, s)));
+        FK_TRY((launch_axis_pass<T, false>(t1y, wty, y0, s)));
     }
     // probes
     if (st->nprobes > 0) {
@@ -1455,13 +1439,13 @@ static int reduce_and_assemble(fkski_stats *st, const uint32_t *perm, const Rec4
             const int64_t M1 = g.M[1], M2 = g.M[2];
             FK_TRY(sc.get(&z2, sizeof(T) * (size_t)(st->nprobes * 4 * (M0 - 3) * M1 * M2)));
             AxisPass p1{(int64_t)st->nprobes * 4, 1, M0 - 3, M2, (int)(M1 - 3), (int)M1};
-            FK_TRY((launch_axis_pass<T, false>(z1, z2, p1, E, s)));
+            FK_TRY((launch_axis_pass<T, false>(z1, z2, p1, s)));
             AxisPass p0{(int64_t)st->nprobes, 1, 1, M1 * M2, (int)(M0 - 3), (int)M0};
-            FK_TRY((launch_axis_pass<T, false>(z2, wtz, p0, E, s)));
+            FK_TRY((launch_axis_pass<T, false>(z2, wtz, p0, s)));
         } else if (D == 2) {
             const int64_t M1 = g.M[1];
             AxisPass p0{(int64_t)st->nprobes, 1, 1, M1, (int)(M0 - 3), (int)M0};
-            FK_TRY((launch_axis_pass<T, false>(z1, wtz, p0, E, s)));
+            FK_TRY((launch_axis_pass<T, false>(z1, wtz, p0, s)));
         }
     }
     return FKSKI_OK;
