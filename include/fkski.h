@@ -42,7 +42,8 @@ extern "C" {
 #define FKSKI_E_NONFINITE (-3)     /* NaN or Inf in X, y or the probes                             */
 #define FKSKI_E_NOT_CONVERGED (-4) /* maxiter reached; outputs are still written, info filled      */
 #define FKSKI_E_BREAKDOWN (-5)     /* CG breakdown: p^T A p <= 0 or a non-finite inner product      */
-#define FKSKI_E_TIMEOUT (-6)       /* a bounded device wait gave up (never a trap)                  */
+#define FKSKI_E_TIMEOUT (-6)       /* a bounded device wait gave up (reserved: no kernel of this
+                                      build waits on another; reductions use last-block counters) */
 #define FKSKI_E_OOM (-7)           /* device allocation failed                                      */
 #define FKSKI_E_CUDA (-8)          /* another CUDA runtime error                                    */
 #define FKSKI_E_UNSUPPORTED (-9)   /* a size beyond what this build supports (see each call)        */
