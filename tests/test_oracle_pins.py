@@ -196,6 +196,23 @@ def test_rademacher_splitmix_golden(oracle_mod):
 
 # ----------------------------------------------------------------- K_G (Sec. 2.2)
 
+def test_kernel_values_golden(oracle_mod):
+    """The kernel conventions by number: the RBF's 1/2 inside the exponent, the scale factor,
+    ARD per-axis lengthscales, the Matern-5/2 polynomial, and the lengthscale derivative
+    (tests/golden/kernel_values.txt, closed forms evaluated independently)."""
+    from oracle import core
+    for kind, s, ell, off, val, *_ in _load("kernel_values.txt"):
+        ell_v = tuple(float(v) for v in ell.split(","))
+        diff = np.array([[float(v) for v in off.split(",")]])
+        ktype = synth.MATERN52 if kind == "matern52" else synth.RBF
+        kern = synth.Kernel(ktype, ell_v, float(s), 1.0)
+        if kind == "d_l0":
+            got = core.kernel_dvalue(kern, diff, ("ell", 0))[0]
+        else:
+            got = core.kernel_value(kern, diff)[0]
+        assert got == pytest.approx(float(val), rel=1e-14), (kind, s, ell, off)
+
+
 @pytest.mark.parametrize("d", [1, 2, 3])
 def test_kg_kronecker_equals_dense(oracle_mod, d):
     from oracle import core
