@@ -1,7 +1,8 @@
 /*
  * fkski CPU oracle -- TEST INFRASTRUCTURE ONLY.
  *
- * Plain, slow, single-threaded FP64 definitions of what the GPU path computes.  It shares no code
+ * Plain, slow FP64 definitions of what the GPU path computes (the precompute uses OpenMP threads
+ * over disjoint cell slabs with a fixed summation order, so results do not depend on them).  It shares no code
  * with the CUDA library and is used only by tests/, by __graft_entry__.smoke() and by the
  * cpu_baseline leg of bench.py.  Build with -ffp-contract=off so that the float sequence that
  * decides a cell index is evaluated exactly as written.
@@ -21,6 +22,9 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -228,59 +232,63 @@ int or_w_rows(const or_grid *g, const void *X, int xdtype, int64_t n, int64_t *c
 }
 
 /* ------------------------------------------------------------------ sufficient statistics
- * W^T W = sum_i w_i w_i^T, W^T y = sum_i y_i w_i, y^T y = sum_i y_i^2 (Sec. 3.1), accumulated
- * point by point in input order in FP64.  W^T W is stored as its 7^d diagonals (Claim 2: entries
- * are nonzero only for grid offsets delta in {-3..3}^d):
+ * W^T W = sum_i w_i w_i^T, W^T y = sum_i y_i w_i, y^T y = sum_i y_i^2 (Sec. 3.1) in FP64.
+ * W^T W is stored as its 7^d diagonals (Claim 2: entries are nonzero only for grid offsets delta
+ * in {-3..3}^d):
  *   band[o * m + j] = (W^T W)[j, j + delta(o)],  o = sum_k (delta_k + 3) 7^(d-1-k).
  * Probe statistics: wtz[p * m + j] = (W^T z_p)[j] with z_p(i) = or_rademacher(seed, p, i).
  * Sort: perm is the stable sort of points by linear cell key (ties by input index);
- * offsets[c] .. offsets[c+1] is the segment of cell c.  Any output pointer may be NULL. */
-int or_precompute(const or_grid *g, const void *X, int xdtype, const void *y, int64_t n,
-                  int nprobe, uint64_t seed, uint32_t *keys, int64_t *perm, int64_t *offsets,
-                  double *band, double *wty, double *yty, double *wtz)
+ * offsets[c] .. offsets[c+1] is the segment of cell c.  Any output pointer may be NULL.
+ *
+ * Summation order (fixed, whatever the number of threads): points are summed in sorted order
+ * (cell key, then input index).  Threads own disjoint slabs of cells: slab s holds the cells
+ * whose first-axis index lies in [4s, 4s + 4), so its points touch grid nodes [4s, 4s + 6] on
+ * that axis; the even slabs run first (their node ranges are disjoint, so they run in
+ * parallel), then the odd slabs.  Every entry therefore receives its terms in one order: the
+ * even slab's points in sorted order, then the odd slab's.  y^T y is summed per slab and the
+ * slab sums are added in slab order. */
+static void point_terms(const or_grid *g, const int64_t cell[3], const double t[3], int64_t node[64],
+                        double wv[64], int aidx[64][3])
 {
     const int d = g->d;
-    if (d < 1 || d > 3 || n < 1) return OR_E_INVALID;
-    int64_t m = 1, ncell = 1;
-    for (int k = 0; k < d; ++k) {
-        if (g->M[k] < 4 || !(g->h[k] > 0.0)) return OR_E_INVALID;
-        m *= g->M[k];
-        ncell *= g->M[k] - 3;
-    }
     const int64_t nnz = ipow(4, d);
-    const int64_t nband = ipow(7, d);
-    uint32_t *kk = keys ? keys : (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
-    if (!kk) return OR_E_OOM;
-    if (band) memset(band, 0, sizeof(double) * (size_t)(nband * m));
-    if (wty) memset(wty, 0, sizeof(double) * (size_t)m);
-    if (wtz && nprobe > 0) memset(wtz, 0, sizeof(double) * (size_t)(nprobe * m));
+    double w[3][4];
+    for (int k = 0; k < d; ++k) or_keys_weights(t[k], w[k]);
+    for (int64_t q = 0; q < nnz; ++q) {
+        int64_t rem = q, nd = 0;
+        double v = 1.0;
+        int a[3] = {0, 0, 0};
+        for (int k = d - 1; k >= 0; --k) { a[k] = (int)(rem % 4); rem /= 4; }
+        for (int k = 0; k < d; ++k) {
+            nd = nd * g->M[k] + (cell[k] - 1 + a[k]);
+            v *= w[k][a[k]];
+            aidx[q][k] = a[k];
+        }
+        node[q] = nd;
+        wv[q] = v;
+    }
+}
+
+/* Accumulate the points perm[b..e) (one slab, sorted order) into the statistics; returns the slab's
+ * sum of y_i^2. */
+static double slab_sums(const or_grid *g, const void *X, int xdtype, const void *y, int64_t n, int nprobe,
+                        uint64_t seed, const int64_t *perm, int64_t b, int64_t e, int64_t m,
+                        double *band, double *wty, double *wtz)
+{
+    const int d = g->d;
+    const int64_t nnz = ipow(4, d);
     double yy = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
+    for (int64_t s = b; s < e; ++s) {
+        const int64_t i = perm[s];
         int64_t cell[3];
-        double t[3], w[3][4];
-        int st = point_cell(g, X, xdtype, n, i, cell, t);
-        if (st) { if (!keys) free(kk); return st; }
-        double yi = xdtype == 0 ? (double)((const float *)y)[i] : ((const double *)y)[i];
-        if (!isfinite(yi)) { if (!keys) free(kk); return OR_E_NONFINITE; }
-        kk[i] = cell_linear(g, cell);
-        for (int k = 0; k < d; ++k) or_keys_weights(t[k], w[k]);
+        double t[3];
+        point_cell(g, X, xdtype, n, i, cell, t);  /* checked when the keys were formed */
+        const double yi = xdtype == 0 ? (double)((const float *)y)[i] : ((const double *)y)[i];
         yy += yi * yi;
         int64_t node[64];
         double wv[64];
         int aidx[64][3];
-        for (int64_t q = 0; q < nnz; ++q) {
-            int64_t rem = q, nd = 0;
-            double v = 1.0;
-            int a[3] = {0, 0, 0};
-            for (int k = d - 1; k >= 0; --k) { a[k] = (int)(rem % 4); rem /= 4; }
-            for (int k = 0; k < d; ++k) {
-                nd = nd * g->M[k] + (cell[k] - 1 + a[k]);
-                v *= w[k][a[k]];
-                aidx[q][k] = a[k];
-            }
-            node[q] = nd;
-            wv[q] = v;
-        }
+        point_terms(g, cell, t, node, wv, aidx);
         if (band) {
             for (int64_t qa = 0; qa < nnz; ++qa) {
                 for (int64_t qb = 0; qb < nnz; ++qb) {
@@ -294,23 +302,117 @@ int or_precompute(const or_grid *g, const void *X, int xdtype, const void *y, in
             for (int64_t q = 0; q < nnz; ++q) wty[node[q]] += yi * wv[q];
         if (wtz)
             for (int p = 0; p < nprobe; ++p) {
-                double z = or_rademacher(seed, p, i);
+                const double z = or_rademacher(seed, p, i);
                 for (int64_t q = 0; q < nnz; ++q) wtz[(int64_t)p * m + node[q]] += z * wv[q];
             }
     }
-    if (yty) *yty = yy;
-    if (perm || offsets) {
-        int64_t *cnt = (int64_t *)calloc((size_t)(ncell + 1), sizeof(int64_t));
-        if (!cnt) { if (!keys) free(kk); return OR_E_OOM; }
+    return yy;
+}
+
+int or_precompute(const or_grid *g, const void *X, int xdtype, const void *y, int64_t n,
+                  int nprobe, uint64_t seed, uint32_t *keys, int64_t *perm, int64_t *offsets,
+                  double *band, double *wty, double *yty, double *wtz)
+{
+    const int d = g->d;
+    if (d < 1 || d > 3 || n < 1) return OR_E_INVALID;
+    int64_t m = 1, ncell = 1;
+    for (int k = 0; k < d; ++k) {
+        if (g->M[k] < 4 || !(g->h[k] > 0.0)) return OR_E_INVALID;
+        m *= g->M[k];
+        ncell *= g->M[k] - 3;
+    }
+    const int64_t nband = ipow(7, d);
+    uint32_t *kk = keys ? keys : (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    int64_t *pp = perm ? perm : (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *cnt = (int64_t *)calloc((size_t)(ncell + 1), sizeof(int64_t));
+    if (!kk || !pp || !cnt) {
+        if (!keys) free(kk);
+        if (!perm) free(pp);
+        free(cnt);
+        return OR_E_OOM;
+    }
+    /* cell keys (independent per point); the error reported is the first point's in input order */
+    int64_t bad_i = n;
+    int bad_st = OR_OK;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t cell[3];
+        double t[3];
+        int st = point_cell(g, X, xdtype, n, i, cell, t);
+        if (st == OR_OK) {
+            const double yi = xdtype == 0 ? (double)((const float *)y)[i] : ((const double *)y)[i];
+            if (!isfinite(yi)) st = OR_E_NONFINITE;
+        }
+        if (st != OR_OK) {
+#pragma omp critical
+            if (i < bad_i) { bad_i = i; bad_st = st; }
+            kk[i] = 0;
+        } else {
+            kk[i] = cell_linear(g, cell);
+        }
+    }
+    int rc = bad_st;
+    if (rc == OR_OK) {
+        /* stable counting sort by key */
         for (int64_t i = 0; i < n; ++i) cnt[kk[i] + 1] += 1;
         for (int64_t c = 0; c < ncell; ++c) cnt[c + 1] += cnt[c];
         if (offsets) memcpy(offsets, cnt, sizeof(int64_t) * (size_t)(ncell + 1));
-        if (perm)
-            for (int64_t i = 0; i < n; ++i) perm[cnt[kk[i]]++] = i;
-        free(cnt);
+        {
+            int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ncell + 1));
+            if (!pos) rc = OR_E_OOM;
+            else {
+                memcpy(pos, cnt, sizeof(int64_t) * (size_t)(ncell + 1));
+                for (int64_t i = 0; i < n; ++i) pp[pos[kk[i]]++] = i;
+                free(pos);
+            }
+        }
     }
+    if (rc == OR_OK && (band || wty || wtz || yty)) {
+        if (band) memset(band, 0, sizeof(double) * (size_t)(nband * m));
+        if (wty) memset(wty, 0, sizeof(double) * (size_t)m);
+        if (wtz && nprobe > 0) memset(wtz, 0, sizeof(double) * (size_t)(nprobe * m));
+        const int64_t per0 = ncell / (g->M[0] - 3);   /* cells per first-axis index */
+        const int64_t nslab = (g->M[0] - 3 + 3) / 4;
+        double *yslab = (double *)calloc((size_t)nslab, sizeof(double));
+        if (!yslab) rc = OR_E_OOM;
+        for (int phase = 0; phase < 2 && rc == OR_OK; ++phase) {
+#pragma omp parallel for schedule(dynamic, 1)
+            for (int64_t sl = phase; sl < nslab; sl += 2) {
+                const int64_t c0 = 4 * sl, c1 = c0 + 4 < g->M[0] - 3 ? c0 + 4 : g->M[0] - 3;
+                yslab[sl] = slab_sums(g, X, xdtype, y, n, nprobe, seed, pp, cnt[c0 * per0], cnt[c1 * per0], m,
+                                      band, wty, wtz);
+            }
+        }
+        if (rc == OR_OK && yty) {
+            double yy = 0.0;
+            for (int64_t sl = 0; sl < nslab; ++sl) yy += yslab[sl];
+            *yty = yy;
+        }
+        free(yslab);
+    }
+    free(cnt);
     if (!keys) free(kk);
-    return OR_OK;
+    if (!perm) free(pp);
+    return rc;
+}
+
+/* Threads the oracle may use (OpenMP); 0 leaves the OpenMP default. */
+void or_set_threads(int k)
+{
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* Posterior mean at test points: mu(x*) = w_{x*}^T v (Def. 1 mean; Fact 2 mean with v = z_bar). */

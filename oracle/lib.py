@@ -18,11 +18,12 @@ def lib_path() -> str:
 
 
 def build(force: bool = False) -> str:
-    """Compile fkski_oracle.c with gcc (-ffp-contract=off keeps the key arithmetic as written)."""
+    """Compile fkski_oracle.c with gcc (-ffp-contract=off keeps the key arithmetic as written;
+    -fopenmp for the precompute's cell-slab threads)."""
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC",
            _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
@@ -68,6 +69,10 @@ def get():
         L.or_precompute.argtypes = [ctypes.POINTER(OrGrid), P, ctypes.c_int, P, ctypes.c_int64,
                                     ctypes.c_int, ctypes.c_uint64, P, P, P, P, P, P, P]
         L.or_predict.argtypes = [ctypes.POINTER(OrGrid), P, P, ctypes.c_int, ctypes.c_int64, P]
+        L.or_set_threads.argtypes = [ctypes.c_int]
+        L.or_set_threads.restype = None
+        L.or_max_threads.argtypes = []
+        L.or_max_threads.restype = ctypes.c_int
         for f in ("or_keys", "or_w_rows", "or_precompute", "or_predict", "or_cell_key_f32",
                   "or_cell_key_f64"):
             getattr(L, f).restype = ctypes.c_int
