@@ -3,8 +3,10 @@
 One step = the whole hot path on the radar-shaped 3-D workload (n = 20 volumes x 14 sweeps x 720
 azimuths x 593 gates = 119,548,800 FP32 points, grid 128 x 128 x 32, m = 524,288; Sec. 5's 120M
 radar run): precompute of W^T W / W^T y (cell keys, stable sort, per-cell reduction, band
-assembly), the factorized-CG posterior mean (spectra, SpMV + K_G per iteration, rtol 1e-5) and
-prediction at 65,536 test points.  Inputs are resident in HBM and far larger than L2.
+assembly), the factorized-CG posterior mean run to its tolerance (spectra, SpMV + K_G per
+iteration, rtol 1e-5, MIXED: double-float arithmetic on the FP32 band) and prediction at 65,536
+test points.  Inputs are resident in HBM and far larger than L2.  The line reports the solve's
+status, iterations, final relative residual and time to solution.
 
 value      = precompute throughput (Gpoints/s), the metric's first quantity; ms/CG iteration,
              the fwd+bwd log-likelihood step on the gradient workload (n = 1e7, 64^3 grid, 16
@@ -157,8 +159,8 @@ def radar_problem(volumes: int, device: str):
 
 
 def cpu_oracle_precompute_rate(X: np.ndarray, y: np.ndarray, grid, sample: int, repeats: int = 1):
-    """The CPU oracle (single-threaded C, FP64) computing W^T W, W^T y, y^T y and the stable cell
-    sort on the first `sample` points; returns (Gpoints/s, seconds)."""
+    """The CPU oracle (C, FP64, OpenMP over cell slabs on every host core) computing W^T W, W^T y,
+    y^T y and the stable cell sort on the first `sample` points; returns (Gpoints/s, seconds)."""
     import oracle
     from oracle import core
     oracle.build()
@@ -171,6 +173,69 @@ def cpu_oracle_precompute_rate(X: np.ndarray, y: np.ndarray, grid, sample: int, 
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
     return sample / best / 1e9, best
+
+
+def host_info():
+    """Host cores and CPU model (nproc, lscpu) of the machine the CPU baseline runs on."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Architecture", "CPU(s)", "Thread(s) per core", "Socket(s)"):
+                info[k.strip()] = v.strip()
+    except Exception:
+        pass
+    return info
+
+
+def cpu_baseline_suite(prob, sample_all: int, sample_one: int):
+    """The FP64 CPU oracle as it stands, on the host cores (OpenMP precompute over cell slabs) and
+    on one core: precompute on bounded samples of the four workloads, and the n-space CG (Alg. 1,
+    plain SKI, CSR W + K_G) per iteration on c1-c3 (numpy/scipy, n sampled for c3).  Returns the
+    cpu_baseline object of the JSON line (value: radar precompute on all cores)."""
+    import oracle
+    from oracle import core, lib
+    from paper_2101_11751_gb300 import synth
+    oracle.build()
+    L = lib.get()
+    ncores = os.cpu_count() or 1
+    out = {"kind": "oracle", "host": host_info()}
+    work = {"c1 sine_1d": synth.sine_1d(), "c2 gmm_2d": synth.gmm_2d(n=max(sample_all, sample_one)),
+            "c3 grf_3d": synth.grf_3d(n=max(sample_all, sample_one)), "c4 radar_3d": prob}
+    pre = {}
+    for name, pr in work.items():
+        res = {}
+        for label, k, ns in (("all_cores", ncores, sample_all), ("one_core", 1, sample_one)):
+            L.or_set_threads(k)
+            ns = min(ns, pr.n)
+            Xs = np.ascontiguousarray(pr.X[:, :ns])
+            ys = np.ascontiguousarray(pr.y[:ns])
+            t0 = time.perf_counter()
+            core.precompute(pr.grid, Xs, ys)
+            dt = time.perf_counter() - t0
+            res[label] = {"points": int(ns), "threads": k, "s": dt, "gpoints_per_s": ns / dt / 1e9}
+        pre[name] = res
+    L.or_set_threads(ncores)
+    out["precompute"] = pre
+    cg_ms = {}
+    for name in ("c1 sine_1d", "c2 gmm_2d", "c3 grf_3d"):
+        pr = work[name]
+        ns = min(pr.n, 1_000_000)
+        W = core.w_csr(pr.grid, np.ascontiguousarray(pr.X[:, :ns]))
+        mv = core.ski_operator(pr.grid, pr.kernel, W)
+        b = np.asarray(pr.y[:ns], dtype=np.float64)
+        core.cg(mv, b, None, 0.0, 2)
+        t0 = time.perf_counter()
+        core.cg(mv, b, None, 0.0, 10)
+        cg_ms[name] = {"n": int(ns), "m": int(pr.grid.m), "ms_per_iter": (time.perf_counter() - t0) / 10 * 1e3}
+    out["nspace_cg"] = cg_ms
+    r4 = pre["c4 radar_3d"]["all_cores"]
+    out.update(value=r4["gpoints_per_s"], unit="Gpoints/s", cores=ncores,
+               sample=f"first {r4['points']} radar points, W^T W / W^T y / stable sort in FP64 on {ncores} "
+                      f"threads ({r4['s']:.1f} s); one core: {pre['c4 radar_3d']['one_core']['gpoints_per_s']:.3g} "
+                      f"Gpoints/s on {pre['c4 radar_3d']['one_core']['points']} points")
+    return out
 
 
 def per_iter_ms(run, k1: int = 32, k2: int = 96) -> float:
@@ -215,19 +280,21 @@ def serving_batch(api, synth, dev, reps: int = 3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sts = api.precompute_batched(Xs, ys, grids)
-        a, v, info = api.solve_batched(sts, kerns, rtol=1e-4, maxiter=4000, allow_not_converged=True)
+        a, v, info = api.solve_batched(sts, kerns, rtol=1e-4, maxiter=20000, allow_not_converged=True)
         mus = api.predict_batched(sts, v, Xt)
         torch.cuda.synchronize()
         if r > 0:
             times.append(time.perf_counter() - t0)
         iters = [i["iters"] for i in info]
+        n_conv = sum(1 for i in info if i["status"] == api.OK)
         for st in sts:
             st.close()
     n_total = sum(p.X.shape[1] for p in probs)
     t = statistics.mean(times)
     return {"workload": "batch_2d: 64 problems, n ~ log-U[1e4, 2e6], grids 32..256^2, 1e5 test points each",
             "points": int(n_total), "ms": t * 1e3, "problems_per_s": len(probs) / t,
-            "gpoints_per_s": n_total / t / 1e9, "cg_iters_max": int(max(iters)), "cg_iters_median": float(np.median(iters))}
+            "gpoints_per_s": n_total / t / 1e9, "cg_iters_max": int(max(iters)), "cg_iters_median": float(np.median(iters)),
+            "converged": f"{n_conv}/{len(probs)}"}
 
 
 def sine_sweep(api, synth, dev):
@@ -248,6 +315,7 @@ def reference_arm(args):
         return
     prob = radar_problem(args.volumes, "cpu")
     sample = args.ref_sample
+    cores = os.cpu_count() or 1  # the oracle's OpenMP threads (its default: every host core)
     for _ in range(args.warmup):
         cpu_oracle_precompute_rate(prob.X, prob.y, prob.grid, sample)
     times = []
@@ -260,8 +328,9 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"radar_3d sample of {sample} points (precompute only)", "grid": "128x128x32"},
-            "cpu_baseline": {"value": v, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {sample} radar points, W^T W / W^T y / sort in FP64"},
+            "cpu_baseline": {"value": v, "unit": "Gpoints/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first {sample} radar points, W^T W / W^T y / sort in FP64, "
+                                       f"{cores} OpenMP threads", "host": host_info()},
             "e2e": {"value": v, "unit": "Gpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -276,9 +345,12 @@ def main():
     ap.add_argument("--volumes", type=int, default=20, help="radar volumes (20 = 119.5M points)")
     ap.add_argument("--no-grad", action="store_true", help="skip the fwd+bwd log-likelihood section")
     ap.add_argument("--grad-n", type=int, default=10_000_000)
-    ap.add_argument("--ref-sample", type=int, default=200_000)
-    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
-    ap.add_argument("--maxiter", type=int, default=4000)
+    ap.add_argument("--ref-sample", type=int, default=1_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000, help="points per workload, all host cores")
+    ap.add_argument("--cpu-sample-one", type=int, default=100_000, help="points per workload, one core")
+    ap.add_argument("--maxiter", type=int, default=60000)
+    ap.add_argument("--grad-maxiter", type=int, default=4096)
+    ap.add_argument("--no-iter-vs-n", action="store_true", help="skip ms/iteration at n = 1e7, 3e7, 1.2e8")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     ap.add_argument("--no-ski", action="store_true", help="skip the plain-SKI per-iteration comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem serving batch")
@@ -315,7 +387,7 @@ def main():
         st = api.precompute(Xd, yd, grid)
         if ev:
             ev[1].record(stream)
-        a, v, info = api.solve(st, kern, rtol=rtol, maxiter=args.maxiter, check_every=16, allow_not_converged=True)
+        a, v, info = api.solve(st, kern, rtol=rtol, maxiter=args.maxiter, check_every=32, allow_not_converged=True)
         if ev:
             ev[2].record(stream)
         mu = api.predict(st, v, Xsd)
@@ -332,12 +404,14 @@ def main():
     sampler.start()
     launches0 = api._lib.fkski_kernel_launches()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    iters = []
+    iters, statuses, resids = [], [], []
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
     for k in range(args.steps):
         info, mu = step(X, y, Xs, evs[k])
         iters.append(info["iters"])
+        statuses.append(info["status"])
+        resids.append(info["rel_residual"])
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     launches = api._lib.fkski_kernel_launches() - launches0
@@ -349,6 +423,8 @@ def main():
     pre_ms_max = dist_max(dist, pre_ms, dev)
     step_ms_max = dist_max(dist, step_ms, dev)
     cg_iters = int(statistics.median(iters))
+    status_names = {api.OK: "OK", api.E_NOT_CONVERGED: "NOT_CONVERGED", api.E_BREAKDOWN: "BREAKDOWN"}
+    solve_status = status_names.get(max(statuses, key=lambda c: c != api.OK), str(statuses[0]))
 
     # kernel-level timings on the same data: banded SpMV and K_G (burst, events on this stream)
     st = api.precompute(X, y, grid)
@@ -383,6 +459,8 @@ def main():
         e2e_pre.append(time.perf_counter() - t0)
         st.close()
         del Xd, yd
+        if k >= 2:
+            continue  # the whole step (a converged solve) from host buffers: two passes
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Xd = Xh.to(dev, non_blocking=True)
@@ -439,24 +517,42 @@ def main():
         Xg = torch.from_numpy(gp.X).to(dev)
         yg = torch.from_numpy(gp.y).to(dev)
         sg = api.precompute(Xg, yg, gp.grid, n_probes=16, probe_seed=0)
-        api.grad(sg, gp.kernel, rtol=1e-4, maxiter=args.maxiter)   # warm-up
+        gmax = args.grad_maxiter
+        api.grad(sg, gp.kernel, rtol=1e-4, maxiter=gmax, allow_not_converged=True)   # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        Lg, gg, ginfo = api.grad(sg, gp.kernel, rtol=1e-4, maxiter=args.maxiter)
+        Lg, gg, ginfo = api.grad(sg, gp.kernel, rtol=1e-4, maxiter=gmax, allow_not_converged=True)
         torch.cuda.synchronize()
         fwd_bwd_ms = (time.perf_counter() - t0) * 1e3
         t0 = time.perf_counter()
-        Lf, finfo = api.loglik_forward(sg, gp.kernel, rtol=1e-4, maxiter=args.maxiter, precision=api.DOUBLE)
+        Lf, finfo = api.loglik_forward(sg, gp.kernel, rtol=1e-4, maxiter=gmax, precision=api.DOUBLE,
+                                       allow_not_converged=True)
         torch.cuda.synchronize()
         plain_ms = (time.perf_counter() - t0) * 1e3
         sg.close()
-        grad_info = {"workload": f"grf_3d n={gp.n} grid 64^3 (m={gp.grid.m}) RBF ARD, 16 Rademacher probes",
+        grad_info = {"workload": f"grf_3d n={gp.n} grid 64^3 (m={gp.grid.m}) RBF ARD, 16 Rademacher probes, rtol 1e-4",
                      "fwd_bwd_ms": fwd_bwd_ms, "plain_fp64_fwd_ms": plain_ms,
                      "fwd_bwd_over_plain_fwd": fwd_bwd_ms / plain_ms,
                      "loglik_mixed": Lg, "loglik_fp64": Lf, "grad": gg,
+                     "status_mixed": status_names.get(ginfo["status"], str(ginfo["status"])),
+                     "status_fp64": status_names.get(finfo["status"], str(finfo["status"])),
+                     "rel_residual_mixed": ginfo["rel_residual"], "rel_residual_fp64": finfo["rel_residual"],
                      "cg_iters_mixed_max": max(ginfo["iters"]), "cg_iters_fp64_max": max(finfo["iters"])}
 
     # plain SKI vs the factorized solver, per iteration (radar workload and the sine sweep)
+    # per-iteration time at the radar shape for growing n (Sec. 3.2: independent of n)
+    iter_vs_n = None
+    if not args.no_iter_vs_n:
+        iter_vs_n = []
+        npv = prob.meta["points_per_volume"]
+        for vols in (1, 3, 20):  # n = 6.0e6, 1.8e7, 1.2e8
+            nn = vols * npv
+            st_n = api.precompute(X[:, :nn].contiguous(), y[:nn].contiguous(), grid)
+            ms = per_iter_ms(lambda k: api.solve(st_n, kern, rtol=0.0, maxiter=k, check_every=32,
+                                                 allow_not_converged=True), 64, 576)
+            st_n.close()
+            iter_vs_n.append({"n": int(nn), "ms_per_cg_iter": ms})
+
     comparison = None
     if not args.no_ski:
         comparison = [ski_vs_gsgp(api, synth, dev, X, y, grid, kern, "radar_3d (this step's workload)")]
@@ -467,10 +563,7 @@ def main():
     # CPU oracle baseline (rank 0 at N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample > 0:
-        rate, secs = cpu_oracle_precompute_rate(prob.X, prob.y, grid, args.cpu_sample)
-        cpu = {"value": rate, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {args.cpu_sample} radar points, W^T W / W^T y / stable sort in FP64 "
-                         f"({secs:.1f} s)"}
+        cpu = cpu_baseline_suite(prob, args.cpu_sample, args.cpu_sample_one)
 
     if rank != 0:
         return
@@ -488,6 +581,8 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "precompute_ms": pre_ms_max, "precompute_hbm_frac": pre_bytes / (pre_ms_max / 1e3) / 1e9 / hbm_peak,
         "solve_ms": sol_ms, "predict_ms": pred_ms, "cg_iters": cg_iters,
+        "solve_status": solve_status, "rel_residual": max(resids), "time_to_solution_ms": sol_ms,
+        "solver": "factorized CG, Alg. 5 start (x0 = y / sigma^2), MIXED (double-float on the FP32 band)",
         "ms_per_cg_iter": sol_ms / max(cg_iters, 1),
         "roofline": {"kernel": SPMV_KERNEL + " (W^T W x, 172 of the 343 FP32 diagonals)", "bound": "hbm", "achieved": spmv_gbs,
                      "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": spmv_gbs / hbm_peak,
@@ -515,6 +610,8 @@ def main():
     }
     if grad_info is not None:
         line["grad"] = grad_info
+    if iter_vs_n is not None:
+        line["iter_vs_n"] = iter_vs_n
     if comparison is not None:
         line["ski_vs_gsgp"] = comparison
     if batch is not None:

@@ -59,14 +59,21 @@ extern "C" {
                                 y_hat from a few CG steps on W^T W (see fkski_solve)            */
 #define FKSKI_X0_Y_OVER_S2 1 /* Alg. 5 (simplified EFCG, x0 = y / sigma^2, r0 in span(W))            */
 
-#define FKSKI_MIXED 0  /* FP32 band, FFT and Krylov vectors; FP64 solution, scalars, cross-warp
-                          inner-product sums, and the periodic true-residual replacement.
-                          Attainable accuracy: every FP32 K_G / band product carries a normwise
-                          rounding error near 1e-6, which a CG step on A = W K W^T + sigma^2 I
-                          amplifies by up to ||A|| / sigma^2.  On ill-conditioned systems rtol
-                          much below 1e-5 can then end in FKSKI_E_NOT_CONVERGED or
-                          FKSKI_E_BREAKDOWN; use FKSKI_DOUBLE for such tolerances.          */
-#define FKSKI_DOUBLE 1 /* FP64 throughout                                                      */
+#define FKSKI_MIXED 0  /* FP32 band (the bulk of the bytes), every other vector and all operator
+                          arithmetic in double-float form (pairs of FP32 numbers combined by
+                          error-free transformations, about 46-bit accuracy) on the FP32 pipes;
+                          FP64 solution, scalars and cross-warp inner-product sums.  The
+                          products carry rounding near 1e-14 instead of FP32's 1e-7, so the CG
+                          iteration counts follow those of FP64 CG.  Outputs are FP32.       */
+#define FKSKI_DOUBLE 1 /* FP64 throughout (GB300's FP64 pipe is far slower than its FP32 pipe)  */
+#define FKSKI_FP32 2   /* FP32 band, FFT and Krylov vectors; FP64 solution, scalars, cross-warp
+                          inner-product sums, and the periodic true-residual replacement with
+                          an FP64 SpMV and K_G ("reliable updates").  The fastest iteration, but
+                          every FP32 K_G / band product carries a normwise rounding error near
+                          1e-7..1e-6 that a CG step on A = W K W^T + sigma^2 I amplifies by up to
+                          ||A|| / sigma^2: iteration counts grow well beyond FP64 CG's, and on
+                          ill-conditioned systems rtol much below 1e-5 can end in
+                          FKSKI_E_NOT_CONVERGED or FKSKI_E_BREAKDOWN.  Outputs are FP32.      */
 
 /* ------------------------------------------------------------------ configuration structs */
 
@@ -93,7 +100,7 @@ typedef struct {
     double rtol;          /* stop when ||r_k||_2 <= rtol * ||b||_2, b = y or the probe z_p      */
     int maxiter;          /* CG iteration cap                                                  */
     int x0_mode;          /* FKSKI_X0_ZERO or FKSKI_X0_Y_OVER_S2 (fkski_solve only)             */
-    int precision;        /* FKSKI_MIXED or FKSKI_DOUBLE                                       */
+    int precision;        /* FKSKI_MIXED, FKSKI_DOUBLE or FKSKI_FP32                           */
     int check_every;      /* iterations per captured CUDA graph between host convergence checks */
     int n_probes;         /* Rademacher probes accumulated by fkski_precompute (<= 64)         */
     uint64_t probe_seed;  /* probe z_p(i) = sign of SplitMix64(seed) output k = p*2^40 + i + 1 */
@@ -225,17 +232,17 @@ FKSKI_API int fkski_band_mvm(const fkski_stats *st, const void *x, void *u, int 
 /* ------------------------------------------------------------------ posterior mean (Sec. 4, App. B)
  * Solves the SKI system (W K_G W^T + sigma^2 I) z = y by factorized CG using only the sufficient
  * statistics: Alg. 5 (x0 = y/sigma^2) or Alg. 3 (x0 = 0), one B(x) = [(K_G W^T W + sigma^2 I)x,
- * W^T W x] per iteration.  Outputs (device, m entries, FP32 for MIXED / FP64 for DOUBLE):
+ * W^T W x] per iteration.  Outputs (device, m entries, FP32 for MIXED and FP32, FP64 for DOUBLE):
  *   a_out = W^T z   and   v_out = K_G W^T z  (= z_bar, the GSGP posterior mean of theta, Fact 2).
  * With x0 = 0 the paper's Alg. 3 represents iterates as W v_hat + c y; here y is first split as
  * y = W y_hat + y' (y_hat: 8 CG steps on W^T W y_hat = W^T y) and iterates as W v_hat + c y'.
  * Both are exact; the split keeps y's out-of-range(W) part (an eigenvector of A) from cancelling
  * against in-range terms in the inner products of Claim 4, which otherwise costs ~30% more
  * iterations in FP64 and breaks down in FP32.
- * MIXED: at the end of a chunk of opts->check_every iterations, a right-hand side whose residual
+ * FP32: at the end of a chunk of opts->check_every iterations, a right-hand side whose residual
  * fell 10x since its last replacement (or below the tolerance) gets the true residual of its FP64
  * solution (FP64 SpMV and FP64 K_G) in place of the recursive one; convergence is declared only
- * on that true residual.
+ * on that true residual.  MIXED and DOUBLE test the recursive residual, as the paper's EFCG does.
  * Stops when ||r_k|| <= rtol ||y||.  info (host, may be NULL) receives iterations and residual.
  * Returns OK, NOT_CONVERGED (outputs written), BREAKDOWN, INVALID_ARG, OOM, CUDA.
  * Synchronizes the stream every opts->check_every iterations to test convergence. */

@@ -85,6 +85,19 @@ def keys(grid, X: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
     return k, t
 
 
+def cell_sort(grid, X: np.ndarray, y: np.ndarray) -> Dict[str, np.ndarray]:
+    """The precompute's cell sort alone (Sec. 3.1 reading: stable by cell key, ties by input
+    index): keys, perm and segment offsets, O(n)."""
+    X = np.ascontiguousarray(X)
+    y = np.ascontiguousarray(y, dtype=X.dtype)
+    n = X.shape[1]
+    out = dict(keys=np.zeros(n, np.uint32), perm=np.zeros(n, np.int64),
+               offsets=np.zeros(grid.ncells + 1, np.int64))
+    _check(get().or_precompute(or_grid(grid), ptr(X), _xdtype(X), ptr(y), n, 0, 0, ptr(out["keys"]),
+                               ptr(out["perm"]), ptr(out["offsets"]), None, None, None, None))
+    return out
+
+
 def rademacher(seed: int, j: int, n: int) -> np.ndarray:
     """Probe j: z(i) = +-1 from SplitMix64 at counter j*2^40 + i + 1."""
     out = np.zeros(n)

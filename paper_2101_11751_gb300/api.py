@@ -21,7 +21,7 @@ E_BREAKDOWN, E_TIMEOUT, E_OOM, E_CUDA, E_UNSUPPORTED, E_IO = -5, -6, -7, -8, -9,
 F32, F64 = 0, 1
 RBF, MATERN52 = 0, 1
 X0_ZERO, X0_Y_OVER_S2 = 0, 1
-MIXED, DOUBLE = 0, 1
+MIXED, DOUBLE, FP32 = 0, 1, 2
 
 
 class FkskiError(RuntimeError):
@@ -321,7 +321,7 @@ def solve(st: Stats, kernel, rtol: float = 1e-6, maxiter: int = 1000, x0_mode: i
     """fkski_solve: returns (a = W^T z, v = K_G W^T z, info dict)."""
     load()
     m = st.info()["m"]
-    dt = torch.float32 if precision == MIXED else torch.float64
+    dt = torch.float64 if precision == DOUBLE else torch.float32
     a = torch.empty(m, dtype=dt, device="cuda")
     v = torch.empty(m, dtype=dt, device="cuda")
     o = opts(rtol=rtol, maxiter=maxiter, x0_mode=x0_mode, precision=precision, check_every=check_every)
@@ -426,7 +426,7 @@ def solve_batched(sts: Sequence[Stats], kernels, rtol: float = 1e-6, maxiter: in
     """fkski_solve_batched: returns lists a_p, v_p and per-problem info dicts."""
     load()
     P = len(sts)
-    dt = torch.float32 if precision == MIXED else torch.float64
+    dt = torch.float64 if precision == DOUBLE else torch.float32
     ms = [st.info()["m"] for st in sts]
     a = [torch.empty(m, dtype=dt, device="cuda") for m in ms]
     v = [torch.empty(m, dtype=dt, device="cuda") for m in ms]
@@ -465,7 +465,9 @@ def _grad_opts(rtol, maxiter, precision, budget, check_every):
 
 
 def loglik_forward(st: Stats, kernel, rtol=1e-4, maxiter=1000, precision=MIXED, budget=1 << 30,
-                   check_every=16, stream=None):
+                   check_every=16, stream=None, allow_not_converged: bool = False):
+    """fkski_loglik_forward: (L, info).  Raises FkskiError when a solve stops at maxiter unless
+    allow_not_converged is set (then info['status'] is E_NOT_CONVERGED and L is approximate)."""
     load()
     L = ctypes.c_double()
     inf = CInfo()
@@ -473,9 +475,10 @@ def loglik_forward(st: Stats, kernel, rtol=1e-4, maxiter=1000, precision=MIXED, 
     k = c_kernel(kernel)
     code = _lib.fkski_loglik_forward(st.handle, ctypes.byref(k), ctypes.byref(o), ctypes.byref(L),
                                      ctypes.byref(inf), _stream(stream))
-    if code not in (OK, E_NOT_CONVERGED):
+    if not (allow_not_converged and code == E_NOT_CONVERGED):
         _check(code, "fkski_loglik_forward")
-    return L.value, dict(iters=list(inf.iters_rhs[: 1 + st.info()["n_probes"]]), status=code)
+    return L.value, dict(iters=list(inf.iters_rhs[: 1 + st.info()["n_probes"]]), status=code,
+                         rel_residual=inf.rel_residual)
 
 
 def loglik_backward(st: Stats, kernel, rtol=1e-4, maxiter=1000, precision=MIXED, budget=1 << 30,
@@ -490,7 +493,10 @@ def loglik_backward(st: Stats, kernel, rtol=1e-4, maxiter=1000, precision=MIXED,
     return list(g)
 
 
-def grad(st: Stats, kernel, rtol=1e-4, maxiter=1000, precision=MIXED, check_every=16, stream=None):
+def grad(st: Stats, kernel, rtol=1e-4, maxiter=1000, precision=MIXED, check_every=16, stream=None,
+         allow_not_converged: bool = False):
+    """fkski_grad: (L, gradient, info).  Raises FkskiError when a solve stops at maxiter unless
+    allow_not_converged is set."""
     load()
     d = st.grid.d
     L = ctypes.c_double()
@@ -500,9 +506,10 @@ def grad(st: Stats, kernel, rtol=1e-4, maxiter=1000, precision=MIXED, check_ever
     k = c_kernel(kernel)
     code = _lib.fkski_grad(st.handle, ctypes.byref(k), ctypes.byref(o), ctypes.byref(L), g, ctypes.byref(inf),
                            _stream(stream))
-    if code not in (OK, E_NOT_CONVERGED):
+    if not (allow_not_converged and code == E_NOT_CONVERGED):
         _check(code, "fkski_grad")
-    return L.value, list(g), dict(iters=list(inf.iters_rhs[: 1 + st.info()["n_probes"]]), status=code)
+    return L.value, list(g), dict(iters=list(inf.iters_rhs[: 1 + st.info()["n_probes"]]), status=code,
+                                  rel_residual=inf.rel_residual)
 
 
 class LogMarginalLikelihood(torch.autograd.Function):
@@ -510,7 +517,9 @@ class LogMarginalLikelihood(torch.autograd.Function):
 
     forward runs fkski_loglik_forward (solves + SLQ); backward runs fkski_loglik_backward
     (derivative-Toeplitz MVMs and Hutchinson traces), reusing the forward's solutions when they
-    fit the iterate budget and recomputing them otherwise."""
+    fit the iterate budget and recomputing them otherwise.  A solve that stops at maxiter raises
+    FkskiError (E_NOT_CONVERGED) in forward or backward, so an unconverged L or gradient never
+    reaches the optimiser silently."""
 
     @staticmethod
     def forward(ctx, theta: torch.Tensor, st: Stats, ktype: int, rtol: float, maxiter: int, precision: int,

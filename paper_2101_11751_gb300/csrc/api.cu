@@ -16,8 +16,8 @@ void destroy_stats(fkski_stats *st) {
     cudaGetDevice(&cur);
     if (st->device != cur) cudaSetDevice(st->device);
     free_solve_work(st->work);
-    void *ptrs[] = {st->band_alt, st->wty_alt, st->wtz_alt, st->keys, st->perm, st->offsets, st->lowrank, st->pts,
-                    st->pkeys};
+    void *ptrs[] = {st->band_alt, st->wty_alt, st->wtz_alt, st->wty_df, st->wtz_df, st->keys, st->perm, st->offsets,
+                    st->lowrank, st->pts, st->pkeys};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     // pool blocks: once the device is idle (cudaFree above already waited for it when it ran),
@@ -41,9 +41,11 @@ void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_rel
 // like): freed blocks stay cached in the pool (release threshold: unlimited), so repeated calls
 // of the same size map no new memory.  fkski_trim_memory() hands the cache back.
 static std::mutex g_pool_mu;
-static cudaMemPool_t g_pool[64];
+static constexpr int kMaxDevices = 64;
+static cudaMemPool_t g_pool[kMaxDevices];
 
 static cudaError_t pool_for(int dev, cudaMemPool_t *out) {
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;  // beyond the pool table
     std::lock_guard<std::mutex> lock(g_pool_mu);
     if (!g_pool[dev]) {
         cudaMemPoolProps props;
@@ -150,7 +152,7 @@ long long fkski_kernel_launches(void) { return g_launches.load(std::memory_order
 
 int fkski_trim_memory(void) {
     std::lock_guard<std::mutex> lock(g_pool_mu);
-    for (int d = 0; d < 64; ++d)
+    for (int d = 0; d < kMaxDevices; ++d)
         if (g_pool[d] && cudaMemPoolTrimTo(g_pool[d], 0) != cudaSuccess) return note_cuda_error(cudaGetLastError(), __FILE__, __LINE__);
     return FKSKI_OK;
 }

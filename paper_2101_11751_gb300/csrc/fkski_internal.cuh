@@ -8,8 +8,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 
 #include "../../include/fkski.h"
+#include "dfloat.cuh"
 
 namespace fk {
 // Records the failing CUDA call (thread-local) for fkski_last_error_detail(); returns the status.
@@ -49,6 +51,21 @@ void count_launches(long long k);
 namespace fk {
 
 constexpr int kMaxProbes = 64;
+
+// Internal element-type code of double-float vectors (dfloat.cuh) next to FKSKI_F32 / FKSKI_F64;
+// never seen at the C ABI.
+constexpr int FK_DF = 2;
+template <typename T>
+constexpr int dtype_of() {
+    return sizeof(T) == 4 ? FKSKI_F32 : (std::is_same<T, dfl>::value ? FK_DF : FKSKI_F64);
+}
+// Element type of the band matrix a solve in vector type T reads: FP32 for double-float vectors.
+template <typename T>
+struct BandOf { using type = T; };
+template <>
+struct BandOf<dfl> { using type = float; };
+template <typename T>
+using BandT = typename BandOf<T>::type;
 constexpr int kMaxD = 3;
 
 inline int64_t ipow(int64_t b, int e) {
@@ -120,6 +137,9 @@ struct fkski_stats {
     void *band_alt;
     void *wty_alt;
     void *wtz_alt;
+    // W^T y and W^T z as double-float vectors (the MIXED solves), made on first use
+    void *wty_df;
+    void *wtz_df;
     // optional sort export
     uint32_t *keys;
     uint32_t *perm;

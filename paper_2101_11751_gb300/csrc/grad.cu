@@ -263,7 +263,7 @@ static int forward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_
                          cudaStream_t s) {
     const int R = 1 + st->nprobes;
     const int64_t m = st->m;
-    const int dt = sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64;
+    const int dt = dtype_of<T>();
     Slot<T> sl;
     FK_TRY(slot_get<T>(st, R, m, true, sl));
     std::vector<int> it(R, 0);
@@ -310,7 +310,7 @@ static int forward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_
 template <typename T>
 static int backward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, double *grad,
                           fkski_info *info, cudaStream_t s) {
-    const int dt = sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64;
+    const int dt = dtype_of<T>();
     if (!grad_sol_valid(st, kern, dt)) {
         double Ltmp;
         fkski_opts o2 = *o;
@@ -381,6 +381,8 @@ static int check_grad_args(fkski_stats *st, const fkski_kernel *kern, fkski_opts
     if (st->nprobes < 1) return FKSKI_E_INVALID_ARG;
     if (!(kern->noise_var > 0.0)) return FKSKI_E_INVALID_ARG;
     if (o->maxiter < 1 || o->maxiter > SLQ_MAXK) return FKSKI_E_INVALID_ARG;
+    if (o->precision != FKSKI_MIXED && o->precision != FKSKI_DOUBLE && o->precision != FKSKI_FP32)
+        return FKSKI_E_INVALID_ARG;
     return FKSKI_OK;
 }
 
@@ -390,8 +392,9 @@ int loglik_forward_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_o
     FK_TRY(check_grad_args(st, kern, &o, opts));
     if (!L) return FKSKI_E_INVALID_ARG;
     if (info) memset(info, 0, sizeof(*info));
-    return o.precision == FKSKI_DOUBLE ? forward_typed<double>(st, kern, &o, L, info, s)
-                                       : forward_typed<float>(st, kern, &o, L, info, s);
+    if (o.precision == FKSKI_DOUBLE) return forward_typed<double>(st, kern, &o, L, info, s);
+    if (o.precision == FKSKI_FP32) return forward_typed<float>(st, kern, &o, L, info, s);
+    return forward_typed<dfl>(st, kern, &o, L, info, s);
 }
 
 int loglik_backward_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, double *grad,
@@ -399,8 +402,9 @@ int loglik_backward_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_
     fkski_opts o;
     FK_TRY(check_grad_args(st, kern, &o, opts));
     if (!grad) return FKSKI_E_INVALID_ARG;
-    return o.precision == FKSKI_DOUBLE ? backward_typed<double>(st, kern, &o, grad, info, s)
-                                       : backward_typed<float>(st, kern, &o, grad, info, s);
+    if (o.precision == FKSKI_DOUBLE) return backward_typed<double>(st, kern, &o, grad, info, s);
+    if (o.precision == FKSKI_FP32) return backward_typed<float>(st, kern, &o, grad, info, s);
+    return backward_typed<dfl>(st, kern, &o, grad, info, s);
 }
 
 

@@ -30,6 +30,8 @@ template <>
 struct Cx<float> { using t = float2; };
 template <>
 struct Cx<double> { using t = double2; };
+template <>
+struct Cx<dfl> { using t = dfl2; };
 
 template <typename T>
 __device__ __forceinline__ void sincospi_t(T x, T *s, T *c);
@@ -51,6 +53,16 @@ __device__ __forceinline__ void make_twiddles(typename Cx<T>::t *tw, int L) {
         tw[k].y = -s;
     }
 }
+// Double-float twiddles: the FP64 values rounded once to double-float.
+template <>
+__device__ __forceinline__ void make_twiddles<dfl>(dfl2 *tw, int L) {
+    for (int k = threadIdx.x; k < L / 2; k += blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)k / (double)L, &s, &c);
+        tw[k].x = dfl(c);
+        tw[k].y = dfl(-s);
+    }
+}
 
 // Butterfly arithmetic with every rounding spelled out (no contraction left to the compiler), so
 // that the radix-2 and radix-4 stage groupings below give bit-identical results: the tuner's
@@ -63,6 +75,10 @@ __device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b
 __device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ dfl r_add(dfl a, dfl b) { return a + b; }
+__device__ __forceinline__ dfl r_sub(dfl a, dfl b) { return a - b; }
+__device__ __forceinline__ dfl r_mul(dfl a, dfl b) { return a * b; }
+__device__ __forceinline__ dfl r_fma(dfl a, dfl b, dfl c) { return a * b + c; }
 
 // DIF butterfly: (u, v) -> (u + v, (u - v) w)
 template <typename C>
@@ -780,7 +796,7 @@ void kgop_destroy(KgOp *op) {
     delete op;
 }
 
-static size_t esz(int dtype) { return dtype == FKSKI_F32 ? 4 : 8; }
+static size_t esz(int dtype) { return dtype == FKSKI_F32 ? 4 : 8; }  // FP64 and double-float: 8
 
 static int ensure(void **p, size_t &have, size_t want) {
     if (have >= want && *p) return FKSKI_OK;
@@ -894,6 +910,8 @@ int kgop_set(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s) {
             if (!op->tw_ok[a]) {
                 if (op->dtype == FKSKI_F32)
                     k_twiddles<float><<<1, FFT_T, 0, s>>>((float2 *)op->tw[a], op->L[a]);
+                else if (op->dtype == FK_DF)
+                    k_twiddles<dfl><<<1, FFT_T, 0, s>>>((dfl2 *)op->tw[a], op->L[a]);
                 else
                     k_twiddles<double><<<1, FFT_T, 0, s>>>((double2 *)op->tw[a], op->L[a]);
                 FK_LAUNCH();
@@ -906,6 +924,10 @@ int kgop_set(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s) {
                 FK_TRY(raise_smem_limit((const void *)k_spectrum_1d<float>, sm));
                 k_spectrum_1d<float><<<1, FFT_T, sm, s>>>((float *)op->lam[a], (int)op->g.M[a], op->L[a], op->g.h[a],
                                                           kern->lengthscale[a], deriv, scale);
+            } else if (op->dtype == FK_DF) {
+                FK_TRY(raise_smem_limit((const void *)k_spectrum_1d<dfl>, sm));
+                k_spectrum_1d<dfl><<<1, FFT_T, sm, s>>>((dfl *)op->lam[a], (int)op->g.M[a], op->L[a], op->g.h[a],
+                                                        kern->lengthscale[a], deriv, scale);
             } else {
                 FK_TRY(raise_smem_limit((const void *)k_spectrum_1d<double>, sm));
                 k_spectrum_1d<double><<<1, FFT_T, sm, s>>>((double *)op->lam[a], (int)op->g.M[a], op->L[a], op->g.h[a],
@@ -915,7 +937,9 @@ int kgop_set(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s) {
         }
         return FKSKI_OK;
     }
-    return op->dtype == FKSKI_F32 ? bttb_spectrum<float>(op, kern, param, s) : bttb_spectrum<double>(op, kern, param, s);
+    if (op->dtype == FKSKI_F32) return bttb_spectrum<float>(op, kern, param, s);
+    if (op->dtype == FK_DF) return bttb_spectrum<dfl>(op, kern, param, s);
+    return bttb_spectrum<double>(op, kern, param, s);
 }
 
 // ------------------------------------------------------------------ pass configuration and tuner
@@ -931,8 +955,12 @@ struct PassCfg {
 
 // Passes that run the register kernel (L = L1 * L2, L1 <= 16): FP32 up to L = 256; FP64 up to
 // L = 64 (its 16-value columns need twice the registers, and for L = 128, 256 the
-// shared-memory kernel is as fast or faster).  The rule depends on the shape only.
-static bool reg_fft_ok(int dtype, int L) { return L >= 8 && L <= (dtype == FKSKI_F32 ? 256 : 64); }
+// shared-memory kernel is as fast or faster); double-float up to DF_REG_LMAX.  The rule depends
+// on the shape only.
+constexpr int DF_REG_LMAX = 256;
+static bool reg_fft_ok(int dtype, int L) {
+    return L >= 8 && L <= (dtype == FKSKI_F32 ? 256 : (dtype == FK_DF ? DF_REG_LMAX : 64));
+}
 
 struct PassKey {
     int dtype, L, M;
@@ -1149,7 +1177,9 @@ int kgop_tune(KgOp *op, int nrhs, cudaStream_t s) {
     if (op->kind != FKSKI_RBF || nrhs < 1) return FKSKI_OK;
     for (int a = 0; a < op->d; ++a)
         if (!op->lam[a] || !op->tw[a]) return FKSKI_E_INVALID_ARG;  // spectra first (kgop_set)
-    return op->dtype == FKSKI_F32 ? kron_tune<float>(op, nrhs, s) : kron_tune<double>(op, nrhs, s);
+    if (op->dtype == FKSKI_F32) return kron_tune<float>(op, nrhs, s);
+    if (op->dtype == FK_DF) return kron_tune<dfl>(op, nrhs, s);
+    return kron_tune<double>(op, nrhs, s);
 }
 
 // One line per tuned pass shape: "dtype L M S lines -> radix cl threads ms".
@@ -1159,7 +1189,7 @@ size_t kg_tuning_table(char *buf, size_t len) {
     char line[200];
     for (const auto &kv : g_tune) {
         snprintf(line, sizeof(line), "%s L=%d M=%d S=%lld lines=%lld -> radix %d, %d lines/CTA, %d threads, %.4f ms\n",
-                 kv.first.dtype == FKSKI_F32 ? "f32" : "f64", kv.first.L, kv.first.M, (long long)kv.first.S,
+                 kv.first.dtype == FKSKI_F32 ? "f32" : (kv.first.dtype == FK_DF ? "df" : "f64"), kv.first.L, kv.first.M, (long long)kv.first.S,
                  (long long)kv.first.nlines, kv.second.radix, kv.second.cl, kv.second.threads, (double)kv.second.ms);
         out += line;
     }
@@ -1259,10 +1289,14 @@ static int kgop_apply_any(KgOp *op, const void *v, void *out, int nrhs, const vo
     if (op->kind == FKSKI_RBF) {
         if (op->dtype == FKSKI_F32)
             return kron_apply<float>(op, (const float *)v, (float *)out, nrhs, (const float *)addv, alpha_dev, alpha, s);
+        if (op->dtype == FK_DF)
+            return kron_apply<dfl>(op, (const dfl *)v, (dfl *)out, nrhs, (const dfl *)addv, alpha_dev, alpha, s);
         return kron_apply<double>(op, (const double *)v, (double *)out, nrhs, (const double *)addv, alpha_dev, alpha, s);
     }
     if (op->dtype == FKSKI_F32)
         return bttb_apply<float>(op, (const float *)v, (float *)out, nrhs, (const float *)addv, alpha_dev, alpha, s);
+    if (op->dtype == FK_DF)
+        return bttb_apply<dfl>(op, (const dfl *)v, (dfl *)out, nrhs, (const dfl *)addv, alpha_dev, alpha, s);
     return bttb_apply<double>(op, (const double *)v, (double *)out, nrhs, (const double *)addv, alpha_dev, alpha, s);
 }
 

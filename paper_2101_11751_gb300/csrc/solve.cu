@@ -133,6 +133,16 @@ __device__ __forceinline__ double warp_sum_partials(const double *part, int npar
 }
 
 // ------------------------------------------------------------------ band SpMV
+// acc + b x for a band value b and a vector entry x; for double-float vectors the FP32 band value
+// multiplies exactly (TwoProd) and the sum is a double-float addition.
+template <typename TB, typename TX>
+__device__ __forceinline__ TX band_fma(TB b, TX x, TX acc) { return fma((TX)b, x, acc); }
+template <>
+__device__ __forceinline__ dfl band_fma<float, dfl>(float b, dfl x, dfl acc) {
+    df_acc_fx(acc, b, x);
+    return acc;
+}
+
 // u[r][j] = sum_o band[o][j] * x[r][j + off(o)]  (entries whose neighbour is off-grid are zero,
 // so the neighbour index is only clamped to stay in memory).  Band in TB, vectors in TX.
 // Optional partial dots per rhs: q0 = u.x, q1 = x.g.  `gate` skips the launch's work when set.
@@ -151,12 +161,12 @@ __global__ void __launch_bounds__(CG_T) k_band_spmv(const TB *__restrict__ band,
 #pragma unroll
         for (int k = 0; k < RB; ++k) acc[k] = TX(0);
         for (int o = 0; o < nband; ++o) {
-            const TX b = (TX)band[(int64_t)o * m + j];
+            const TB b = band[(int64_t)o * m + j];
             int64_t nb = j + offs.off[o];
             nb = nb < 0 ? 0 : (nb >= m ? m - 1 : nb);
 #pragma unroll
             for (int k = 0; k < RB; ++k)
-                if (k < R) acc[k] = fma(b, x[(int64_t)k * m + nb], acc[k]);
+                if (k < R) acc[k] = band_fma<TB, TX>(b, x[(int64_t)k * m + nb], acc[k]);
         }
 #pragma unroll
         for (int k = 0; k < RB; ++k)
@@ -463,8 +473,21 @@ __device__ __forceinline__ Quad<double> ld_quad<double>(const double *p, bool st
     return Quad<double>{{a.x, a.y, b.x, b.y}};
 }
 
+template <>
+__device__ __forceinline__ Quad<dfl> ld_quad<dfl>(const dfl *p, bool stream) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    const float4 a = stream ? __ldcs(q) : __ldg(q);
+    const float4 b = stream ? __ldcs(q + 1) : __ldg(q + 1);
+    return Quad<dfl>{{dfl(a.x, a.y), dfl(a.z, a.w), dfl(b.x, b.y), dfl(b.z, b.w)}};
+}
+
 template <typename T>
 __device__ __forceinline__ void st_quad(T *p, const T v[4]);
+template <>
+__device__ __forceinline__ void st_quad<dfl>(dfl *p, const dfl v[4]) {
+    reinterpret_cast<float4 *>(p)[0] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
+}
 template <>
 __device__ __forceinline__ void st_quad<float>(float *p, const float v[4]) {
     *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
@@ -525,7 +548,7 @@ __global__ void __launch_bounds__(CG_T, RB <= 2 ? 2 : 1) k_band_spmv4g(const TB 
 #pragma unroll
                     for (int e = 0; e < 7; ++e)
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[k][q] = fma((TX)b[e].v[q], v[e + 1 + q], acc[k][q]);
+                        for (int q = 0; q < 4; ++q) acc[k][q] = band_fma<TB, TX>(b[e].v[q], v[e + 1 + q], acc[k][q]);
                 }
             }
         }
@@ -553,6 +576,139 @@ __global__ void __launch_bounds__(CG_T, RB <= 2 ? 2 : 1) k_band_spmv4g(const TB 
             const double s1 = block_sum<TX>(dq1[k], sh);
             if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ * Rtot + (r0 + k) * NQ + 1] = s1;
         }
+    }
+}
+
+// The half-band product for one double-float right-hand side (the MIXED iterations): the same
+// traversal as k_band_spmv4h (direct quads of the stored upper diagonals at i0, mirrored quads
+// around i0 - rowbase), with x and u as double-float values (a 12-wide window is six 16-byte
+// loads) and every band product accumulated exactly by band_fma.  The band stays FP32, so the
+// bytes read per launch are the FP32 half band plus 16 B per node for x and u.
+template <int NROW, int FIN>
+__global__ void __launch_bounds__(CG_T, 2) k_band_spmv4hd(const float *__restrict__ hb, const dfl *__restrict__ x,
+                                                           dfl *__restrict__ u, int64_t m, RowOffs rows,
+                                                           double *__restrict__ part, int NQ, const dfl *__restrict__ g,
+                                                           const int *__restrict__ gate, int nwork, CgFin fin) {
+    if (gate && *gate) return;
+    __shared__ double sh[CG_T / 32];
+    if ((int)blockIdx.x >= nwork) {
+        if (part && threadIdx.x == 0)
+            for (int q = 0; q < NQ && q < 2; ++q) part[(int64_t)blockIdx.x * NQ + q] = 0.0;
+        if (FIN && last_block(&fin.ctl->fin_cnt[0])) {
+            fin_gamma_dev<FIN == 2>(part, gridDim.x, fin.S, fin.state, fin.want, fin.iters, fin.hist, fin.ctl, fin.mode);
+            if (threadIdx.x == 0) fin.ctl->fin_cnt[0] = 0;
+        }
+        return;
+    }
+    constexpr int C = NROW / 2;  // centre row
+    dfl dq0 = dfl(0), dq1 = dfl(0);
+    const int64_t nquad = m >> 2;
+    auto ld4 = [&](const float *base, int64_t j) -> float4 {
+        if (j >= 0 && j + 4 <= m) {
+            float4 r;
+            asm volatile("ld.global.nc.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                         : "l"(base + j));
+            return r;
+        }
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto xwin = [&](int64_t w0, dfl v[12]) {  // x[w0 .. w0 + 11], zero off the ends
+        if (w0 >= 0 && w0 + 12 <= m) {
+            const float4 *q = reinterpret_cast<const float4 *>(x + w0);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const float4 f = __ldg(q + c);
+                v[2 * c] = dfl(f.x, f.y);
+                v[2 * c + 1] = dfl(f.z, f.w);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 12; ++j) v[j] = (w0 + j >= 0 && w0 + j < m) ? x[w0 + j] : dfl(0);
+        }
+    };
+    auto comp = [](const float4 &f, int q) { return q == 0 ? f.x : (q == 1 ? f.y : (q == 2 ? f.z : f.w)); };
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nquad; t += (int64_t)nwork * blockDim.x) {
+        const int64_t i0 = t << 2;
+        dfl acc[4] = {dfl(0), dfl(0), dfl(0), dfl(0)};
+        {
+            dfl v[12];
+            xwin(i0 - 4, v);
+            float4 hc[4], hp[4];
+#pragma unroll
+            for (int dx = 0; dx < 4; ++dx) {
+                hc[dx] = ld4(hb + (int64_t)dx * m, i0);
+                hp[dx] = dx ? ld4(hb + (int64_t)dx * m, i0 - 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int dx = 0; dx < 4; ++dx)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[q] = band_fma<float, dfl>(comp(hc[dx], q), v[q + dx + 4], acc[q]);
+                    if (dx > 0) {
+                        const int j = q - dx;
+                        const float h = j < 0 ? comp(hp[dx], j + 4) : comp(hc[dx], j);
+                        acc[q] = band_fma<float, dfl>(h, v[j + 4], acc[q]);
+                    }
+                }
+        }
+#pragma unroll 1
+        for (int u_ = 0; u_ < C; ++u_) {
+            const int row = C + 1 + u_;
+            const int64_t rb = rows.base[row];
+            const float *hrow = hb + (int64_t)(4 + u_ * 7) * m;
+            {
+                float4 dq[7];
+#pragma unroll
+                for (int e = 0; e < 7; ++e) dq[e] = ld4(hrow + (int64_t)e * m, i0);
+                dfl v[12];
+                xwin(i0 + rb - 4, v);
+#pragma unroll
+                for (int e = 0; e < 7; ++e)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] = band_fma<float, dfl>(comp(dq[e], q), v[q + e + 1], acc[q]);
+            }
+            dfl vm[12];
+            xwin(i0 - rb - 4, vm);
+            const int64_t j0 = i0 - rb;
+#pragma unroll
+            for (int e = 0; e < 7; ++e) {
+                const float *hd = hrow + (int64_t)e * m;
+                const float4 qa = e > 3 ? ld4(hd, j0 - 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 qb = ld4(hd, j0);
+                const float4 qc = e < 3 ? ld4(hd, j0 + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int tt = 3 - e + q;
+                    const float h = tt < 0 ? comp(qa, tt + 4) : (tt < 4 ? comp(qb, tt) : comp(qc, tt - 4));
+                    acc[q] = band_fma<float, dfl>(h, vm[tt + 4], acc[q]);
+                }
+            }
+        }
+        float4 *uq = reinterpret_cast<float4 *>(u + i0);
+        uq[0] = make_float4(acc[0].hi, acc[0].lo, acc[1].hi, acc[1].lo);
+        uq[1] = make_float4(acc[2].hi, acc[2].lo, acc[3].hi, acc[3].lo);
+        if (part) {
+            const Quad<dfl> xv = ld_quad<dfl>(x + i0, false);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dq0 = fma(acc[q], xv.v[q], dq0);
+            if (g) {
+                const Quad<dfl> gv = ld_quad<dfl>(g + i0, false);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dq1 = fma(xv.v[q], gv.v[q], dq1);
+            }
+        }
+    }
+    if (!part) return;
+    const double s0 = block_sum<dfl>(dq0, sh);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ + 0] = s0;
+    if (NQ > 1) {
+        const double s1 = block_sum<dfl>(dq1, sh);
+        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NQ + 1] = s1;
+    }
+    if (FIN && last_block(&fin.ctl->fin_cnt[0])) {
+        fin_gamma_dev<FIN == 2>(part, gridDim.x, fin.S, fin.state, fin.want, fin.iters, fin.hist, fin.ctl, fin.mode);
+        if (threadIdx.x == 0) fin.ctl->fin_cnt[0] = 0;
     }
 }
 
@@ -641,6 +797,20 @@ static int launch_spmv(const TB *band, const fkski_grid &g, const TX *x, TX *u, 
             return FKSKI_OK;
         }
     }
+    if constexpr (std::is_same<TB, float>::value && std::is_same<TX, dfl>::value) {
+        if (R == 1 && spmv4_ok(g, m, band, x, u, gv)) {
+            // one double-float rhs: the symmetric half band, as for FP32
+            const RowOffs ro = make_rows(g);
+            const int nrow = g.d == 3 ? 49 : (g.d == 2 ? 7 : 1);
+            const float *hb = band + (int64_t)((nrow / 2) * 7 + 3) * m;
+            const int nwork = std::min(nblocks, num_sms() * 2);
+            if (g.d == 3) k_band_spmv4hd<49, 0><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, nwork, CgFin{});
+            else if (g.d == 2) k_band_spmv4hd<7, 0><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, nwork, CgFin{});
+            else k_band_spmv4hd<1, 0><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, nwork, CgFin{});
+            FK_LAUNCH();
+            return FKSKI_OK;
+        }
+    }
     if constexpr (!(std::is_same<TB, float>::value && std::is_same<TX, float>::value)) {
         if (spmv4_ok(g, m, band, x, u, gv)) {
             const RowOffs ro = make_rows(g);
@@ -707,6 +877,23 @@ static int launch_spmvh_fin(const float *band, const fkski_grid &g, const float 
     else if (g.d == 2) k_band_spmv4h<7, F><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork, fin);
     else k_band_spmv4h<1, F><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, 1, 0, nwork, fin);
 
+    FK_LAUNCH();
+    return FKSKI_OK;
+}
+
+// The same for one double-float rhs (FP32 band).
+template <bool GEN>
+static int launch_spmvh_fin(const float *band, const fkski_grid &g, const dfl *x, dfl *u, int64_t m, double *part,
+                            int NQ, const dfl *gv, const int *gate, int nblocks, const CgFin &fin, cudaStream_t s) {
+    if (!spmv4_ok(g, m, band, x, u, gv)) return FKSKI_E_UNSUPPORTED;
+    const RowOffs ro = make_rows(g);
+    const int nrow = g.d == 3 ? 49 : (g.d == 2 ? 7 : 1);
+    const float *hb = band + (int64_t)((nrow / 2) * 7 + 3) * m;
+    const int nwork = std::min(nblocks, num_sms() * 2);
+    constexpr int F = GEN ? 2 : 1;
+    if (g.d == 3) k_band_spmv4hd<49, F><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, nwork, fin);
+    else if (g.d == 2) k_band_spmv4hd<7, F><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, nwork, fin);
+    else k_band_spmv4hd<1, F><<<nblocks, CG_T, 0, s>>>(hb, x, u, m, ro, part, NQ, gv, gate, nwork, fin);
     FK_LAUNCH();
     return FKSKI_OK;
 }
@@ -1069,7 +1256,7 @@ __global__ void k_cg_resid(int64_t m, int R, const double *__restrict__ w64, con
 
 // ------------------------------------------------------------------ workspace
 struct SolveWork {
-    KgOp *kg[2];
+    KgOp *kg[3];  // K_G operators by element type: FP32, FP64, double-float
     void *buf;
     size_t buf_bytes;
     double *S;
@@ -1094,7 +1281,7 @@ struct SolveWork {
 
 void free_solve_work(SolveWork *w) {
     if (!w) return;
-    for (int i = 0; i < 2; ++i) kgop_destroy(w->kg[i]);
+    for (int i = 0; i < 3; ++i) kgop_destroy(w->kg[i]);
     if (w->buf) cudaFree(w->buf);
     if (w->S) cudaFree(w->S);
     if (w->part) cudaFree(w->part);
@@ -1145,7 +1332,7 @@ static int work_get(fkski_stats *st, SolveWork **out) {
 }
 
 static int work_kg(fkski_stats *st, SolveWork *w, int dtype, KgOp **op) {
-    const int i = dtype == FKSKI_F32 ? 0 : 1;
+    const int i = dtype == FKSKI_F32 ? 0 : (dtype == FK_DF ? 2 : 1);
     if (!w->kg[i]) FK_TRY(kgop_create(&st->grid, dtype, &w->kg[i]));
     *op = w->kg[i];
     return FKSKI_OK;
@@ -1172,9 +1359,29 @@ static int work_hist(SolveWork *w, int R, int maxiter) {
     return FKSKI_OK;
 }
 
-// Converted copies of the statistics in the solve precision.
+// Converted copies of the statistics in the solve precision.  Double-float solves read the FP32
+// band (stored, or converted from FP64 statistics) and double-float copies of W^T y and W^T z.
 template <typename T>
-static int stats_as(fkski_stats *st, const T **band, const T **wty, const T **wtz, cudaStream_t s) {
+static int stats_as(fkski_stats *st, const BandT<T> **band, const T **wty, const T **wtz, cudaStream_t s) {
+    if constexpr (std::is_same<T, dfl>::value) {
+        const float *bf, *wf, *zf;
+        FK_TRY(stats_as<float>(st, &bf, &wf, &zf, s));
+        *band = bf;
+        if (!st->wty_df) {
+            FK_TRY(dev_alloc(&st->wty_df, sizeof(dfl) * st->m));
+            k_convert<dfl><<<256, 256, 0, s>>>(st->wty, st->dtype == FKSKI_F64, (dfl *)st->wty_df, st->m);
+            FK_LAUNCH();
+            if (st->nprobes > 0) {
+                FK_TRY(dev_alloc(&st->wtz_df, sizeof(dfl) * st->nprobes * st->m));
+                k_convert<dfl><<<1024, 256, 0, s>>>(st->wtz, st->dtype == FKSKI_F64, (dfl *)st->wtz_df,
+                                                    st->nprobes * st->m);
+                FK_LAUNCH();
+            }
+        }
+        *wty = (const dfl *)st->wty_df;
+        *wtz = (const dfl *)st->wtz_df;
+        return FKSKI_OK;
+    } else {
     const int want = sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64;
     const int64_t nb = ipow(7, st->d) * st->m;
     if (st->dtype == want) {
@@ -1201,10 +1408,12 @@ static int stats_as(fkski_stats *st, const T **band, const T **wty, const T **wt
     *wty = (const T *)st->wty_alt;
     *wtz = (const T *)st->wtz_alt;
     return FKSKI_OK;
+    }
 }
 
 int stats_band_as(fkski_stats *st, int dtype, const void **band, const void **wty, const void **wtz, cudaStream_t s) {
     if (dtype == FKSKI_F32) return stats_as<float>(st, (const float **)band, (const float **)wty, (const float **)wtz, s);
+    if (dtype == FK_DF) return stats_as<dfl>(st, (const float **)band, (const dfl **)wty, (const dfl **)wtz, s);
     return stats_as<double>(st, (const double **)band, (const double **)wty, (const double **)wtz, s);
 }
 
@@ -1355,13 +1564,15 @@ static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_op
     if (r0_in && (GEN || !rho0_in)) return FKSKI_E_INVALID_ARG;
     SolveWork *w;
     FK_TRY(work_get(st, &w));
-    const int dt = sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64;
+    const int dt = dtype_of<T>();
     KgOp *kg, *kg64;
     FK_TRY(work_kg(st, w, dt, &kg));
     FK_TRY(work_kg(st, w, FKSKI_F64, &kg64));
     FK_TRY(kgop_set(kg, kern, -1, s));
     if (kg64 != kg) FK_TRY(kgop_set(kg64, kern, -1, s));
-    const T *band, *wty, *wtz;
+    using TB = BandT<T>;
+    const TB *band;
+    const T *wty, *wtz;
     FK_TRY(stats_as<T>(st, &band, &wty, &wtz, s));
     const int64_t m = st->m;
     const size_t nT = (size_t)R * m;
@@ -1379,8 +1590,9 @@ static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_op
     hc.maxiter = o->maxiter;
     hc.R = R;
     hc.sig2 = s2;
-    // reliable updates: on for FP32 vectors unless the caller chose (1 on, 2 off)
-    hc.replace = o->reliable_updates == 1 ? 1 : (o->reliable_updates == 2 ? 0 : (sizeof(T) == 4 ? 1 : 0));
+    // reliable updates: on for FP32 vectors unless the caller chose (1 on, 2 off); FP64 and
+    // double-float recurrences track the true residual without them
+    hc.replace = o->reliable_updates == 1 ? 1 : (o->reliable_updates == 2 ? 0 : (std::is_same<T, float>::value ? 1 : 0));
     hc.delta2 = 0.01;
     FK_CUDA(cudaMemcpyAsync(w->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, s));
     std::vector<double> hS((size_t)NF * R, 0.0);
@@ -1428,7 +1640,7 @@ static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_op
         k_pick<<<1, 128, 0, s>>>(sums, 4, R, rr);
         FK_LAUNCH();
         for (int it = 0; it < BCG_STEPS; ++it) {
-            FK_TRY((launch_spmv<T, T>(band, st->grid, V.p, V.s, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
+            FK_TRY((launch_spmv<TB, T>(band, st->grid, V.p, V.s, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
             k_dots4<T, T><<<gb, CG_T, 0, s>>>(V.p, V.s, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R, w->part, nullptr);
             k_fin_sums<<<(unsigned)cdiv(R * 4 * 32, 256), 256, 0, s>>>(w->part, gb, R, 4, sums);
             k_bcg_xr<T><<<gv, 256, 0, s>>>(m, R, V.u, V.v, V.p, V.s, sums, rr, mask);
@@ -1441,7 +1653,7 @@ static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_op
         // r_hat_0 (FP64 and T); W^T W b_hat in FP64; g' and the scalars of b'
         k_r0_init<T><<<gv, 256, 0, s>>>(m, R, V.u, V.w64, s2, V.r0, V.r, mask);
         FK_LAUNCH();
-        FK_TRY((launch_spmv<T, double>(band, st->grid, V.r0, V.t64, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
+        FK_TRY((launch_spmv<TB, double>(band, st->grid, V.r0, V.t64, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
         k_gprime<T><<<gv, 256, 0, s>>>(m, R, V.g0, V.t64, V.g, mask);
         k_convert_t<T, double><<<gv, 256, 0, s>>>(V.g0, V.w64, (int64_t)nT, 1.0);
         k_dots4<double, double><<<gb, CG_T, 0, s>>>(V.r0, V.w64, V.r0, V.t64, nullptr, nullptr, nullptr, nullptr, m, R,
@@ -1472,7 +1684,7 @@ static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_op
     // u = W^T W r with its partials, then the gamma step (taken by the product's last block when
     // the half-band kernel applies, else by its own one-block launch)
     auto spmv_gamma = [&](const int *gate, int mode, cudaStream_t st_) -> int {
-        if constexpr (std::is_same<T, float>::value) {
+        if constexpr (std::is_same<T, float>::value || std::is_same<T, dfl>::value) {
             if (R == 1) {
                 const int rc0 = launch_spmvh_fin<GEN>(band, st->grid, V.r, V.u, m, w->part, NQ, GEN ? V.g : nullptr, gate,
                                                       (int)gb, CgFin{w->S, w->state, w->want, w->iters, hb, w->ctl, mode},
@@ -1480,7 +1692,7 @@ static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_op
                 if (rc0 != FKSKI_E_UNSUPPORTED) return rc0;
             }
         }
-        FK_TRY((launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, gate, gb, st_)));
+        FK_TRY((launch_spmv<TB, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, gate, gb, st_)));
         k_cg_fin_gamma<GEN><<<1, 256, 0, st_>>>(w->part, gb, w->S, w->state, w->want, w->iters, hb, w->ctl, mode);
         FK_LAUNCH();
         return FKSKI_OK;
@@ -1520,11 +1732,11 @@ static int fcg_prepare(fkski_stats *st, const fkski_kernel *kern, const fkski_op
         FK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
         kgop_set_gate(kg64, gate_conf);
         // true residual in FP64: w64 = K (W^T W x_hat) + sigma^2 x_hat; gamma from it
-        rc = launch_spmv<T, double>(band, st->grid, V.x, V.t64, m, R, nullptr, 1, nullptr, gate_conf, gb, cs);
+        rc = launch_spmv<TB, double>(band, st->grid, V.x, V.t64, m, R, nullptr, 1, nullptr, gate_conf, gb, cs);
         if (rc == FKSKI_OK) rc = kgop_apply_dev(kg64, V.t64, V.w64, R, V.x, sig2_dev, cs);
         if (rc == FKSKI_OK) {
             k_cg_resid<T, GEN><<<gv, CG_T, 0, cs>>>(m, R, V.w64, V.r0, V.kg, V.r, w->S, w->state, w->want, w->ctl);
-            rc = launch_spmv<T, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, gate_conf, gb, cs);
+            rc = launch_spmv<TB, T>(band, st->grid, V.r, V.u, m, R, w->part, NQ, GEN ? V.g : nullptr, gate_conf, gb, cs);
         }
         if (rc == FKSKI_OK)
             k_cg_fin_replace<GEN><<<1, 256, 0, cs>>>(w->part, gb, w->S, w->state, w->want, w->iters, ha, w->ctl);
@@ -1593,36 +1805,46 @@ __global__ void k_wtx64(const double *__restrict__ Bx, const T *__restrict__ g0,
 template <typename T>
 static int fcg_wtx64(fkski_stats *st, CgVecs<T> &V, int R, double *out64, cudaStream_t s) {
     SolveWork *w = st->work;
-    const T *band, *wty, *wtz;
+    const BandT<T> *band;
+    const T *wty, *wtz;
     FK_TRY(stats_as<T>(st, &band, &wty, &wtz, s));
     const int64_t m = st->m;
     const unsigned gb = (unsigned)grid_blocks(m);
     const unsigned gv = (unsigned)std::min<int64_t>(cdiv((int64_t)R * m, 256), 152 * 8);
-    FK_TRY((launch_spmv<T, double>(band, st->grid, V.x, V.t64, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
+    FK_TRY((launch_spmv<BandT<T>, double>(band, st->grid, V.x, V.t64, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
     k_wtx64<T><<<gv, 256, 0, s>>>(V.t64, V.g0, V.g, out64, m, R, w->S);
     FK_LAUNCH();
     return FKSKI_OK;
 }
 
-// a = W^T z (FP64 -> T) and v = K_G a (FP64 product -> T) of a finished single-rhs solve.
+// Element type of the mean outputs a, v: FP32 for the MIXED (double-float) solves.
 template <typename T>
-static int mean_outputs(fkski_stats *st, CgVecs<T> &V, T *a_out, T *v_out, cudaStream_t s) {
+struct OutOf { using type = T; };
+template <>
+struct OutOf<dfl> { using type = float; };
+template <typename T>
+using OutT = typename OutOf<T>::type;
+
+// a = W^T z (FP64 -> output type) and v = K_G a (FP64 product -> output type) of a finished
+// single-rhs solve.
+template <typename T>
+static int mean_outputs(fkski_stats *st, CgVecs<T> &V, OutT<T> *a_out, OutT<T> *v_out, cudaStream_t s) {
     SolveWork *w = st->work;
     const int64_t m = st->m;
     FK_TRY(fcg_wtx64<T>(st, V, 1, V.w64, s));
     KgOp *kg64 = w->kg[1];
     FK_TRY(kgop_apply(kg64, V.w64, V.r0, 1, nullptr, 0.0, s));
     const unsigned gv = (unsigned)std::min<int64_t>(cdiv(m, 256), 152 * 8);
-    k_convert_t<double, T><<<gv, 256, 0, s>>>(V.w64, a_out, m, 1.0);
+    k_convert_t<double, OutT<T>><<<gv, 256, 0, s>>>(V.w64, a_out, m, 1.0);
     FK_LAUNCH();
-    k_convert_t<double, T><<<gv, 256, 0, s>>>(V.r0, v_out, m, 1.0);
+    k_convert_t<double, OutT<T>><<<gv, 256, 0, s>>>(V.r0, v_out, m, 1.0);
     FK_LAUNCH();
     return FKSKI_OK;
 }
 
 template <typename T>
-static int solve_mean(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, bool gen, T *a_out, T *v_out,
-                      fkski_info *info, cudaStream_t s) {
+static int solve_mean(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, bool gen, OutT<T> *a_out,
+                      OutT<T> *v_out, fkski_info *info, cudaStream_t s) {
     CgVecs<T> V;
     int it = 0, status = 0;
     double res = 0.0;
@@ -1652,7 +1874,10 @@ int solve_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts
     const bool gen = o.x0_mode == FKSKI_X0_ZERO;
     if (o.precision == FKSKI_DOUBLE)
         return solve_mean<double>(st, kern, &o, gen, (double *)a_out, (double *)v_out, info, s);
-    return solve_mean<float>(st, kern, &o, gen, (float *)a_out, (float *)v_out, info, s);
+    if (o.precision == FKSKI_FP32)
+        return solve_mean<float>(st, kern, &o, gen, (float *)a_out, (float *)v_out, info, s);
+    if (o.precision != FKSKI_MIXED) return FKSKI_E_INVALID_ARG;
+    return solve_mean<dfl>(st, kern, &o, gen, (float *)a_out, (float *)v_out, info, s);
 }
 
 // ------------------------------------------------------------------ batch of independent problems
@@ -1774,7 +1999,7 @@ static int solve_batched_typed(int P, fkski_stats *const *sts, const fkski_kerne
         int it = 0, status = FKSKI_OK;
         double res = 0.0;
         rc = fcg_collect<T>(sts[p], 1, &it, &res, &status, s);
-        if (rc == FKSKI_OK) rc = mean_outputs<T>(sts[p], V[p], (T *)a_out[p], (T *)v_out[p], s);
+        if (rc == FKSKI_OK) rc = mean_outputs<T>(sts[p], V[p], (OutT<T> *)a_out[p], (OutT<T> *)v_out[p], s);
         if (info) {
             info[p].iters = it;
             info[p].iters_rhs[0] = it;
@@ -1806,7 +2031,9 @@ int solve_batched_impl(int P, fkski_stats *const *sts, const fkski_kernel *kerne
     }
     if (info) memset(info, 0, sizeof(fkski_info) * P);
     if (o.precision == FKSKI_DOUBLE) return solve_batched_typed<double>(P, sts, kernels, &o, a_out, v_out, info, s);
-    return solve_batched_typed<float>(P, sts, kernels, &o, a_out, v_out, info, s);
+    if (o.precision == FKSKI_FP32) return solve_batched_typed<float>(P, sts, kernels, &o, a_out, v_out, info, s);
+    if (o.precision != FKSKI_MIXED) return FKSKI_E_INVALID_ARG;
+    return solve_batched_typed<dfl>(P, sts, kernels, &o, a_out, v_out, info, s);
 }
 
 int band_mvm_impl(const fkski_stats *stc, const void *x, void *u, int nrhs, int dtype, cudaStream_t s) {
@@ -1870,6 +2097,7 @@ static int grad_solve_t(fkski_stats *st, const fkski_kernel *kern, const fkski_o
 int grad_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, int dtype, void *sol, double *a64,
                double *zx, int *iters, double *res, int *status, cudaStream_t s) {
     if (dtype == FKSKI_F32) return grad_solve_t<float>(st, kern, o, (float *)sol, a64, zx, iters, res, status, s);
+    if (dtype == FK_DF) return grad_solve_t<dfl>(st, kern, o, (dfl *)sol, a64, zx, iters, res, status, s);
     return grad_solve_t<double>(st, kern, o, (double *)sol, a64, zx, iters, res, status, s);
 }
 
@@ -2153,7 +2381,8 @@ static int posterior_cov_typed(fkski_stats *st, const fkski_kernel *kern, const 
     FK_TRY(work_get(st, &w));
     KgOp *kg64;
     FK_TRY(work_kg(st, w, FKSKI_F64, &kg64));
-    const T *band, *wty, *wtz;
+    const BandT<T> *band;
+    const T *wty, *wtz;
     FK_TRY(stats_as<T>(st, &band, &wty, &wtz, s));
     double *bh = nullptr, *tmp = nullptr, *sums = nullptr;
     int *dstatus = nullptr;
@@ -2179,7 +2408,7 @@ static int posterior_cov_typed(fkski_stats *st, const fkski_kernel *kern, const 
         FK_TRY(kgop_set(kg64, kern, -1, s));
         FK_TRY(kgop_apply(kg64, tmp, bh, R, nullptr, 0.0, s));
         // ||W b_hat_r||^2 = b_hat_r^T (W^T W) b_hat_r
-        FK_TRY((launch_spmv<T, double>(band, st->grid, bh, tmp, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
+        FK_TRY((launch_spmv<BandT<T>, double>(band, st->grid, bh, tmp, m, R, nullptr, 1, nullptr, nullptr, gb, s)));
         k_dots4<double, double><<<gb, CG_T, 0, s>>>(bh, tmp, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, m, R,
                                                     w->part, nullptr);
         k_fin_sums<<<(unsigned)cdiv(R * 4 * 32, 256), 256, 0, s>>>(w->part, gb, R, 4, sums);
@@ -2249,13 +2478,20 @@ int posterior_cov_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_op
     if (!(kern->noise_var > 0.0) || !std::isfinite(kern->noise_var)) return FKSKI_E_INVALID_ARG;
     if (o.maxiter < 1 || !(o.rtol >= 0.0)) return FKSKI_E_INVALID_ARG;
     if (info) memset(info, 0, sizeof(*info));
-    const bool dbl = o.precision == FKSKI_DOUBLE;
-    if (xdtype == FKSKI_F32)
-        return dbl ? posterior_cov_typed<double, float>(st, kern, &o, (const float *)Xs, ns, cov, info, s)
-                   : posterior_cov_typed<float, float>(st, kern, &o, (const float *)Xs, ns, cov, info, s);
-    if (xdtype == FKSKI_F64)
-        return dbl ? posterior_cov_typed<double, double>(st, kern, &o, (const double *)Xs, ns, cov, info, s)
-                   : posterior_cov_typed<float, double>(st, kern, &o, (const double *)Xs, ns, cov, info, s);
+    if (o.precision != FKSKI_MIXED && o.precision != FKSKI_DOUBLE && o.precision != FKSKI_FP32)
+        return FKSKI_E_INVALID_ARG;
+    if (xdtype == FKSKI_F32) {
+        const float *X = (const float *)Xs;
+        if (o.precision == FKSKI_DOUBLE) return posterior_cov_typed<double, float>(st, kern, &o, X, ns, cov, info, s);
+        if (o.precision == FKSKI_FP32) return posterior_cov_typed<float, float>(st, kern, &o, X, ns, cov, info, s);
+        return posterior_cov_typed<dfl, float>(st, kern, &o, X, ns, cov, info, s);
+    }
+    if (xdtype == FKSKI_F64) {
+        const double *X = (const double *)Xs;
+        if (o.precision == FKSKI_DOUBLE) return posterior_cov_typed<double, double>(st, kern, &o, X, ns, cov, info, s);
+        if (o.precision == FKSKI_FP32) return posterior_cov_typed<float, double>(st, kern, &o, X, ns, cov, info, s);
+        return posterior_cov_typed<dfl, double>(st, kern, &o, X, ns, cov, info, s);
+    }
     return FKSKI_E_INVALID_ARG;
 }
 

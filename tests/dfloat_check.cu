@@ -1,0 +1,41 @@
+// Host driver for tests/test_dfloat_host.py: reads operands (C99 hex floats), prints the
+// double-float results of csrc/dfloat.cuh (a host build of the inline functions the kernels use).
+//   c v                  dfl(v) from a double
+//   a|s|m ah al bh bl    (ah + al) + - * (bh + bl)
+//   f ah al b            (ah + al) * b, b an FP32 number
+//   x ah al b xh xl      (ah + al) + b * (xh + xl), the band-product accumulation
+#include <cstdio>
+#include "dfloat.cuh"
+
+using fk::dfl;
+
+int main() {
+    char op[8];
+    while (scanf("%7s", op) == 1) {
+        dfl r;
+        if (op[0] == 'c') {
+            double v;
+            if (scanf("%la", &v) != 1) return 1;
+            r = dfl(v);
+        } else if (op[0] == 'f') {
+            float ah, al, b;
+            if (scanf("%a %a %a", &ah, &al, &b) != 3) return 1;
+            r = fk::df_mul_f(dfl(ah, al), b);
+        } else if (op[0] == 'x') {
+            float ah, al, b, xh, xl;
+            if (scanf("%a %a %a %a %a", &ah, &al, &b, &xh, &xl) != 5) return 1;
+            r = dfl(ah, al);
+            fk::df_acc_fx(r, b, dfl(xh, xl));
+        } else {
+            float ah, al, bh, bl;
+            if (scanf("%a %a %a %a", &ah, &al, &bh, &bl) != 4) return 1;
+            const dfl a(ah, al), b(bh, bl);
+            if (op[0] == 'a') r = a + b;
+            else if (op[0] == 's') r = a - b;
+            else if (op[0] == 'm') r = a * b;
+            else return 2;
+        }
+        printf("%a %a\n", r.hi, r.lo);
+    }
+    return 0;
+}

@@ -47,6 +47,35 @@ def test_precompute_matches_oracle(fk, oracle_mod, d, M, n, dtype, clustered):
     np.testing.assert_allclose(ex["ztz"], [n] * 3)
 
 
+def test_skewed_cell_fp32(fk, oracle_mod):
+    """One cell holding 2e5 FP32 points (it spans many tiles and all warps of the per-cell
+    moment reduction, and its FP32 partial sums run over the most terms) next to sparse cells:
+    keys, permutation and offsets bit-exact, band and W^T y within 1e-6 of the FP64 oracle."""
+    from oracle import core
+    from paper_2101_11751_gb300 import synth
+    rng = np.random.default_rng(17)
+    grid = synth.grid_for_box([0.0] * 3, [1.0] * 3, (10, 9, 8))
+    # dense cell: cell indices (3, 2, 1) -> the box [lo + (c+1) h, lo + (c+2) h) per axis
+    c = np.array([3, 2, 1])
+    lo = np.array(grid.lo) + (c + 1) * np.array(grid.h)
+    dense = lo[:, None] + rng.uniform(0.02, 0.98, size=(3, 200000)) * np.array(grid.h)[:, None]
+    sparse = rng.uniform(0.0, 1.0, size=(3, 30000))
+    X = np.ascontiguousarray(np.concatenate([dense, sparse], axis=1)[:, rng.permutation(230000)].astype(np.float32))
+    y = (np.sin(3 * X[0]) + X[1] * X[2] + 0.1 * rng.normal(size=X.shape[1])).astype(np.float32)
+    st = fk.precompute(_tt(X), _tt(y), grid, keep_sort=True)
+    ex = fk.stats_export(st)
+    srt = fk.stats_export_sort(st)
+    ref = core.precompute(grid, X, y)
+    assert np.max(np.diff(ref["offsets"])) >= 199000
+    np.testing.assert_array_equal(srt["keys"], ref["keys"])
+    np.testing.assert_array_equal(srt["perm"], ref["perm"])
+    np.testing.assert_array_equal(srt["offsets"], ref["offsets"])
+    eb, ew = rel_fro(ex["band"], ref["band"]), rel_fro(ex["wty"], ref["wty"])
+    print(f"skewed cell: band rel {eb:.2e} max {max_rel(ex['band'], ref['band']):.2e}, W^T y rel {ew:.2e}")
+    assert eb <= 1e-6 and max_rel(ex["band"], ref["band"]) <= 1e-6
+    assert ew <= 1e-6 and max_rel(ex["wty"], ref["wty"]) <= 1e-6
+
+
 def test_sort_three_radix_passes(fk, oracle_mod):
     """More than 2^20 cells: three 7-bit digit passes; keys/permutation/offsets bit-exact."""
     from oracle import core

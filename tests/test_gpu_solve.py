@@ -2,7 +2,10 @@
 
 Bar: posterior mean (v = K_G W^T z on the grid, and mu at test points) within 1e-4 relative L2 of
 the oracle at equal CG tolerance and start; iteration counts close (App. C.2: they differ only
-through finite precision)."""
+through finite precision): FP64 within max(3, 5%) of the oracle, MIXED (double-float arithmetic)
+at most 1.25x the oracle's.  The FP32 mode keeps its Krylov vectors and products in FP32, whose
+rounding makes CG take more iterations on these systems (about 2.4x on the 2-D case); it is held
+to the same mean bar and to a lower bound on the count."""
 import numpy as np
 import pytest
 import torch
@@ -39,19 +42,33 @@ def test_mean_matches_nspace_cg(fk, oracle_mod, d, M, n, kern, rtol, prec, x0_mo
     assert rel_fro(v.double().cpu().numpy(), v_ref) <= 1e-4
     # a = W^T z: Alg. 3 on FP32 statistics mixes W^T y (FP32-accumulated) with y^T y in its scalar
     # terms, consistent to ~1e-7 relative, which bounds a's accuracy near 5e-4; Alg. 5 has no such term.
-    a_tol = 1e-3 if (x0_mode == 0 and prec == 0) else 1e-4
+    a_tol = 1e-3 if (x0_mode == 0 and dtype == np.float32) else 1e-4
     assert rel_fro(a.double().cpu().numpy(), a_ref) <= a_tol
     # iteration counts: FP64 runs are the paper's EFCG and track the n-space recurrence (App. C.2,
-    # Fig. 5).  MIXED runs keep the Krylov vectors in FP32, which loses CG's superlinear
-    # convergence on these ill-conditioned systems (more iterations, same accuracy).
+    # Fig. 5); MIXED runs the same recurrence in double-float arithmetic on FP32 band values.
     if prec == 1:
         assert abs(info["iters"] - it_ref) <= max(3, 0.05 * it_ref), (info["iters"], it_ref)
     else:
-        assert info["iters"] >= it_ref - max(3, 0.05 * it_ref)
+        assert it_ref - max(3, 0.05 * it_ref) <= info["iters"] <= 1.25 * it_ref + 3, (info["iters"], it_ref)
     Xs = np.random.default_rng(3).uniform(0, 1, size=(d, 1000)).astype(dtype)
     mu = fk.predict(st, v, _tt(Xs)).double().cpu().numpy()
     mu_ref = core.predict(grid, v_ref, Xs)
     assert rel_fro(mu, mu_ref) <= 1e-4
+
+
+@pytest.mark.parametrize("x0_mode", [0, 1])
+def test_fp32_mode_mean(fk, oracle_mod, x0_mode):
+    """The FP32 mode (FP32 Krylov vectors with FP64 residual replacement): same mean bar; its
+    iteration count is bounded below only (FP32 rounding delays CG's convergence)."""
+    from oracle import core
+    grid, X, y = problem(2, (48, 48), 30000, seed=13)
+    kern = synth.Kernel(synth.RBF, (0.1, 0.15), 1.0, 0.01)
+    st = fk.precompute(_tt(X), _tt(y), grid)
+    a, v, info = fk.solve(st, kern, rtol=1e-6, maxiter=6000, x0_mode=x0_mode, precision=fk.FP32)
+    _, v_ref, it_ref, _ = core.nspace_mean(grid, kern, X, y, rtol=1e-6, x0_mode=x0_mode)
+    assert v.dtype == torch.float32
+    assert rel_fro(v.double().cpu().numpy(), v_ref) <= 1e-4
+    assert info["iters"] >= it_ref - max(3, 0.05 * it_ref)
 
 
 def test_mean_against_tight_oracle(fk, oracle_mod):
