@@ -337,8 +337,16 @@ def cg(matvec, b: np.ndarray, x0: Optional[np.ndarray], eps: float, maxiter: int
 
 
 def ski_operator(grid, kernel, W: sp.csr_matrix):
-    """v -> (W K_G W^T + sigma^2 I) v, the SKI system of Def. 1."""
+    """v -> (W K_G W^T + sigma^2 I) v, the SKI system of Def. 1.  Where kg_matvec would apply
+    K_G as a dense matrix (non-separable kernel, m <= 4096) that matrix is formed once here
+    instead of on every product."""
     s2 = kernel.noise_var
+    if kernel.type != RBF and grid.m <= 4096:
+        K = kg_dense(grid, kernel)
+
+        def mv(v):
+            return W @ (K @ (W.T @ v)) + s2 * v
+        return mv
 
     def mv(v):
         return W @ kg_matvec(grid, kernel, W.T @ v) + s2 * v
