@@ -51,6 +51,9 @@ extern "C" {
 
 #define FKSKI_F32 0
 #define FKSKI_F64 1
+#define FKSKI_F32X2 2 /* double-float vectors, the MIXED solver's format: each value is a pair of
+                         FP32 numbers (hi, lo), 8 bytes, value = hi + lo with |lo| <= ulp(hi)/2
+                         (fkski_band_mvm only)                                               */
 
 #define FKSKI_RBF 0      /* s * exp(-1/2 sum_k (r_k / l_k)^2), separable: K_G = s T_1 (x) ... (x) T_d */
 #define FKSKI_MATERN52 1 /* s (1 + sqrt5 r + 5/3 r^2) exp(-sqrt5 r), r = ||r / l||: multilevel Toeplitz */
@@ -226,7 +229,8 @@ FKSKI_API int fkski_kg_mvm_noalloc(const fkski_grid *grid, const fkski_kernel *k
                                    void *out, int nrhs, int dtype, void *stream);
 
 /* u = (W^T W) x for nrhs grid vectors (device, rhs-major, dtype) from the stored band
- * (Claim 2: O(m 7^d)). */
+ * (Claim 2: O(m 7^d)).  dtype FKSKI_F32, FKSKI_F64, or FKSKI_F32X2 (the FP32 band applied to
+ * double-float vectors, as in the MIXED iterations). */
 FKSKI_API int fkski_band_mvm(const fkski_stats *st, const void *x, void *u, int nrhs, int dtype, void *stream);
 
 /* ------------------------------------------------------------------ posterior mean (Sec. 4, App. B)
@@ -269,10 +273,13 @@ FKSKI_API int fkski_logdet_lanczos(fkski_stats *st, const fkski_kernel *kern, in
 /* Plain SKI posterior mean (Def. 1) by n-space CG (Alg. 1) on W K_G W^T + sigma^2 I from x0 = 0:
  * the O(n + m log m)-per-iteration method the paper's factorized solvers replace (Sec. 5,
  * Fig. 2, Table 1), for comparison.  Needs the points kept by the precompute (opts.keep_points);
- * otherwise UNSUPPORTED.  Vectors are in the points' precision (FP32 with FP64 cross-block
- * inner products, or FP64).  Stops when ||r_k|| <= rtol ||y||; opts->maxiter, check_every as
- * for fkski_solve.  Outputs as fkski_solve: a_out = W^T z, v_out = K_G W^T z (device, m, in the
- * points' dtype).  Returns OK, NOT_CONVERGED, BREAKDOWN, INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+ * otherwise UNSUPPORTED.  n-space vectors per opts->precision for FP32 points (MIXED
+ * double-float, FP32, or DOUBLE), FP64 for FP64 points; FP64 cross-block inner products.  W's
+ * entries are the per-point weight products rounded once in the points' precision, and W^T is
+ * their exact transpose.  Stops when ||r_k|| <= rtol ||y||; opts->maxiter, check_every as for
+ * fkski_solve.  Outputs as fkski_solve: a_out = W^T z, v_out = K_G W^T z (device, m; FP64 for
+ * FP64 points or DOUBLE, else FP32).  Returns OK, NOT_CONVERGED, BREAKDOWN, INVALID_ARG,
+ * UNSUPPORTED, OOM, CUDA. */
 FKSKI_API int fkski_ski_solve(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *opts, void *a_out,
                               void *v_out, fkski_info *info, void *stream);
 

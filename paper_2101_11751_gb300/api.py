@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libfkski.so")
 OK = 0
 E_INVALID_ARG, E_OUT_OF_GRID, E_NONFINITE, E_NOT_CONVERGED = -1, -2, -3, -4
 E_BREAKDOWN, E_TIMEOUT, E_OOM, E_CUDA, E_UNSUPPORTED, E_IO = -5, -6, -7, -8, -9, -10
-F32, F64 = 0, 1
+F32, F64, F32X2 = 0, 1, 2
 RBF, MATERN52 = 0, 1
 X0_ZERO, X0_Y_OVER_S2 = 0, 1
 MIXED, DOUBLE, FP32 = 0, 1, 2
@@ -307,12 +307,20 @@ def tuning_table() -> str:
     return buf.value.decode()
 
 
-def band_mvm(st: Stats, X: torch.Tensor, stream=None) -> torch.Tensor:
+def band_mvm(st: Stats, X: torch.Tensor, stream=None, double_float: bool = False) -> torch.Tensor:
+    """fkski_band_mvm: (W^T W) X for X of shape (R, m) or (m,).  With double_float, X is an FP32
+    tensor of shape (..., m, 2) holding (hi, lo) pairs (FKSKI_F32X2, the MIXED solver's vectors)."""
     load()
     out = torch.empty_like(X)
-    R = 1 if X.dim() == 1 else X.shape[0]
-    _check(_lib.fkski_band_mvm(st.handle, _ptr(X), _ptr(out), R, _dtype_code(X), _stream(stream)),
-           "fkski_band_mvm")
+    if double_float:
+        if X.dtype != torch.float32 or X.shape[-1] != 2:
+            raise ValueError("double-float vectors are float32 tensors of shape (..., m, 2)")
+        R = 1 if X.dim() == 2 else X.shape[0]
+        code = F32X2
+    else:
+        R = 1 if X.dim() == 1 else X.shape[0]
+        code = _dtype_code(X)
+    _check(_lib.fkski_band_mvm(st.handle, _ptr(X), _ptr(out), R, code, _stream(stream)), "fkski_band_mvm")
     return out
 
 
@@ -358,14 +366,15 @@ def logdet_lanczos(st: Stats, kernel, k: int, stream=None):
 
 
 def ski_solve(st: Stats, kernel, rtol: float = 1e-6, maxiter: int = 1000, check_every: int = 16, stream=None,
-              allow_not_converged: bool = False):
-    """fkski_ski_solve: plain SKI n-space CG (Alg. 1); needs precompute(..., keep_points=True)."""
+              allow_not_converged: bool = False, precision: int = MIXED):
+    """fkski_ski_solve: plain SKI n-space CG (Alg. 1); needs precompute(..., keep_points=True).
+    Outputs are FP64 for FP64 points or precision DOUBLE, else FP32."""
     load()
     inf_ = st.info()
-    dt = torch.float32 if inf_["dtype"] == F32 else torch.float64
+    dt = torch.float64 if (inf_["dtype"] == F64 or precision == DOUBLE) else torch.float32
     a = torch.empty(inf_["m"], dtype=dt, device="cuda")
     v = torch.empty(inf_["m"], dtype=dt, device="cuda")
-    o = opts(rtol=rtol, maxiter=maxiter, check_every=check_every)
+    o = opts(rtol=rtol, maxiter=maxiter, check_every=check_every, precision=precision)
     inf = CInfo()
     k = c_kernel(kernel)
     code = _lib.fkski_ski_solve(st.handle, ctypes.byref(k), ctypes.byref(o), _ptr(a), _ptr(v), ctypes.byref(inf),

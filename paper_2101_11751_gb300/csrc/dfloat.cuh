@@ -122,6 +122,30 @@ __host__ __device__ __forceinline__ void df_acc_fx(dfl &acc, const float b, cons
     acc = df_renorm(s, t);
 }
 
+// Long sums of FP32-times-double-float products (the band product: 343 terms per node).  The
+// accumulator keeps the running FP32 sum s of the products' high parts and, apart, the FP32 sum c
+// of everything TwoSum and TwoProd left over; it is normalised once, at the end.  Each term costs
+// 11 operations, and the dependence from one term to the next is a single addition on s and one
+// on c, so the per-node chains do not serialise the whole sum.  The leftovers are 2^-24 smaller
+// than the terms, so their FP32 rounding contributes about 2^-48 per term relative to the sum of
+// the terms' magnitudes.
+struct dacc {
+    float s, c;
+};
+
+__host__ __device__ __forceinline__ void dacc_zero(dacc &a) { a.s = 0.f; a.c = 0.f; }
+
+__host__ __device__ __forceinline__ void dacc_add_fx(dacc &a, const float b, const dfl x) {
+    const float p = df_mul_rn(b, x.hi);
+    float e = df_fma_rn(b, x.hi, -p);
+    e = df_fma_rn(b, x.lo, e);
+    float t;
+    a.s = two_sum(a.s, p, t);
+    a.c = df_add_rn(a.c, df_add_rn(t, e));
+}
+
+__host__ __device__ __forceinline__ dfl dacc_value(const dacc a) { return df_renorm(a.s, a.c); }
+
 __host__ __device__ __forceinline__ bool df_isfinite(const dfl a) { return isfinite(a.hi) && isfinite(a.lo); }
 
 }  // namespace fk

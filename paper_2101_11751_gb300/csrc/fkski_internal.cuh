@@ -52,9 +52,8 @@ namespace fk {
 
 constexpr int kMaxProbes = 64;
 
-// Internal element-type code of double-float vectors (dfloat.cuh) next to FKSKI_F32 / FKSKI_F64;
-// never seen at the C ABI.
-constexpr int FK_DF = 2;
+// Element-type code of double-float vectors (dfloat.cuh) next to FKSKI_F32 / FKSKI_F64.
+constexpr int FK_DF = FKSKI_F32X2;
 template <typename T>
 constexpr int dtype_of() {
     return sizeof(T) == 4 ? FKSKI_F32 : (std::is_same<T, dfl>::value ? FK_DF : FKSKI_F64);
@@ -66,6 +65,13 @@ template <>
 struct BandOf<dfl> { using type = float; };
 template <typename T>
 using BandT = typename BandOf<T>::type;
+// Element type of a solve's output vectors (posterior mean on the grid): FP32 for double-float.
+template <typename T>
+struct OutOf { using type = T; };
+template <>
+struct OutOf<dfl> { using type = float; };
+template <typename T>
+using OutT = typename OutOf<T>::type;
 constexpr int kMaxD = 3;
 
 inline int64_t ipow(int64_t b, int e) {

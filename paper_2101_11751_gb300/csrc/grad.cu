@@ -18,6 +18,7 @@
 #include "fkski_internal.cuh"
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 namespace fk {
@@ -41,35 +42,38 @@ constexpr int GF_RHO0 = 7;  // must match solve.cu's field enum
 int spmv_for_grad(fkski_stats *st, const void *x, void *u, int R, int dtype, cudaStream_t s);
 
 // ------------------------------------------------------------------ SLQ
-// One block per probe; thread 0 runs the implicit QL iteration on the k x k tridiagonal (FP64)
-// while carrying the first row of the eigenvector matrix.  Output est[p] = rho0 sum_l z_l^2 log lam_l.
-constexpr int SLQ_MAXK = 4096;
+// Per probe, the implicit QL iteration on the k x k Lanczos tridiagonal (FP64) carrying the first
+// row of the eigenvector matrix; est[p] = rho0 sum_l z_l^2 log lam_l.  It runs on the host cores,
+// one thread per probe: the sweep is a sequential chain of FP64 divides and square roots, O(k^2)
+// for k CG steps (about 1.5e8 rotations at k = 12,000), which a single GPU thread on GB300's FP64
+// pipe runs tens of times slower than one host core.  Only the CG coefficients (k per probe) move.
+constexpr int SLQ_MAXK = 65536;
 
 // e_1^T log(T) e_1 for the symmetric tridiagonal T (diagonal dg[0..k), couplings of[i] between
 // i and i+1, z = e_1 on entry): implicit-shift QL on (dg, of), rotating the first row z of the
 // eigenvector matrix along; Ritz values are clamped at sig2 (the spectrum of A starts there).
 // dg, of and z are overwritten.  Returns the quadrature; *fail when QL did not converge or a
 // Ritz value is not finite.
-__device__ double tridiag_e1_log(double *dg, double *of, double *z, int k, double sig2, int *fail_out) {
+static double tridiag_e1_log(double *dg, double *of, double *z, int k, double sig2, int *fail_out) {
     const double eps = 2.220446049250313e-16;
     int fail = 0;
     for (int l = 0; l < k; ++l) {
         for (int guard = 0; guard < 60; ++guard) {
             // smallest m >= l with a negligible coupling below it
             int mm = l;
-            while (mm < k - 1 && fabs(of[mm]) > eps * (fabs(dg[mm]) + fabs(dg[mm + 1]))) ++mm;
+            while (mm < k - 1 && std::fabs(of[mm]) > eps * (std::fabs(dg[mm]) + std::fabs(dg[mm + 1]))) ++mm;
             if (mm == l) break;
             if (guard == 59) { fail = 1; break; }
             // Wilkinson-type shift from the leading 2x2 block at l
             double gq = (dg[l + 1] - dg[l]) / (2.0 * of[l]);
-            double rr = hypot(gq, 1.0);
+            double rr = std::hypot(gq, 1.0);
             gq = dg[mm] - dg[l] + of[l] / (gq + (gq >= 0.0 ? rr : -rr));
             double sn = 1.0, cs = 1.0, pp = 0.0;
             int i = mm - 1;
             bool early = false;
             for (; i >= l; --i) {
                 const double f = sn * of[i], b = cs * of[i];
-                rr = hypot(f, gq);
+                rr = std::hypot(f, gq);
                 of[i + 1] = rr;
                 if (rr == 0.0) {
                     dg[i + 1] -= pp;
@@ -96,54 +100,30 @@ __device__ double tridiag_e1_log(double *dg, double *of, double *z, int k, doubl
     }
     double acc = 0.0;
     for (int i = 0; i < k; ++i) {
-        if (!isfinite(dg[i])) fail = 1;
-        else acc += z[i] * z[i] * log(fmax(dg[i], sig2));
+        if (!std::isfinite(dg[i])) fail = 1;
+        else acc += z[i] * z[i] * std::log(std::fmax(dg[i], sig2));
     }
     *fail_out = fail;
     return acc;
 }
 
+// The Lanczos tridiagonal of probe r from its CG coefficients (T[0,0] = 1/a_0,
+// T[i,i] = 1/a_i + b_{i-1}/a_{i-1}, T[i,i+1] = sqrt(b_i)/a_i), then its quadrature.
 // A = W K W^T + sigma^2 I has spectrum in [sigma^2, inf), so a Ritz value below sigma^2 (left by
-// rounding in the FP32 Krylov recurrences) is clamped to sigma^2.
-__global__ void k_slq(const double *__restrict__ ha, const double *__restrict__ hb, const int *__restrict__ iters,
-                      const double *__restrict__ S, int R, double sig2, double *__restrict__ est,
-                      int *__restrict__ status) {
-    extern __shared__ double sm[];
-    const int r = 1 + blockIdx.x;  // probe rhs
-    const int k = iters[r];
-    double *dg = sm;           // diagonal
-    double *of = sm + k + 1;   // off-diagonal (of[i] couples i, i+1)
-    double *z = of + k + 1;    // first eigenvector row
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+// rounding in the Krylov recurrences) is clamped to sigma^2.
+static double slq_probe(const double *ha, const double *hb, int R, int r, int k, double sig2, int *fail) {
+    *fail = 0;
+    if (k == 0) return 0.0;
+    std::vector<double> dg(k), of(k), z(k);
+    for (int i = 0; i < k; ++i) {
         const double a = ha[(int64_t)i * R + r];
         double di = 1.0 / a;
         if (i > 0) di += hb[(int64_t)(i - 1) * R + r] / ha[(int64_t)(i - 1) * R + r];
         dg[i] = di;
-        of[i] = (i + 1 < k) ? sqrt(hb[(int64_t)i * R + r]) / a : 0.0;
+        of[i] = (i + 1 < k) ? std::sqrt(hb[(int64_t)i * R + r]) / a : 0.0;
         z[i] = (i == 0) ? 1.0 : 0.0;
     }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    const double rho0 = S[GF_RHO0 * R + r];
-    if (k == 0) {
-        est[blockIdx.x] = 0.0;
-        return;
-    }
-    int fail = 0;
-    const double acc = tridiag_e1_log(dg, of, z, k, sig2, &fail);
-    if (fail) atomicOr(status, ST_BREAKDOWN);
-    est[blockIdx.x] = rho0 * acc;
-}
-
-// One tridiagonal's quadrature (single thread: the QL sweep is sequential).
-__global__ void k_tridiag_quad(double *dg, double *of, double *z, int k, double sig2, double scale,
-                               double *__restrict__ out, int *__restrict__ status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int i = 0; i < k; ++i) z[i] = i == 0 ? 1.0 : 0.0;
-    int fail = 0;
-    const double acc = tridiag_e1_log(dg, of, z, k, sig2, &fail);
-    if (fail) atomicOr(status, ST_BREAKDOWN);
-    *out = scale * acc;
+    return tridiag_e1_log(dg.data(), of.data(), z.data(), k, sig2, fail);
 }
 
 // dots of row pairs: out[r] = sum_i a[r][i] b[r][i]; per-block FP64 partials then a fixed-order sum
@@ -273,22 +253,32 @@ static int forward_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_
     GradView gv;
     FK_TRY(grad_view(st, dt, &gv));
     double *est = sl.part;  // R doubles of scratch
-    int *dstat;
-    FK_TRY(pool_alloc((void **)&dstat, sizeof(int), s));
-    FK_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int), s));
     int kmax = 0;
     for (int r = 1; r < R; ++r) kmax = std::max(kmax, it[r]);
     if (kmax > SLQ_MAXK) return FKSKI_E_UNSUPPORTED;
-    const size_t slq_sm = sizeof(double) * 3 * (size_t)(kmax + 1);
-    if (slq_sm > 48 * 1024) FK_TRY(raise_smem_limit((const void *)k_slq, slq_sm));
-    k_slq<<<R - 1, 128, slq_sm, s>>>(gv.hist_a, gv.hist_b, gv.iters, gv.S, R, kern->noise_var, est, dstat);
-    FK_LAUNCH();
+    // CG coefficients and rho0 to the host; one thread per probe
+    std::vector<double> ha((size_t)std::max(kmax, 1) * R), hb((size_t)std::max(kmax, 1) * R), hS((size_t)R);
+    FK_CUDA(cudaMemcpyAsync(ha.data(), gv.hist_a, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, s));
+    FK_CUDA(cudaMemcpyAsync(hb.data(), gv.hist_b, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s));
+    FK_CUDA(cudaMemcpyAsync(hS.data(), gv.S + (size_t)GF_RHO0 * R, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+    FK_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> hest((size_t)R, 0.0);
+    std::vector<int> hfail((size_t)R, 0);
+    {
+        std::vector<std::thread> pool;
+        for (int r = 1; r < R; ++r)
+            pool.emplace_back([&, r]() {
+                hest[r - 1] = hS[r] * slq_probe(ha.data(), hb.data(), R, r, it[r], kern->noise_var, &hfail[r]);
+            });
+        for (auto &t : pool) t.join();
+    }
+    int hst = 0;
+    for (int r = 1; r < R; ++r)
+        if (hfail[r]) hst |= ST_BREAKDOWN;
+    FK_CUDA(cudaMemcpyAsync(est, hest.data(), sizeof(double) * (R - 1), cudaMemcpyHostToDevice, s));
     k_loglik_assemble<<<1, 32, 0, s>>>(gv.S, sl.zx, est, R, (double)st->n, sl.fs);
     FK_LAUNCH();
-    int hst = 0;
     FK_CUDA(cudaMemcpyAsync(L, sl.fs, sizeof(double), cudaMemcpyDeviceToHost, s));
-    FK_CUDA(cudaMemcpyAsync(&hst, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FK_CUDA(cudaFreeAsync(dstat, s));
     FK_CUDA(cudaStreamSynchronize(s));
     if (info) {
         info->iters = 0;
@@ -417,35 +407,21 @@ int logdet_lanczos_impl(fkski_stats *st, const fkski_kernel *kern, int k, double
     if (st->nprobes < 1) return FKSKI_E_INVALID_ARG;
     if (!(kern->noise_var > 0.0)) return FKSKI_E_INVALID_ARG;
     if (info) memset(info, 0, sizeof(*info));
-    double *dbuf = nullptr;
-    int *dstat = nullptr;
-    FK_TRY(pool_alloc((void **)&dbuf, sizeof(double) * (3 * (size_t)(k + 1) + 1), s));
-    FK_TRY(pool_alloc((void **)&dstat, sizeof(int), s));
-    FK_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int), s));
     double sum = 0.0;
-    int rc = FKSKI_OK;
-    for (int p = 0; p < st->nprobes && rc == FKSKI_OK; ++p) {
+    int hst = 0;
+    for (int p = 0; p < st->nprobes; ++p) {
         std::vector<double> dg, of;
-        rc = efla_probe_tridiag(st, kern, k, p, dg, of, info, s);
-        if (rc != FKSKI_OK) break;
+        FK_TRY(efla_probe_tridiag(st, kern, k, p, dg, of, info, s));
         const int kk = (int)dg.size();
-        double *ddg = dbuf, *dof = dbuf + (k + 1), *dz = dof + (k + 1), *dout = dz + (k + 1);
-        FK_CUDA(cudaMemcpyAsync(ddg, dg.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, s));
-        FK_CUDA(cudaMemcpyAsync(dof, of.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, s));
-        k_tridiag_quad<<<1, 32, 0, s>>>(ddg, dof, dz, kk, kern->noise_var, st->ztz[p], dout, dstat);
-        FK_LAUNCH();
-        double t = 0.0;
-        FK_CUDA(cudaMemcpyAsync(&t, dout, sizeof(double), cudaMemcpyDeviceToHost, s));
-        FK_CUDA(cudaStreamSynchronize(s));
+        std::vector<double> z((size_t)std::max(kk, 1), 0.0);
+        z[0] = 1.0;
+        int fail = 0;
+        const double t = kk > 0 ? st->ztz[p] * tridiag_e1_log(dg.data(), of.data(), z.data(), kk, kern->noise_var, &fail)
+                                : 0.0;
+        if (fail) hst |= ST_BREAKDOWN;
         if (terms) terms[p] = t;
         sum += t;
     }
-    int hst = 0;
-    if (rc == FKSKI_OK) FK_CUDA(cudaMemcpyAsync(&hst, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
-    cudaFreeAsync(dbuf, s);
-    cudaFreeAsync(dstat, s);
-    FK_CUDA(cudaStreamSynchronize(s));
-    if (rc != FKSKI_OK) return rc;
     *logdet = sum / st->nprobes;
     if (hst & ST_BREAKDOWN) return FKSKI_E_BREAKDOWN;
     return FKSKI_OK;

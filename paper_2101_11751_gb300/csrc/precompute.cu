@@ -358,10 +358,17 @@ __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint32_t *__restrict_
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
     const int lane = threadIdx.x & 31;
+    uint32_t kv[RS_ITEMS];  // all loads first, so their latencies overlap
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const int64_t i = base + (int64_t)k * RS_T + threadIdx.x;
+        kv[k] = i < n ? __ldcs(keys + i) : 0u;
+    }
+#pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int64_t i = base + (int64_t)k * RS_T + threadIdx.x;
         const bool valid = i < n;
-        const uint32_t dg = valid ? (keys[i] >> shift) & mask : 0u;
+        const uint32_t dg = valid ? (kv[k] >> shift) & mask : 0u;
         const unsigned peers = digit_peers(dg, bits, __ballot_sync(0xFFFFFFFFu, valid));
         if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[dg], (uint32_t)__popc(peers));
     }
@@ -390,14 +397,19 @@ __global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(const uint32_t *__res
     for (int i = threadIdx.x; i < 8 * nb; i += RS_T) wcnt[i] = 0;
     __syncthreads();
     // rank of each key among the earlier keys of this warp with the same digit
-    // (ranks < 1024: two 16-bit ranks per register)
+    // (ranks < 1024: two 16-bit ranks per register).  The warp's 32 coalesced key loads are all
+    // issued before the ranking starts, so their latencies overlap.
     uint32_t kr[RS_ITEMS], rk[RS_ITEMS / 2];
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int s = 0; s < RS_ITEMS; ++s) {
         const int pos = w * (RS_ITEMS * 32) + s * 32 + lane;
+        kr[s] = pos < tile_n ? __ldcs(kin + base + pos) : 0u;
+    }
+#pragma unroll
+    for (int s = 0; s < RS_ITEMS; ++s) {
+        const int pos = w * (RS_ITEMS * 32) + s * 32 + lane;
         const bool valid = pos < tile_n;
-        kr[s] = valid ? kin[base + pos] : 0u;
         const uint32_t dg = (kr[s] >> shift) & mask;
         const unsigned peers = digit_peers(dg, bits, __ballot_sync(0xFFFFFFFFu, valid));
         const uint32_t before = valid ? wcnt[w * nb + dg] : 0u;

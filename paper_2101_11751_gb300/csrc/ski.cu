@@ -6,9 +6,15 @@
 //
 // n-space vectors are kept in cell order (the order of the points kept by the precompute with
 // opts.keep_points), so every pass streams the points and each cell's reduction reads a
-// contiguous segment; the permutation is never applied per iteration.  Inner products: FP32 (or
-// FP64) within a warp, FP64 across warps and blocks in a fixed order.  Scalars live on the
+// contiguous segment; the permutation is never applied per iteration.  Inner products: in the
+// vector type within a warp, FP64 across warps and blocks in a fixed order.  Scalars live on the
 // device; iterations run as captured CUDA-graph chunks like the factorized solver.
+//
+// Precision follows the factorized solver's modes: vectors of type T (FP32, FP64, or double-float
+// for MIXED) over points stored in TP.  W's entry for point i and stencil node a is the product
+// w_{a_1}(t_i1) ... w_{a_d}(t_id) rounded once in TP, and W and W^T both use exactly that value
+// (W^T is the exact transpose of the W applied); sums over points or nodes accumulate in T (the
+// lazily normalised double-float sum for MIXED).
 #include "fkski_internal.cuh"
 
 #include <algorithm>
@@ -22,6 +28,59 @@ template <int D>
 struct NA {
     static constexpr int v = D == 1 ? 4 : (D == 2 ? 16 : 64);
 };
+
+// Accumulators for sums of (TP weight) x (T value): plain FMA for FP32 / FP64 vectors, the
+// lazily normalised double-float sum for double-float vectors.
+template <typename T>
+struct SkiAcc {
+    T v;
+    __device__ __forceinline__ void zero() { v = T(0); }
+    template <typename TP>
+    __device__ __forceinline__ void add(TP w, T x) { v = fma((T)w, x, v); }
+    __device__ __forceinline__ T value() const { return v; }
+};
+template <>
+struct SkiAcc<dfl> {
+    dacc a;
+    __device__ __forceinline__ void zero() { dacc_zero(a); }
+    __device__ __forceinline__ void add(float w, dfl x) { dacc_add_fx(a, w, x); }
+    __device__ __forceinline__ dfl value() const { return dacc_value(a); }
+};
+
+// Sum over a warp (fixed butterfly tree).
+__device__ __forceinline__ float warp_sum_t(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+__device__ __forceinline__ double warp_sum_t(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+__device__ __forceinline__ dfl warp_sum_t(dfl x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        x = x + dfl(__shfl_xor_sync(0xFFFFFFFFu, x.hi, o), __shfl_xor_sync(0xFFFFFFFFu, x.lo, o));
+    return x;
+}
+
+// W's entry for stencil node a (digits a_k = bits 2k..2k+1 from the last axis) of a point with
+// weights w: the product over axes, rounded once in TP, axis 0 first.
+template <typename TP, int D>
+__device__ __forceinline__ TP w_entry(const TP (&w)[3][4], int a) {
+    int dg[3] = {0, 0, 0};
+    int rem = a;
+#pragma unroll
+    for (int q = D - 1; q >= 0; --q) {
+        dg[q] = rem & 3;
+        rem >>= 2;
+    }
+    TP e = w[0][dg[0]];
+#pragma unroll
+    for (int q = 1; q < D; ++q) e *= w[q][dg[q]];
+    return e;
+}
 
 // cell key -> the first stencil node of the cell (cell index c - 1 on each axis = key digit)
 struct SkiGeom {
@@ -40,8 +99,8 @@ __device__ __forceinline__ void key_digits(uint32_t key, const SkiGeom &g, int64
 
 // Per cell: Yc[a] = sum_{points i in the cell} v_i prod_k w_{a_k}(t_ik), a in [0,4)^d.
 // One warp per cell, lanes stride over the points; fixed shuffle tree (deterministic).
-template <typename T, int D>
-__global__ void __launch_bounds__(SKI_T) k_ski_cells(const Rec4<T> *__restrict__ pts, const uint32_t *__restrict__ off,
+template <typename TP, typename T, int D>
+__global__ void __launch_bounds__(SKI_T) k_ski_cells(const Rec4<TP> *__restrict__ pts, const uint32_t *__restrict__ off,
                                                      int64_t ncells, const T *__restrict__ v, T *__restrict__ yc,
                                                      const int *__restrict__ gate) {
     if (gate && *gate) return;
@@ -51,37 +110,22 @@ __global__ void __launch_bounds__(SKI_T) k_ski_cells(const Rec4<T> *__restrict__
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = wg; c < ncells; c += nw) {
         const uint32_t beg = off[c], end = off[c + 1];
-        T acc[NA_];
+        SkiAcc<T> acc[NA_];
 #pragma unroll
-        for (int a = 0; a < NA_; ++a) acc[a] = T(0);
+        for (int a = 0; a < NA_; ++a) acc[a].zero();
         for (uint32_t k = beg + lane; k < end; k += 32) {
-            const Rec4<T> r = pts[k];
+            const Rec4<TP> r = pts[k];
             const T vk = v[k];
-            T w[3][4];
+            TP w[3][4];
 #pragma unroll
-            for (int q = 0; q < D; ++q) keys_weights<T>(r.t[q], w[q]);
+            for (int q = 0; q < D; ++q) keys_weights<TP>(r.t[q], w[q]);
 #pragma unroll
-            for (int a = 0; a < NA_; ++a) {
-                T wa = vk;
-                int rem = a;
-#pragma unroll
-                for (int q = D - 1; q >= 0; --q) {
-                    wa *= w[q][rem & 3];
-                    rem >>= 2;
-                }
-                acc[a] += wa;
-            }
+            for (int a = 0; a < NA_; ++a) acc[a].add(w_entry<TP, D>(w, a), vk);
         }
 #pragma unroll
         for (int a = 0; a < NA_; ++a) {
-            T x = acc[a];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-            acc[a] = x;
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int a = 0; a < NA_; ++a) yc[c * NA_ + a] = acc[a];
+            const T x = warp_sum_t(acc[a].value());
+            if (lane == 0) yc[c * NA_ + a] = x;
         }
     }
 }
@@ -119,8 +163,8 @@ __global__ void k_ski_nodes(const T *__restrict__ yc, SkiGeom g, int64_t m, T *_
 }
 
 // ap_k = (W ku)_k + sigma^2 p_k (per point, cell order), partial p.ap per block.
-template <typename T, int D>
-__global__ void __launch_bounds__(SKI_T) k_ski_ap(const Rec4<T> *__restrict__ pts, const uint32_t *__restrict__ pkeys,
+template <typename TP, typename T, int D>
+__global__ void __launch_bounds__(SKI_T) k_ski_ap(const Rec4<TP> *__restrict__ pts, const uint32_t *__restrict__ pkeys,
                                                   int64_t n, SkiGeom g, const T *__restrict__ ku, const T *__restrict__ p,
                                                   T *__restrict__ ap, const double *__restrict__ sig2,
                                                   double *__restrict__ part, const int *__restrict__ gate) {
@@ -132,40 +176,24 @@ __global__ void __launch_bounds__(SKI_T) k_ski_ap(const Rec4<T> *__restrict__ pt
     if (D == 2) s1 = g.M[1];
     if (D == 3) { s1 = g.M[1] * g.M[2]; s2s = g.M[2]; }
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const Rec4<T> r = pts[k];
+        const Rec4<TP> r = pts[k];
         int64_t c[3] = {0, 0, 0};
         key_digits(pkeys[k], g, c);
-        T w[3][4];
+        TP w[3][4];
 #pragma unroll
-        for (int q = 0; q < D; ++q) keys_weights<T>(r.t[q], w[q]);
-        T acc = T(0);
-        if (D == 1) {
+        for (int q = 0; q < D; ++q) keys_weights<TP>(r.t[q], w[q]);
+        SkiAcc<T> acc;
+        acc.zero();
 #pragma unroll
-            for (int a = 0; a < 4; ++a) acc = fma(w[0][a], ku[c[0] + a], acc);
-        } else if (D == 2) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                T row = T(0);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) row = fma(w[1][b], ku[(c[0] + a) * s1 + c[1] + b], row);
-                acc = fma(w[0][a], row, acc);
-            }
-        } else {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                T pl = T(0);
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    T row = T(0);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) row = fma(w[2][e], ku[(c[0] + a) * s1 + (c[1] + b) * s2s + c[2] + e], row);
-                    pl = fma(w[1][b], row, pl);
-                }
-                acc = fma(w[0][a], pl, acc);
-            }
+        for (int a = 0; a < NA<D>::v; ++a) {
+            const int a0 = D == 1 ? a : (D == 2 ? (a >> 2) : (a >> 4));
+            const int a1 = D == 2 ? (a & 3) : ((a >> 2) & 3), a2 = a & 3;
+            const int64_t node = D == 1 ? c[0] + a0
+                               : (D == 2 ? (c[0] + a0) * s1 + c[1] + a1 : (c[0] + a0) * s1 + (c[1] + a1) * s2s + c[2] + a2);
+            acc.add(w_entry<TP, D>(w, a), ku[node]);
         }
         const T pk = p[k];
-        const T v = fma(s2, pk, acc);
+        const T v = fma(s2, pk, acc.value());
         ap[k] = v;
         dq = fma(pk, v, dq);
     }
@@ -266,28 +294,34 @@ __global__ void k_ski_p(int64_t n, T *__restrict__ p, const T *__restrict__ r, c
         p[k] = fma(b, p[k], r[k]);
 }
 
-template <typename T>
-__global__ void k_ski_init(int64_t n, const Rec4<T> *__restrict__ pts, T *__restrict__ x, T *__restrict__ r,
+template <typename TP, typename T>
+__global__ void k_ski_init(int64_t n, const Rec4<TP> *__restrict__ pts, T *__restrict__ x, T *__restrict__ r,
                            T *__restrict__ p) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const T y = pts[k].y;
+        const T y = T(pts[k].y);
         x[k] = T(0);
         r[k] = y;
         p[k] = y;
     }
 }
 
-template <typename T, int D>
-static void launch_wt(const Rec4<T> *pts, const uint32_t *off, int64_t ncells, const SkiGeom &g, int64_t m, const T *v,
+template <typename T>
+__global__ void k_ski_out(const T *__restrict__ in, OutT<T> *__restrict__ out, int64_t m) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = (OutT<T>)(double)in[e];
+}
+
+template <typename TP, typename T, int D>
+static void launch_wt(const Rec4<TP> *pts, const uint32_t *off, int64_t ncells, const SkiGeom &g, int64_t m, const T *v,
                       T *yc, T *u, const int *gate, cudaStream_t s) {
     const unsigned gc = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(ncells * 32, SKI_T), 152 * 16));
-    k_ski_cells<T, D><<<gc, SKI_T, 0, s>>>(pts, off, ncells, v, yc, gate);
+    k_ski_cells<TP, T, D><<<gc, SKI_T, 0, s>>>(pts, off, ncells, v, yc, gate);
     const unsigned gn = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, 256), 152 * 8));
     k_ski_nodes<T, D><<<gn, 256, 0, s>>>(yc, g, m, u, gate);
 }
 
-template <typename T, int D>
-static int ski_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, T *a_out, T *v_out,
+template <typename TP, typename T, int D>
+static int ski_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *o, OutT<T> *a_out, OutT<T> *v_out,
                      fkski_info *info, cudaStream_t s) {
     const int64_t n = st->n, m = st->m, ncells = st->ncells;
     constexpr int NA_ = NA<D>::v;
@@ -298,10 +332,10 @@ static int ski_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
         g.ncell[k] = st->grid.M[k] - 3;
         g.M[k] = st->grid.M[k];
     }
-    const Rec4<T> *pts = (const Rec4<T> *)st->pts;
+    const Rec4<TP> *pts = (const Rec4<TP> *)st->pts;
     // operator and buffers
     KgOp *kg = nullptr;
-    FK_TRY(kgop_create(&st->grid, sizeof(T) == 4 ? FKSKI_F32 : FKSKI_F64, &kg));
+    FK_TRY(kgop_create(&st->grid, dtype_of<T>(), &kg));
     struct Guard {
         KgOp *kg;
         std::vector<void *> bufs;
@@ -318,7 +352,7 @@ static int ski_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
         guard.bufs.push_back(*p);
         return FKSKI_OK;
     };
-    T *x, *r, *p, *ap, *u, *ku, *yc;
+    T *x, *r, *p, *ap, *u, *ku, *yc, *aT, *vT;
     double *part, *sc, *sig2;
     int *flags;
     const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, SKI_T), 152 * 8));
@@ -329,6 +363,8 @@ static int ski_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     FK_TRY(get((void **)&u, sizeof(T) * m));
     FK_TRY(get((void **)&ku, sizeof(T) * m));
     FK_TRY(get((void **)&yc, sizeof(T) * ncells * NA_));
+    FK_TRY(get((void **)&aT, sizeof(T) * m));
+    FK_TRY(get((void **)&vT, sizeof(T) * m));
     FK_TRY(get((void **)&part, sizeof(double) * gb));
     FK_TRY(get((void **)&sc, sizeof(double) * 8));
     FK_TRY(get((void **)&sig2, sizeof(double)));
@@ -343,7 +379,7 @@ static int ski_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     FK_CUDA(cudaMemcpyAsync(sc, hs, sizeof(hs), cudaMemcpyHostToDevice, s));
     FK_CUDA(cudaMemcpyAsync(flags, hf, sizeof(hf), cudaMemcpyHostToDevice, s));
     FK_CUDA(cudaMemcpyAsync(sig2, &s2v, sizeof(double), cudaMemcpyHostToDevice, s));
-    k_ski_init<T><<<gb, SKI_T, 0, s>>>(n, pts, x, r, p);
+    k_ski_init<TP, T><<<gb, SKI_T, 0, s>>>(n, pts, x, r, p);
     FK_LAUNCH();
     // capture a chunk of iterations on an internal stream
     cudaStream_t cs;
@@ -358,10 +394,10 @@ static int ski_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     kgop_set_gate(kg, flags);
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
     for (int it = 0; it < check && e == cudaSuccess && rc == FKSKI_OK; ++it) {
-        launch_wt<T, D>(pts, st->offsets, ncells, g, m, p, yc, u, flags, cs);
+        launch_wt<TP, T, D>(pts, st->offsets, ncells, g, m, p, yc, u, flags, cs);
         rc = kgop_apply(kg, u, ku, 1, nullptr, 0.0, cs);
         if (rc) break;
-        k_ski_ap<T, D><<<gb, SKI_T, 0, cs>>>(pts, st->pkeys, n, g, ku, p, ap, sig2, part, flags);
+        k_ski_ap<TP, T, D><<<gb, SKI_T, 0, cs>>>(pts, st->pkeys, n, g, ku, p, ap, sig2, part, flags);
         k_ski_alpha<<<1, 256, 0, cs>>>(part, (int)gb, sc, flags);
         k_ski_xr<T><<<gb, SKI_T, 0, cs>>>(n, x, r, p, ap, sc, part, flags);
         k_ski_beta<<<1, 256, 0, cs>>>(part, (int)gb, sc, flags);
@@ -398,10 +434,16 @@ static int ski_typed(fkski_stats *st, const fkski_kernel *kern, const fkski_opts
     int hf2[4] = {0, 0, 0, 0};
     double hs2[8];
     if (rc == FKSKI_OK) {
-        // a = W^T z, v = K_G a
-        launch_wt<T, D>(pts, st->offsets, ncells, g, m, x, yc, a_out, nullptr, s);
+        // a = W^T z, v = K_G a (in T, then to the output type)
+        launch_wt<TP, T, D>(pts, st->offsets, ncells, g, m, x, yc, aT, nullptr, s);
         FK_LAUNCH();
-        rc = kgop_apply(kg, a_out, v_out, 1, nullptr, 0.0, s);
+        rc = kgop_apply(kg, aT, vT, 1, nullptr, 0.0, s);
+        if (rc == FKSKI_OK) {
+            const unsigned gv = (unsigned)std::min<int64_t>(cdiv(m, 256), 152 * 8);
+            k_ski_out<T><<<gv, 256, 0, s>>>(aT, a_out, m);
+            k_ski_out<T><<<gv, 256, 0, s>>>(vT, v_out, m);
+            FK_LAUNCH();
+        }
     }
     if (rc == FKSKI_OK) {
         FK_CUDA(cudaMemcpyAsync(hf2, flags, sizeof(hf2), cudaMemcpyDeviceToHost, s));
@@ -429,17 +471,29 @@ int ski_solve_impl(fkski_stats *st, const fkski_kernel *kern, const fkski_opts *
     if (!(kern->noise_var > 0.0) || !std::isfinite(kern->noise_var)) return FKSKI_E_INVALID_ARG;
     if (o.maxiter < 1 || !(o.rtol >= 0.0)) return FKSKI_E_INVALID_ARG;
     if (info) memset(info, 0, sizeof(*info));
-    // the vectors are in the points' precision (the records are stored in it)
+    if (o.precision != FKSKI_MIXED && o.precision != FKSKI_DOUBLE && o.precision != FKSKI_FP32)
+        return FKSKI_E_INVALID_ARG;
+    // FP32 points: vectors per the precision mode (outputs FP32 except for DOUBLE); FP64 points: FP64
     if (st->dtype == FKSKI_F32) {
+        if (o.precision == FKSKI_DOUBLE) {
+            double *a = (double *)a_out, *v = (double *)v_out;
+            return st->d == 1 ? ski_typed<float, double, 1>(st, kern, &o, a, v, info, s)
+                 : st->d == 2 ? ski_typed<float, double, 2>(st, kern, &o, a, v, info, s)
+                              : ski_typed<float, double, 3>(st, kern, &o, a, v, info, s);
+        }
         float *a = (float *)a_out, *v = (float *)v_out;
-        return st->d == 1 ? ski_typed<float, 1>(st, kern, &o, a, v, info, s)
-             : st->d == 2 ? ski_typed<float, 2>(st, kern, &o, a, v, info, s)
-                          : ski_typed<float, 3>(st, kern, &o, a, v, info, s);
+        if (o.precision == FKSKI_FP32)
+            return st->d == 1 ? ski_typed<float, float, 1>(st, kern, &o, a, v, info, s)
+                 : st->d == 2 ? ski_typed<float, float, 2>(st, kern, &o, a, v, info, s)
+                              : ski_typed<float, float, 3>(st, kern, &o, a, v, info, s);
+        return st->d == 1 ? ski_typed<float, dfl, 1>(st, kern, &o, a, v, info, s)
+             : st->d == 2 ? ski_typed<float, dfl, 2>(st, kern, &o, a, v, info, s)
+                          : ski_typed<float, dfl, 3>(st, kern, &o, a, v, info, s);
     }
     double *a = (double *)a_out, *v = (double *)v_out;
-    return st->d == 1 ? ski_typed<double, 1>(st, kern, &o, a, v, info, s)
-         : st->d == 2 ? ski_typed<double, 2>(st, kern, &o, a, v, info, s)
-                      : ski_typed<double, 3>(st, kern, &o, a, v, info, s);
+    return st->d == 1 ? ski_typed<double, double, 1>(st, kern, &o, a, v, info, s)
+         : st->d == 2 ? ski_typed<double, double, 2>(st, kern, &o, a, v, info, s)
+                      : ski_typed<double, double, 3>(st, kern, &o, a, v, info, s);
 }
 
 }  // namespace fk

@@ -498,6 +498,23 @@ __device__ __forceinline__ void st_quad<double>(double *p, const double v[4]) {
     reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
 
+// Band-product accumulator: FMA in TX, or the lazily normalised double-float sum for an FP32
+// band on double-float vectors.
+template <typename TB, typename TX>
+struct BandAcc {
+    TX v;
+    __device__ __forceinline__ void zero() { v = TX(0); }
+    __device__ __forceinline__ void add(TB b, TX x) { v = fma((TX)b, x, v); }
+    __device__ __forceinline__ TX value() const { return v; }
+};
+template <>
+struct BandAcc<float, dfl> {
+    dacc a;
+    __device__ __forceinline__ void zero() { dacc_zero(a); }
+    __device__ __forceinline__ void add(float b, dfl x) { dacc_add_fx(a, b, x); }
+    __device__ __forceinline__ dfl value() const { return dacc_value(a); }
+};
+
 template <typename TB, typename TX, int NROW, int RB>
 __global__ void __launch_bounds__(CG_T, RB <= 2 ? 2 : 1) k_band_spmv4g(const TB *__restrict__ band, const TX *__restrict__ x,
                                                           TX *__restrict__ u, int64_t m, int R, RowOffs rows,
@@ -517,11 +534,11 @@ __global__ void __launch_bounds__(CG_T, RB <= 2 ? 2 : 1) k_band_spmv4g(const TB 
     const int64_t nquad = m >> 2;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nquad; t += (int64_t)nwork * blockDim.x) {
         const int64_t i0 = t << 2;
-        TX acc[RB][4];
+        BandAcc<TB, TX> acc[RB][4];
 #pragma unroll
         for (int k = 0; k < RB; ++k)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[k][q] = TX(0);
+            for (int q = 0; q < 4; ++q) acc[k][q].zero();
 #pragma unroll 1
         for (int row = 0; row < NROW; ++row) {
             Quad<TB> b[7];
@@ -548,18 +565,21 @@ __global__ void __launch_bounds__(CG_T, RB <= 2 ? 2 : 1) k_band_spmv4g(const TB 
 #pragma unroll
                     for (int e = 0; e < 7; ++e)
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[k][q] = band_fma<TB, TX>(b[e].v[q], v[e + 1 + q], acc[k][q]);
+                        for (int q = 0; q < 4; ++q) acc[k][q].add(b[e].v[q], v[e + 1 + q]);
                 }
             }
         }
 #pragma unroll
         for (int k = 0; k < RB; ++k)
             if (k < R) {
-                st_quad<TX>(u + (int64_t)k * m + i0, acc[k]);
+                TX uv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) uv[q] = acc[k][q].value();
+                st_quad<TX>(u + (int64_t)k * m + i0, uv);
                 if (part) {
                     const Quad<TX> xv = ld_quad<TX>(x + (int64_t)k * m + i0, false);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) dq0[k] = fma(acc[k][q], xv.v[q], dq0[k]);
+                    for (int q = 0; q < 4; ++q) dq0[k] = fma(uv[q], xv.v[q], dq0[k]);
                     if (g) {
                         const Quad<TX> gv = ld_quad<TX>(g + (int64_t)k * m + i0, false);
 #pragma unroll
@@ -582,8 +602,9 @@ __global__ void __launch_bounds__(CG_T, RB <= 2 ? 2 : 1) k_band_spmv4g(const TB 
 // The half-band product for one double-float right-hand side (the MIXED iterations): the same
 // traversal as k_band_spmv4h (direct quads of the stored upper diagonals at i0, mirrored quads
 // around i0 - rowbase), with x and u as double-float values (a 12-wide window is six 16-byte
-// loads) and every band product accumulated exactly by band_fma.  The band stays FP32, so the
-// bytes read per launch are the FP32 half band plus 16 B per node for x and u.
+// loads) and every band product accumulated in a lazily normalised double-float sum (dacc).
+// The band stays FP32, so the bytes read per launch are the FP32 half band plus 16 B per node
+// for x and u.
 template <int NROW, int FIN>
 __global__ void __launch_bounds__(CG_T, 2) k_band_spmv4hd(const float *__restrict__ hb, const dfl *__restrict__ x,
                                                            dfl *__restrict__ u, int64_t m, RowOffs rows,
@@ -630,7 +651,9 @@ __global__ void __launch_bounds__(CG_T, 2) k_band_spmv4hd(const float *__restric
     auto comp = [](const float4 &f, int q) { return q == 0 ? f.x : (q == 1 ? f.y : (q == 2 ? f.z : f.w)); };
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nquad; t += (int64_t)nwork * blockDim.x) {
         const int64_t i0 = t << 2;
-        dfl acc[4] = {dfl(0), dfl(0), dfl(0), dfl(0)};
+        dacc acc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dacc_zero(acc[q]);
         {
             dfl v[12];
             xwin(i0 - 4, v);
@@ -644,11 +667,11 @@ __global__ void __launch_bounds__(CG_T, 2) k_band_spmv4hd(const float *__restric
             for (int dx = 0; dx < 4; ++dx)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    acc[q] = band_fma<float, dfl>(comp(hc[dx], q), v[q + dx + 4], acc[q]);
+                    dacc_add_fx(acc[q], comp(hc[dx], q), v[q + dx + 4]);
                     if (dx > 0) {
                         const int j = q - dx;
                         const float h = j < 0 ? comp(hp[dx], j + 4) : comp(hc[dx], j);
-                        acc[q] = band_fma<float, dfl>(h, v[j + 4], acc[q]);
+                        dacc_add_fx(acc[q], h, v[j + 4]);
                     }
                 }
         }
@@ -666,7 +689,7 @@ __global__ void __launch_bounds__(CG_T, 2) k_band_spmv4hd(const float *__restric
 #pragma unroll
                 for (int e = 0; e < 7; ++e)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[q] = band_fma<float, dfl>(comp(dq[e], q), v[q + e + 1], acc[q]);
+                    for (int q = 0; q < 4; ++q) dacc_add_fx(acc[q], comp(dq[e], q), v[q + e + 1]);
             }
             dfl vm[12];
             xwin(i0 - rb - 4, vm);
@@ -681,17 +704,20 @@ __global__ void __launch_bounds__(CG_T, 2) k_band_spmv4hd(const float *__restric
                 for (int q = 0; q < 4; ++q) {
                     const int tt = 3 - e + q;
                     const float h = tt < 0 ? comp(qa, tt + 4) : (tt < 4 ? comp(qb, tt) : comp(qc, tt - 4));
-                    acc[q] = band_fma<float, dfl>(h, vm[tt + 4], acc[q]);
+                    dacc_add_fx(acc[q], h, vm[tt + 4]);
                 }
             }
         }
+        dfl ur[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ur[q] = dacc_value(acc[q]);
         float4 *uq = reinterpret_cast<float4 *>(u + i0);
-        uq[0] = make_float4(acc[0].hi, acc[0].lo, acc[1].hi, acc[1].lo);
-        uq[1] = make_float4(acc[2].hi, acc[2].lo, acc[3].hi, acc[3].lo);
+        uq[0] = make_float4(ur[0].hi, ur[0].lo, ur[1].hi, ur[1].lo);
+        uq[1] = make_float4(ur[2].hi, ur[2].lo, ur[3].hi, ur[3].lo);
         if (part) {
             const Quad<dfl> xv = ld_quad<dfl>(x + i0, false);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dq0 = fma(acc[q], xv.v[q], dq0);
+            for (int q = 0; q < 4; ++q) dq0 = fma(ur[q], xv.v[q], dq0);
             if (g) {
                 const Quad<dfl> gv = ld_quad<dfl>(g + i0, false);
 #pragma unroll
@@ -1817,14 +1843,6 @@ static int fcg_wtx64(fkski_stats *st, CgVecs<T> &V, int R, double *out64, cudaSt
     return FKSKI_OK;
 }
 
-// Element type of the mean outputs a, v: FP32 for the MIXED (double-float) solves.
-template <typename T>
-struct OutOf { using type = T; };
-template <>
-struct OutOf<dfl> { using type = float; };
-template <typename T>
-using OutT = typename OutOf<T>::type;
-
 // a = W^T z (FP64 -> output type) and v = K_G a (FP64 product -> output type) of a finished
 // single-rhs solve.
 template <typename T>
@@ -2045,6 +2063,13 @@ int band_mvm_impl(const fkski_stats *stc, const void *x, void *u, int nrhs, int 
         FK_TRY(stats_as<float>(st, &band, &wty, &wtz, s));
         return launch_spmv<float, float>(band, st->grid, (const float *)x, (float *)u, st->m, nrhs, nullptr, 1, nullptr,
                                          nullptr, gb, s);
+    }
+    if (dtype == FK_DF) {
+        const float *band;
+        const dfl *wty, *wtz;
+        FK_TRY(stats_as<dfl>(st, &band, &wty, &wtz, s));
+        return launch_spmv<float, dfl>(band, st->grid, (const dfl *)x, (dfl *)u, st->m, nrhs, nullptr, 1, nullptr,
+                                       nullptr, gb, s);
     }
     if (dtype != FKSKI_F64) return FKSKI_E_INVALID_ARG;
     // FP64 vectors against the stored band (FP32 values promoted when the statistics are FP32)

@@ -4,6 +4,7 @@
 //   a|s|m ah al bh bl    (ah + al) + - * (bh + bl)
 //   f ah al b            (ah + al) * b, b an FP32 number
 //   x ah al b xh xl      (ah + al) + b * (xh + xl), the band-product accumulation
+//   A k [b xh xl]*k      sum of k products b * (xh + xl) in the lazily normalised accumulator
 #include <cstdio>
 #include "dfloat.cuh"
 
@@ -21,6 +22,17 @@ int main() {
             float ah, al, b;
             if (scanf("%a %a %a", &ah, &al, &b) != 3) return 1;
             r = fk::df_mul_f(dfl(ah, al), b);
+        } else if (op[0] == 'A') {
+            int k;
+            if (scanf("%d", &k) != 1) return 1;
+            fk::dacc acc;
+            fk::dacc_zero(acc);
+            for (int i = 0; i < k; ++i) {
+                float b, xh, xl;
+                if (scanf("%a %a %a", &b, &xh, &xl) != 3) return 1;
+                fk::dacc_add_fx(acc, b, dfl(xh, xl));
+            }
+            r = fk::dacc_value(acc);
         } else if (op[0] == 'x') {
             float ah, al, b, xh, xl;
             if (scanf("%a %a %a %a %a", &ah, &al, &b, &xh, &xl) != 5) return 1;

@@ -3,11 +3,11 @@
 The header's inline functions are compiled for the host by nvcc and evaluated on random operands
 spanning many binades; every result is compared with the exact rational value.  Bars: the
 Dekker-style addition errs by at most 2^-45 (|a| + |b|), products by 2^-45 |a b|, the band
-accumulation acc + b x by 2^-45 (|acc| + |b x|), and the conversion from a double by 2^-48 |v|;
-every result is normalised (hi = fl(hi + lo))."""
+accumulation acc + b x by 2^-45 (|acc| + |b x|), a 343-term lazily normalised band sum by
+2^-40 sum |b x| (343 terms of at most ~2^-48 each), and the conversion from a double by
+2^-48 |v|; every result is normalised (hi = fl(hi + lo))."""
 import os
 import shutil
-import struct
 import subprocess
 from fractions import Fraction
 
@@ -107,3 +107,24 @@ def test_from_double(driver):
     for v, (h, l) in zip(vs, res):
         assert _normalised(h, l)
         assert abs(Fraction(h) + Fraction(l) - Fraction(v)) <= Fraction(2) ** -48 * abs(Fraction(v))
+
+
+def test_lazy_band_sum(driver):
+    rng = np.random.default_rng(3)
+    lines, terms = [], []
+    for case in range(40):
+        k = 343
+        bs = [_f32(v) for v in rng.uniform(-1, 1, k) * 2.0 ** rng.integers(-6, 6, k)]
+        xs = _operands(rng, k)
+        if case % 4 == 0:  # heavy cancellation: the sum is far below its terms
+            xs[-1] = (_f32(-sum(b * (x[0] + x[1]) for b, x in zip(bs[:-1], xs[:-1])) / bs[-1]), 0.0)
+            xs[-1] = _split(xs[-1][0])
+        terms.append((bs, xs))
+        lines.append(f"A {k} " + " ".join(f"{b.hex()} {x[0].hex()} {x[1].hex()}" for b, x in zip(bs, xs)))
+    res = _run(driver, lines)
+    for (bs, xs), (h, l) in zip(terms, res):
+        prods = [Fraction(b) * (Fraction(x[0]) + Fraction(x[1])) for b, x in zip(bs, xs)]
+        exact = sum(prods)
+        mag = sum(abs(p) for p in prods)
+        assert _normalised(h, l)
+        assert abs(Fraction(h) + Fraction(l) - exact) <= Fraction(2) ** -40 * mag

@@ -1,12 +1,17 @@
 """Plain SKI baseline (fkski_ski_solve: n-space CG, Alg. 1 from x0 = 0) against the oracle's
 n-space CG and against the factorized solver.
 
-Bars: FP64 -- the posterior mean within 1e-6 relative L2 of the oracle at equal rtol, and the
-iteration count within max(3, 10%): the same recurrence, but the GPU sums its inner products in
-cell order and in blocks, and at rtol 1e-9 on these systems (cond ~1e4) that rounding moves the
-count by several iterations (measured 141 vs 151).  FP32 -- plain FP32 CG as the paper's baseline
-(no FP64 solution, no residual replacement): 3e-4 at rtol 1e-4.  The factorized solver gives the
-same mean (Theorem 1): 1e-6 (FP64), 3e-4 (FP32)."""
+Bars: FP64 points -- the posterior mean within 1e-6 relative L2 of the oracle at equal rtol, and
+the iteration count within max(3, 10%): the same recurrence, but the GPU sums its inner products
+in cell order and in blocks, and at rtol 1e-9 on these systems (cond ~1e4) that rounding moves the
+count by several iterations (measured 141 vs 151).  FP32 points, MIXED (double-float vectors):
+1e-4 at rtol 1e-6 and the iteration count within max(3, 15%): the sums run in cell order as for
+FP64, and W's entries are the FP32 weight products of the FP32 local coordinates (a W within
+~1e-7 of the oracle's FP64 one), which moves the count further (measured 555 vs 520 in 2-D,
+536 vs 477 in 3-D).  The FP32 mode (plain
+FP32 CG, no FP64 solution, no residual replacement) is held to its attainable accuracy, 3e-4 at
+rtol 1e-4: FP32 rounding in every product delays CG on these systems.  The factorized solver
+gives the same mean (Theorem 1): 1e-6 (FP64), 1e-4 (MIXED)."""
 import numpy as np
 import pytest
 import torch
@@ -26,7 +31,8 @@ def _tt(a):
     (2, (30, 26), 12000, synth.Kernel(synth.RBF, (0.12, 0.15), 1.0, 0.02), np.float64, 1e-8),
     (2, (24, 25), 9000, synth.Kernel(synth.MATERN52, (0.1, 0.12), 1.0, 0.02), np.float64, 1e-8),
     (3, (12, 11, 13), 15000, synth.Kernel(synth.RBF, (0.2, 0.25, 0.2), 1.0, 0.05), np.float64, 1e-8),
-    (2, (40, 36), 30000, synth.Kernel(synth.RBF, (0.1, 0.1), 1.0, 0.05), np.float32, 1e-4),
+    (2, (40, 36), 30000, synth.Kernel(synth.RBF, (0.1, 0.1), 1.0, 0.05), np.float32, 1e-6),
+    (3, (12, 11, 13), 20000, synth.Kernel(synth.RBF, (0.2, 0.25, 0.2), 1.0, 0.05), np.float32, 1e-6),
 ])
 def test_ski_matches_oracle_cg(fk, oracle_mod, d, M, n, kern, dtype, rtol):
     from oracle import core
@@ -35,15 +41,27 @@ def test_ski_matches_oracle_cg(fk, oracle_mod, d, M, n, kern, dtype, rtol):
     a, v, info = fk.ski_solve(st, kern, rtol=rtol, maxiter=6000)
     a_ref, v_ref, it_ref, _ = core.nspace_mean(grid, kern, X.astype(np.float64), y.astype(np.float64), rtol=rtol,
                                                x0_mode=0)
-    tol = 1e-6 if dtype == np.float64 else 3e-4
+    tol = 1e-6 if dtype == np.float64 else 1e-4
     assert rel_fro(v.double().cpu().numpy(), v_ref) <= tol
     assert rel_fro(a.double().cpu().numpy(), a_ref) <= max(tol, 1e-5)
-    if dtype == np.float64:
-        assert abs(info["iters"] - it_ref) <= max(3, 0.10 * it_ref), (info["iters"], it_ref)
+    window = 0.10 if dtype == np.float64 else 0.15
+    assert abs(info["iters"] - it_ref) <= max(3, window * it_ref), (info["iters"], it_ref)
     # the factorized solver gives the same posterior mean
     _, v_f, _ = fk.solve(st, kern, rtol=rtol, maxiter=6000, x0_mode=0,
                          precision=fk.DOUBLE if dtype == np.float64 else fk.MIXED)
-    assert rel_fro(v.double().cpu().numpy(), v_f.double().cpu().numpy()) <= (1e-6 if dtype == np.float64 else 3e-4)
+    assert rel_fro(v.double().cpu().numpy(), v_f.double().cpu().numpy()) <= (1e-6 if dtype == np.float64 else 1e-4)
+
+
+def test_ski_fp32_mode(fk, oracle_mod):
+    """Plain FP32 n-space CG (the FP32 mode): held to its attainable accuracy."""
+    from oracle import core
+    grid, X, y = problem(2, (40, 36), 30000, seed=51, dtype=np.float32)
+    kern = synth.Kernel(synth.RBF, (0.1, 0.1), 1.0, 0.05)
+    st = fk.precompute(_tt(X), _tt(y), grid, keep_points=True)
+    a, v, info = fk.ski_solve(st, kern, rtol=1e-4, maxiter=6000, precision=fk.FP32)
+    _, v_ref, _, _ = core.nspace_mean(grid, kern, X.astype(np.float64), y.astype(np.float64), rtol=1e-4, x0_mode=0)
+    assert v.dtype == torch.float32
+    assert rel_fro(v.double().cpu().numpy(), v_ref) <= 3e-4
 
 
 def test_ski_needs_points(fk):
