@@ -59,9 +59,11 @@ def _check_sampled_rows(fk, st, X, y, grid, keys, n_nodes, seed, nprobe=0, probe
     ex = fk.stats_export(st)
     flat = np.ravel_multi_index(tuple(nodes), tuple(M))
     gb, rb = ex["band"][:, flat], ref["band"][:, flat]
-    assert rel_fro(gb, rb) <= 1e-6, rel_fro(gb, rb)
-    assert np.max(np.abs(gb - rb)) <= 1e-6 * np.max(np.abs(rb))
-    assert rel_fro(ex["wty"][flat], ref["wty"][flat]) <= 1e-6
+    eb, em = rel_fro(gb, rb), float(np.max(np.abs(gb - rb)) / np.max(np.abs(rb)))
+    ew = rel_fro(ex["wty"][flat], ref["wty"][flat])
+    print(f"rows at {n_nodes} nodes ({idx.size} points): band rel {eb:.2e} max {em:.2e}, W^T y rel {ew:.2e}")
+    assert eb <= 1e-6 and em <= 1e-6
+    assert ew <= 1e-6
     if nprobe:
         # W^T z over the same points: the probe signs depend on the global point index
         Z = np.stack([core.rademacher(probe_seed, p, X.shape[1])[idx] for p in range(nprobe)])
