@@ -191,6 +191,33 @@ def test_band_mvm_paths(fk, oracle_mod, d, M, R):
     assert rel_fro(u0, U32[:1]) <= 1e-6
 
 
+@pytest.mark.parametrize("d,M,R", [(1, (400,), 1), (2, (36, 44), 1), (3, (12, 10, 16), 1), (3, (9, 8, 10), 1),
+                                   (3, (48, 44, 40), 1), (3, (12, 10, 16), 3)])
+def test_band_mvm_double_float(fk, oracle_mod, d, M, R):
+    """The MIXED solver's band product: double-float (hi, lo) vectors against the stored FP32 band,
+    on the half-band path (one rhs, M_last a multiple of 4; the many-tile grid included), the
+    generic path and several rhs.  Each entry is held to the double-float accumulation bound,
+    |u - (W^T W) x| <= 2^-40 sum_j |b_ij x_j| + 2^-47 |u|, against the exact product of the band
+    values the GPU holds (exported, FP32 values) with the exact values hi + lo it was given."""
+    from oracle import core
+    grid, X, y = problem(d, M, 20000, seed=13)
+    st = fk.precompute(_tt(X), _tt(y), grid)
+    band = fk.stats_export(st)["band"]
+    v = np.random.default_rng(R + d).normal(size=(R, grid.m))
+    hi = v.astype(np.float32)
+    lo = (v - hi.astype(np.float64)).astype(np.float32)
+    xdf = np.stack([hi, lo], axis=-1)
+    x = hi.astype(np.float64) + lo.astype(np.float64)
+    out = fk.band_mvm(st, _tt(xdf if R > 1 else xdf[0]), double_float=True).cpu().numpy().reshape(R, grid.m, 2)
+    u = out[..., 0].astype(np.float64) + out[..., 1].astype(np.float64)
+    uref = core.band_matvec(grid, band, x.T).T
+    scale = core.band_matvec(grid, np.abs(band), np.abs(x).T).T
+    err = np.abs(u - uref)
+    assert np.all(err <= 2.0 ** -40 * scale + 2.0 ** -47 * np.abs(uref)), float(np.max(err / np.maximum(scale, 1e-300)))
+    # normalised pairs: hi = fl(hi + lo)
+    np.testing.assert_array_equal(out[..., 0], (out[..., 0] + out[..., 1]).astype(np.float32))
+
+
 def test_band_mvm_half_many_tiles(fk, oracle_mod):
     """The symmetric half-band product on a grid with more row tiles than SMs, so that each
     persistent CTA walks several tiles and the mirrored windows (up to ~10 tiles back) cross tile
