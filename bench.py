@@ -190,10 +190,11 @@ def host_info():
     return info
 
 
-def cpu_baseline_suite(prob, sample_all: int, sample_one: int):
+def cpu_baseline_suite(prob, sample_all: int, sample_one: int, fwd_bwd_iters: int = 2):
     """The FP64 CPU oracle as it stands, on the host cores (OpenMP precompute over cell slabs) and
     on one core: precompute on bounded samples of the four workloads, and the n-space CG (Alg. 1,
-    plain SKI, CSR W + K_G) per iteration on c1-c3 (numpy/scipy, n sampled for c3).  Returns the
+    plain SKI, CSR W + K_G) per iteration on c1-c3 (numpy/scipy, n sampled for c3), and the FP64
+    fwd+bwd at c3 per CG iteration over its 17 right-hand sides (n = 1e6).  Returns the
     cpu_baseline object of the JSON line (value: radar precompute on all cores)."""
     import oracle
     from oracle import core, lib
@@ -231,6 +232,24 @@ def cpu_baseline_suite(prob, sample_all: int, sample_one: int):
         core.cg(mv, b, None, 0.0, 10)
         cg_ms[name] = {"n": int(ns), "m": int(pr.grid.m), "ms_per_iter": (time.perf_counter() - t0) / 10 * 1e3}
     out["nspace_cg"] = cg_ms
+    if fwd_bwd_iters > 0:
+        # FP64 fwd+bwd at c3 (n-space CG on the mean and the 16 probes, SLQ + Hutchinson, same
+        # probes as the GPU): every solve stopped after k iterations; the difference of two k
+        # gives the cost of one iteration over all 17 right-hand sides, set-up excluded
+        pr = work["c3 grf_3d"]
+        ns = min(pr.n, 1_000_000)
+        Xs = np.ascontiguousarray(pr.X[:, :ns]).astype(np.float64)
+        ys = np.asarray(pr.y[:ns], dtype=np.float64)
+        Z = np.stack([core.rademacher(0, p, ns) for p in range(16)])
+        ts = {}
+        for k in (1, 1 + fwd_bwd_iters):
+            t0 = time.perf_counter()
+            core.loglik_grad_stochastic(pr.grid, pr.kernel, Xs, ys, Z, rtol=0.0, maxiter=k)
+            ts[k] = time.perf_counter() - t0
+        per_it = (ts[1 + fwd_bwd_iters] - ts[1]) / fwd_bwd_iters
+        out["fwd_bwd_c3"] = {"n": int(ns), "m": int(pr.grid.m), "rhs": 17, "probes": 16,
+                             "iters_timed": fwd_bwd_iters, "s_at_1_iter": ts[1],
+                             "s_per_iter_all_rhs": per_it}
     r4 = pre["c4 radar_3d"]["all_cores"]
     out.update(value=r4["gpoints_per_s"], unit="Gpoints/s", cores=ncores,
                sample=f"first {r4['points']} radar points, W^T W / W^T y / stable sort in FP64 on {ncores} "
@@ -351,6 +370,8 @@ def main():
     ap.add_argument("--cpu-sample-one", type=int, default=100_000, help="points per workload, one core")
     ap.add_argument("--maxiter", type=int, default=60000)
     ap.add_argument("--grad-maxiter", type=int, default=30000)
+    ap.add_argument("--cpu-fwd-bwd-iters", type=int, default=2,
+                    help="CG iterations timed in the oracle's FP64 fwd+bwd at c3 (0: skip)")
     ap.add_argument("--no-iter-vs-n", action="store_true", help="skip ms/iteration at n = 1e7, 3e7, 1.2e8")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     ap.add_argument("--no-ski", action="store_true", help="skip the plain-SKI per-iteration comparison")
@@ -585,7 +606,13 @@ def main():
     # CPU oracle baseline (rank 0 at N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample > 0:
-        cpu = cpu_baseline_suite(prob, args.cpu_sample, args.cpu_sample_one)
+        cpu = cpu_baseline_suite(prob, args.cpu_sample, args.cpu_sample_one, args.cpu_fwd_bwd_iters)
+        fb = cpu.get("fwd_bwd_c3")
+        if fb is not None and grad_info is not None:
+            # the oracle at the GPU's iteration count (the larger of the two legs), extrapolated
+            it = max(grad_info["cg_iters_mixed_max"], grad_info["cg_iters_fp64_max"])
+            fb["extrapolated_s_at_gpu_iters"] = fb["s_at_1_iter"] + fb["s_per_iter_all_rhs"] * (it - 1)
+            fb["gpu_iters"] = it
 
     if rank != 0:
         return

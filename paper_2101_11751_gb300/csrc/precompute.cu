@@ -349,6 +349,14 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t dg, int bits, unsigned 
     return __match_any_sync(0xFFFFFFFFu, dg) & valid_mask;
 }
 
+// Key of element i of a pass input: the cell keys themselves (first pass) or the .x half of the
+// packed (key, point index) pairs an earlier pass wrote.
+template <bool PACKED, typename I>
+__device__ __forceinline__ uint32_t rs_key(const uint32_t *__restrict__ kin, I i) {
+    return PACKED ? __ldcs(kin + 2 * i) : __ldcs(kin + i);
+}
+
+template <bool PACKED>
 __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
                                                      int bits, uint32_t *__restrict__ ghist, int64_t ntiles) {
     __shared__ uint32_t h[1 << RS_MAXBITS];
@@ -362,7 +370,7 @@ __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint32_t *__restrict_
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int64_t i = base + (int64_t)k * RS_T + threadIdx.x;
-        kv[k] = i < n ? __ldcs(keys + i) : 0u;
+        kv[k] = i < n ? rs_key<PACKED>(keys, i) : 0u;
     }
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
@@ -376,10 +384,12 @@ __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint32_t *__restrict_
     for (int i = threadIdx.x; i < nb; i += RS_T) ghist[(int64_t)i * ntiles + blockIdx.x] = h[i];
 }
 
-// Scatter one tile stably.  gscan = exclusive scan of ghist in digit-major order.
-template <bool FIRST, bool WRITE_KEYS>
-__global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                                                        uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+// Scatter one tile stably.  gscan = exclusive scan of ghist in digit-major order.  The first pass
+// reads the cell keys (the value is the point index); later passes read the (key, index) pairs
+// an earlier pass wrote.  Passes before the last write (key, index) pairs as one 8-byte store,
+// the last writes the indices only (the permutation).
+template <bool FIRST, bool OUT_PAIRS>
+__global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(const uint32_t *__restrict__ kin, uint32_t *__restrict__ out,
                                                         int64_t n, int shift, int bits,
                                                         const uint32_t *__restrict__ gscan, int64_t ntiles) {
     extern __shared__ uint32_t smem[];
@@ -392,19 +402,29 @@ __global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(const uint32_t *__res
     uint32_t *sval = skey + RS_TILE;         // RS_TILE
     __shared__ uint32_t scan_sh[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    const int tile_n = (int)min((int64_t)RS_TILE, n - base);
+    // point indices fit 32 bits (the permutation is u32)
+    const uint32_t base = blockIdx.x * (uint32_t)RS_TILE;
+    const int tile_n = (int)min((int64_t)RS_TILE, n - (int64_t)base);
     for (int i = threadIdx.x; i < 8 * nb; i += RS_T) wcnt[i] = 0;
     __syncthreads();
     // rank of each key among the earlier keys of this warp with the same digit
     // (ranks < 1024: two 16-bit ranks per register).  The warp's 32 coalesced key loads are all
     // issued before the ranking starts, so their latencies overlap.
+    // Later passes load each (key, index) pair whole (one 8-byte load) and park the index in
+    // sval, in input order, until the ranks are known.
     uint32_t kr[RS_ITEMS], rk[RS_ITEMS / 2];
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int s = 0; s < RS_ITEMS; ++s) {
         const int pos = w * (RS_ITEMS * 32) + s * 32 + lane;
-        kr[s] = pos < tile_n ? __ldcs(kin + base + pos) : 0u;
+        if (FIRST) {
+            kr[s] = pos < tile_n ? __ldcs(kin + base + (uint32_t)pos) : 0u;
+        } else {
+            const uint2 kv = pos < tile_n ? __ldcs(reinterpret_cast<const uint2 *>(kin) + base + (uint32_t)pos)
+                                          : make_uint2(0u, 0u);
+            kr[s] = kv.x;
+            sval[pos] = kv.y;
+        }
     }
 #pragma unroll
     for (int s = 0; s < RS_ITEMS; ++s) {
@@ -450,6 +470,12 @@ __global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(const uint32_t *__res
         }
     }
     __syncthreads();
+    uint32_t vv[FIRST ? 1 : RS_ITEMS];
+    if (!FIRST) {
+#pragma unroll
+        for (int s = 0; s < RS_ITEMS; ++s) vv[FIRST ? 0 : s] = sval[w * (RS_ITEMS * 32) + s * 32 + lane];
+        __syncthreads();
+    }
 #pragma unroll
     for (int s = 0; s < RS_ITEMS; ++s) {
         const int pos = w * (RS_ITEMS * 32) + s * 32 + lane;
@@ -457,16 +483,20 @@ __global__ void __launch_bounds__(RS_T, 2) k_radix_scatter(const uint32_t *__res
             const uint32_t dg = (kr[s] >> shift) & mask;
             const uint32_t lp = tstart[dg] + wcnt[w * nb + dg] + ((s & 1) ? (rk[s >> 1] >> 16) : (rk[s >> 1] & 0xFFFFu));
             skey[lp] = kr[s];
-            sval[lp] = FIRST ? (uint32_t)(base + pos) : vin[base + pos];
+            sval[lp] = FIRST ? base + (uint32_t)pos : vv[FIRST ? 0 : s];
         }
+        if ((s & 7) == 7) __syncwarp();  // bounds how far the counter loads are hoisted (registers)
     }
     __syncthreads();
     for (int i = threadIdx.x; i < tile_n; i += RS_T) {
         const uint32_t key = skey[i];
         const uint32_t dg = (key >> shift) & mask;
         const uint32_t g = gbase[dg] + ((uint32_t)i - tstart[dg]);
-        if (WRITE_KEYS) kout[g] = key;
-        vout[g] = sval[i];
+        const uint32_t val = sval[i];
+        if (OUT_PAIRS)
+            reinterpret_cast<uint2 *>(out)[g] = make_uint2(key, val);
+        else
+            out[g] = val;
     }
 }
 
@@ -475,8 +505,6 @@ static size_t radix_scatter_smem(int bits) {
     return sizeof(uint32_t) * (size_t)(8 * nb + 2 * nb + 2 * RS_TILE);
 }
 
-// Stable sort of `keys` (values < 2^keybits); writes the permutation to perm_out.
-// Scratch: k2 (n), v1 (n), ghist (2^10 * ntiles), bsum.
 // Digit width of the first pass (the others use the same width).
 static int radix_pass_bits(int keybits) {
     keybits = std::max(keybits, 1);
@@ -484,10 +512,12 @@ static int radix_pass_bits(int keybits) {
     return (int)cdiv(keybits, npass);
 }
 
-// With first_hist, ghist already holds the first pass's per-tile histogram (from k_keys).
-static int radix_sort_perm(const uint32_t *keys, int64_t n, int keybits, uint32_t *perm_out, uint32_t *k2a,
-                           uint32_t *k2b, uint32_t *v1, uint32_t *ghist, uint32_t *bsum, bool first_hist,
-                           cudaStream_t s) {
+// Stable sort of `keys` (values < 2^keybits); writes the permutation to perm_out.  Scratch:
+// pairs (2 n words per buffer; the second buffer only with three or more passes), ghist
+// (2^10 * ntiles), bsum.  With first_hist, ghist already holds the first pass's per-tile
+// histogram (from k_keys).
+static int radix_sort_perm(const uint32_t *keys, int64_t n, int keybits, uint32_t *perm_out, uint32_t *pairs_a,
+                           uint32_t *pairs_b, uint32_t *ghist, uint32_t *bsum, bool first_hist, cudaStream_t s) {
     const int64_t ntiles = cdiv(n, RS_TILE);
     keybits = std::max(keybits, 1);
     const int npass = (int)cdiv(keybits, RS_MAXBITS);
@@ -500,35 +530,31 @@ static int radix_sort_perm(const uint32_t *keys, int64_t n, int keybits, uint32_
         FK_TRY(raise_smem_limit((const void *)k_radix_scatter<false, false>, mx));
     }
     const uint32_t *kin = keys;
-    const uint32_t *vin = nullptr;
-    uint32_t *kbufs[2] = {k2a, k2b};
-    uint32_t *vbufs[2] = {v1, perm_out};
-    // make the final pass land in perm_out
-    int vsel = (npass % 2 == 1) ? 1 : 0;
+    uint32_t *pbufs[2] = {pairs_a, pairs_b};
     for (int p = 0; p < npass; ++p) {
         const int shift = p * bits;
         const int b = std::min(bits, keybits - shift);
         const bool first = p == 0, last = p == npass - 1;
         if (!(first && first_hist)) {
-            k_radix_hist<<<(unsigned)ntiles, RS_T, 0, s>>>(kin, n, shift, b, ghist, ntiles);
+            if (first)
+                k_radix_hist<false><<<(unsigned)ntiles, RS_T, 0, s>>>(kin, n, shift, b, ghist, ntiles);
+            else
+                k_radix_hist<true><<<(unsigned)ntiles, RS_T, 0, s>>>(kin, n, shift, b, ghist, ntiles);
             FK_LAUNCH();
         }
         FK_TRY(exclusive_scan_u32(ghist, ghist, ((int64_t)1 << b) * ntiles, false, bsum, s));
-        uint32_t *kout = kbufs[p % 2];
-        uint32_t *vout = vbufs[vsel];
+        uint32_t *out = last ? perm_out : pbufs[p % 2];
         const size_t sm = radix_scatter_smem(b);
         if (first && last)
-            k_radix_scatter<true, false><<<(unsigned)ntiles, RS_T, sm, s>>>(kin, vin, kout, vout, n, shift, b, ghist, ntiles);
+            k_radix_scatter<true, false><<<(unsigned)ntiles, RS_T, sm, s>>>(kin, out, n, shift, b, ghist, ntiles);
         else if (first)
-            k_radix_scatter<true, true><<<(unsigned)ntiles, RS_T, sm, s>>>(kin, vin, kout, vout, n, shift, b, ghist, ntiles);
+            k_radix_scatter<true, true><<<(unsigned)ntiles, RS_T, sm, s>>>(kin, out, n, shift, b, ghist, ntiles);
         else if (last)
-            k_radix_scatter<false, false><<<(unsigned)ntiles, RS_T, sm, s>>>(kin, vin, kout, vout, n, shift, b, ghist, ntiles);
+            k_radix_scatter<false, false><<<(unsigned)ntiles, RS_T, sm, s>>>(kin, out, n, shift, b, ghist, ntiles);
         else
-            k_radix_scatter<false, true><<<(unsigned)ntiles, RS_T, sm, s>>>(kin, vin, kout, vout, n, shift, b, ghist, ntiles);
+            k_radix_scatter<false, true><<<(unsigned)ntiles, RS_T, sm, s>>>(kin, out, n, shift, b, ghist, ntiles);
         FK_LAUNCH();
-        kin = kout;
-        vin = vout;
-        vsel ^= 1;
+        kin = out;
     }
     return FKSKI_OK;
 }
@@ -1469,7 +1495,7 @@ static int precompute_typed(fkski_stats *st, const T *X, const T *y, const T *Z,
     Scratch sc(s);
     const int64_t n = st->n;
     const KeyParams kp = make_key_params(st->grid);
-    uint32_t *keys, *counts, *offsets, *perm, *k2a, *k2b, *v1, *ghist, *bsum;
+    uint32_t *keys, *counts, *offsets, *perm, *pairs_a, *pairs_b = nullptr, *ghist, *bsum;
     Rec4<T> *rec;
     int *dstatus;
     double *ypart, *dyty;
@@ -1481,9 +1507,10 @@ static int precompute_typed(fkski_stats *st, const T *X, const T *y, const T *Z,
     FK_TRY(sc.get(&counts, sizeof(uint32_t) * (ncell + 1)));
     FK_TRY(sc.get(&offsets, sizeof(uint32_t) * (ncell + 1)));
     FK_TRY(sc.get(&perm, sizeof(uint32_t) * n));
-    FK_TRY(sc.get(&k2a, sizeof(uint32_t) * n));
-    FK_TRY(sc.get(&k2b, sizeof(uint32_t) * n));
-    FK_TRY(sc.get(&v1, sizeof(uint32_t) * n));
+    int keybits = 1;
+    while (((int64_t)1 << keybits) < ncell) ++keybits;
+    FK_TRY(sc.get(&pairs_a, sizeof(uint2) * n));
+    if (cdiv(keybits, RS_MAXBITS) > 2) FK_TRY(sc.get(&pairs_b, sizeof(uint2) * n));
     FK_TRY(sc.get(&ghist, sizeof(uint32_t) * ((int64_t)1 << RS_MAXBITS) * ntiles));
     FK_TRY(sc.get(&bsum, sizeof(uint32_t) * (cdiv(maxscan, SCAN_TILE) + 1)));
     FK_TRY(sc.get(&dstatus, sizeof(int) * 4));
@@ -1492,15 +1519,13 @@ static int precompute_typed(fkski_stats *st, const T *X, const T *y, const T *Z,
     FK_TRY(sc.get(&dyty, sizeof(double) * (1 + kMaxProbes)));
     FK_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (ncell + 1), s));
     FK_CUDA(cudaMemsetAsync(dstatus, 0, sizeof(int) * 4, s));
-    int keybits = 1;
-    while (((int64_t)1 << keybits) < ncell) ++keybits;
     k_keys<T, D><<<kblocks, RS_T, 0, s>>>(X, y, n, kp, keys, rec, counts, ypart, dstatus, ghist,
                                          radix_pass_bits(keybits), ntiles);
     FK_LAUNCH();
     k_sum_partials<<<1, 32, 0, s>>>(ypart, kblocks, 1, dyty);
     FK_LAUNCH();
     FK_TRY(exclusive_scan_u32(counts, offsets, ncell, true, bsum, s));
-    FK_TRY(radix_sort_perm(keys, n, keybits, perm, k2a, k2b, v1, ghist, bsum, true, s));
+    FK_TRY(radix_sort_perm(keys, n, keybits, perm, pairs_a, pairs_b, ghist, bsum, true, s));
     FK_TRY((reduce_and_assemble<T, D>(st, perm, rec, offsets, Z, sc, s)));
     if (st->nprobes > 0) {
         if (Z) {
