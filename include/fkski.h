@@ -203,8 +203,10 @@ FKSKI_API int fkski_stats_load(const char *path, fkski_stats **out, void *stream
 FKSKI_API void fkski_destroy(fkski_stats *st);
 
 /* ------------------------------------------------------------------ operators (Sec. 2.2, 3.2)
- * K_G V for nrhs grid vectors (device, rhs-major, dtype), or its derivative w.r.t. one
- * hyperparameter: param = -1 for K_G, k in [0, d) for dK_G/dl_k, d for dK_G/ds.
+ * K_G V for nrhs grid vectors (device, rhs-major, dtype FKSKI_F32, FKSKI_F64 or FKSKI_F32X2:
+ * the MIXED solver's double-float vectors, (hi, lo) FP32 pairs, 8 bytes per value), or its
+ * derivative w.r.t. one hyperparameter: param = -1 for K_G, k in [0, d) for dK_G/dl_k, d for
+ * dK_G/ds.
  * RBF: Kronecker product of symmetric Toeplitz factors, one batched circulant-embedding FFT pass
  * per axis (Sec. 2.2; Lee 1986).  Matern-5/2: d-level circulant embedding (multilevel Toeplitz).
  * The spectra are recomputed on every call; in and out must not alias.  UNSUPPORTED if the

@@ -265,13 +265,19 @@ def stats_load(path: str, grid) -> Stats:
     return st
 
 
-def kg_mvm(grid, kernel, V: torch.Tensor, param: int = -1, stream=None) -> torch.Tensor:
-    """fkski_kg_mvm: K_G V (or dK_G/dtheta V) for V of shape (R, m) or (m,)."""
+def kg_mvm(grid, kernel, V: torch.Tensor, param: int = -1, stream=None, double_float: bool = False) -> torch.Tensor:
+    """fkski_kg_mvm: K_G V (or dK_G/dtheta V) for V of shape (R, m) or (m,).  With double_float,
+    V is an FP32 tensor of shape (..., m, 2) holding (hi, lo) pairs (FKSKI_F32X2)."""
     load()
     out = torch.empty_like(V)
-    R = 1 if V.dim() == 1 else V.shape[0]
+    if double_float:
+        if V.dtype != torch.float32 or V.shape[-1] != 2:
+            raise ValueError("double-float vectors are float32 tensors of shape (..., m, 2)")
+        R, code = (1 if V.dim() == 2 else V.shape[0]), F32X2
+    else:
+        R, code = (1 if V.dim() == 1 else V.shape[0]), _dtype_code(V)
     g, k = c_grid(grid), c_kernel(kernel)
-    _check(_lib.fkski_kg_mvm(ctypes.byref(g), ctypes.byref(k), param, _ptr(V), _ptr(out), R, _dtype_code(V),
+    _check(_lib.fkski_kg_mvm(ctypes.byref(g), ctypes.byref(k), param, _ptr(V), _ptr(out), R, code,
                              _stream(stream)), "fkski_kg_mvm")
     return out
 

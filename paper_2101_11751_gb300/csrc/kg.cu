@@ -79,6 +79,11 @@ __device__ __forceinline__ dfl r_add(dfl a, dfl b) { return a + b; }
 __device__ __forceinline__ dfl r_sub(dfl a, dfl b) { return a - b; }
 __device__ __forceinline__ dfl r_mul(dfl a, dfl b) { return a * b; }
 __device__ __forceinline__ dfl r_fma(dfl a, dfl b, dfl c) { return a * b + c; }
+// a b + c d: for FP32 and FP64 exactly fma(a, b, c d) as written out before; double-float fuses
+// the two products and the sum into one normalisation (df_dot2)
+__device__ __forceinline__ float r_dot2(float a, float b, float c, float d) { return r_fma(a, b, r_mul(c, d)); }
+__device__ __forceinline__ double r_dot2(double a, double b, double c, double d) { return r_fma(a, b, r_mul(c, d)); }
+__device__ __forceinline__ dfl r_dot2(dfl a, dfl b, dfl c, dfl d) { return df_dot2(a, b, c, d); }
 
 // DIF butterfly: (u, v) -> (u + v, (u - v) w)
 template <typename C>
@@ -86,15 +91,15 @@ __device__ __forceinline__ void bf_dif(C &u, C &v, const C w) {
     const auto dx = r_sub(u.x, v.x), dy = r_sub(u.y, v.y);
     u.x = r_add(u.x, v.x);
     u.y = r_add(u.y, v.y);
-    v.x = r_fma(dx, w.x, -r_mul(dy, w.y));
-    v.y = r_fma(dx, w.y, r_mul(dy, w.x));
+    v.x = r_dot2(dx, w.x, -dy, w.y);
+    v.y = r_dot2(dx, w.y, dy, w.x);
 }
 
 // DIT inverse butterfly: t = v conj(w); (u, v) -> (u + t, u - t)
 template <typename C>
 __device__ __forceinline__ void bf_dit(C &u, C &v, const C w) {
-    const auto tx = r_fma(v.x, w.x, r_mul(v.y, w.y));
-    const auto ty = r_fma(v.y, w.x, -r_mul(v.x, w.y));
+    const auto tx = r_dot2(v.x, w.x, v.y, w.y);
+    const auto ty = r_dot2(v.y, w.x, -v.x, w.y);
     v.x = r_sub(u.x, tx);
     v.y = r_sub(u.y, ty);
     u.x = r_add(u.x, tx);
@@ -289,8 +294,8 @@ __global__ void __launch_bounds__(FFT_TMAX) k_kron_pass(const T *__restrict__ in
         }
         const C w = tw[i];
         C v;
-        v.x = r_fma(u.x, w.x, -r_mul(u.y, w.y));
-        v.y = r_fma(u.x, w.y, r_mul(u.y, w.x));
+        v.x = r_dot2(u.x, w.x, -u.y, w.y);
+        v.y = r_dot2(u.x, w.y, u.y, w.x);
         x[c * L + i] = u;
         x[c * L + i + H] = v;
     };
@@ -307,8 +312,8 @@ __global__ void __launch_bounds__(FFT_TMAX) k_kron_pass(const T *__restrict__ in
     // last DIT stage (span L/2) for the kept outputs i < M: u + v conj(w_i)
     auto store_one = [&](int c, int i) {
         const C u = x[c * L + i], v = x[c * L + i + H], w = tw[i];
-        const T tx = r_fma(v.x, w.x, r_mul(v.y, w.y));
-        const T ty = r_fma(v.y, w.x, -r_mul(v.x, w.y));
+        const T tx = r_dot2(v.x, w.x, v.y, w.y);
+        const T ty = r_dot2(v.y, w.x, -v.x, w.y);
         const long long a0 = la[2 * c], a1 = la[2 * c + 1];
         if (a0 >= 0) {
             const int64_t a = a0 + (int64_t)i * S;
@@ -355,6 +360,19 @@ __device__ __forceinline__ C cmulc(const C a, const C b) {  // a * conj(b)
     C r;
     r.x = a.x * b.x + a.y * b.y;
     r.y = a.y * b.x - a.x * b.y;
+    return r;
+}
+// double-float: each part as one fused a b + c d
+__device__ __forceinline__ dfl2 cmul(const dfl2 a, const dfl2 b) {
+    dfl2 r;
+    r.x = df_dot2(a.x, b.x, -a.y, b.y);
+    r.y = df_dot2(a.x, b.y, a.y, b.x);
+    return r;
+}
+__device__ __forceinline__ dfl2 cmulc(const dfl2 a, const dfl2 b) {
+    dfl2 r;
+    r.x = df_dot2(a.x, b.x, a.y, b.y);
+    r.y = df_dot2(a.y, b.x, -a.x, b.y);
     return r;
 }
 
@@ -1332,7 +1350,7 @@ int kg_mvm_impl(const fkski_grid *grid, const fkski_kernel *kern, int param, con
                 int dtype, cudaStream_t s) {
     if (!grid || !kern || !v || !out || nrhs < 1) return FKSKI_E_INVALID_ARG;
     if (grid->d < 1 || grid->d > 3) return FKSKI_E_INVALID_ARG;
-    if (dtype != FKSKI_F32 && dtype != FKSKI_F64) return FKSKI_E_INVALID_ARG;
+    if (dtype != FKSKI_F32 && dtype != FKSKI_F64 && dtype != FK_DF) return FKSKI_E_INVALID_ARG;
     for (int k = 0; k < grid->d; ++k)
         if (grid->M[k] < 4 || !(grid->h[k] > 0.0)) return FKSKI_E_INVALID_ARG;
     if (v == out) return FKSKI_E_INVALID_ARG;

@@ -5,6 +5,7 @@
 //   f ah al b            (ah + al) * b, b an FP32 number
 //   x ah al b xh xl      (ah + al) + b * (xh + xl), the band-product accumulation
 //   A k [b xh xl]*k      sum of k products b * (xh + xl) in the lazily normalised accumulator
+//   d ah al bh bl ch cl dh dl   (ah + al)(bh + bl) + (ch + cl)(dh + dl), one normalisation
 #include <cstdio>
 #include "dfloat.cuh"
 
@@ -33,6 +34,11 @@ int main() {
                 fk::dacc_add_fx(acc, b, dfl(xh, xl));
             }
             r = fk::dacc_value(acc);
+        } else if (op[0] == 'd') {
+            float v[8];
+            for (int i = 0; i < 8; ++i)
+                if (scanf("%a", &v[i]) != 1) return 1;
+            r = fk::df_dot2(dfl(v[0], v[1]), dfl(v[2], v[3]), dfl(v[4], v[5]), dfl(v[6], v[7]));
         } else if (op[0] == 'x') {
             float ah, al, b, xh, xl;
             if (scanf("%a %a %a %a %a", &ah, &al, &b, &xh, &xl) != 5) return 1;

@@ -3,7 +3,8 @@
 The header's inline functions are compiled for the host by nvcc and evaluated on random operands
 spanning many binades; every result is compared with the exact rational value.  Bars: the
 Dekker-style addition errs by at most 2^-45 (|a| + |b|), products by 2^-45 |a b|, the band
-accumulation acc + b x by 2^-45 (|acc| + |b x|), a 343-term lazily normalised band sum by
+accumulation acc + b x by 2^-45 (|acc| + |b x|), the fused a b + c d of the complex products by
+2^-45 (|a b| + |c d|), a 343-term lazily normalised band sum by
 2^-40 sum |b x| (343 terms of at most ~2^-48 each), and the conversion from a double by
 2^-48 |v|; every result is normalised (hi = fl(hi + lo))."""
 import os
@@ -128,3 +129,21 @@ def test_lazy_band_sum(driver):
         mag = sum(abs(p) for p in prods)
         assert _normalised(h, l)
         assert abs(Fraction(h) + Fraction(l) - exact) <= Fraction(2) ** -40 * mag
+
+
+def test_dot2(driver):
+    """a b + c d with one normalisation (the K_G butterflies' complex products), including
+    near-cancelling pairs (c d close to -a b)."""
+    rng = np.random.default_rng(4)
+    A, B, C, D = (_operands(rng, 300) for _ in range(4))
+    for i in range(0, 300, 4):  # c d = -(a b) up to the low parts
+        C[i] = (-A[i][0], _f32(A[i][1] * 0.5))
+        D[i] = (B[i][0], _f32(B[i][1] * 0.25))
+    lines = [f"d {a[0].hex()} {a[1].hex()} {b[0].hex()} {b[1].hex()} {c[0].hex()} {c[1].hex()} "
+             f"{d[0].hex()} {d[1].hex()}" for a, b, c, d in zip(A, B, C, D)]
+    res = _run(driver, lines)
+    fr = lambda t: Fraction(t[0]) + Fraction(t[1])  # noqa: E731
+    for (a, b, c, d), (h, l) in zip(zip(A, B, C, D), res):
+        ab, cd = fr(a) * fr(b), fr(c) * fr(d)
+        assert _normalised(h, l)
+        assert abs(Fraction(h) + Fraction(l) - (ab + cd)) <= Fraction(2) ** -45 * (abs(ab) + abs(cd)), (a, b, c, d)
