@@ -11,9 +11,11 @@
 // L_1 x ... x L_d torus has a real spectrum; vectors are packed in pairs into complex tensors and
 // transformed axis by axis (only the M-extent lines are transformed along each axis).
 //
-// FFT scheme: radix-2 decimation in frequency (natural order in, bit-reversed out), the
-// pointwise spectrum multiply in bit-reversed order, radix-2 decimation in time back (bit-reversed
-// in, natural out) -- no permutation pass.  Twiddles come from sincospi on the device.
+// FFT scheme: decimation in frequency (natural order in, bit-reversed out), the pointwise
+// spectrum multiply in bit-reversed order, decimation in time back (bit-reversed in, natural out)
+// -- no permutation pass.  Stages run in radix-4 groups (three twiddle products per group, the
+// factors of -i exact) with one radix-2 stage when log2 L is odd.  Twiddles come from sincospi
+// on the device.
 #include "fkski_internal.cuh"
 
 #include <algorithm>
@@ -64,9 +66,8 @@ __device__ __forceinline__ void make_twiddles<dfl>(dfl2 *tw, int L) {
     }
 }
 
-// Butterfly arithmetic with every rounding spelled out (no contraction left to the compiler), so
-// that the radix-2 and radix-4 stage groupings below give bit-identical results: the tuner's
-// choice changes speed only.
+// Butterfly arithmetic with every rounding spelled out (no contraction left to the compiler): a
+// result depends on the transform length only, never on the launch shape the tuner picks.
 __device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
@@ -106,6 +107,39 @@ __device__ __forceinline__ void bf_dit(C &u, C &v, const C w) {
     u.y = r_add(u.y, ty);
 }
 
+// W_L^e for 0 <= e < L from the half table (W_L^{e + L/2} = -W_L^e)
+template <typename C>
+__device__ __forceinline__ C tw_at(const C *tw, int e, int L) {
+    C w = tw[e & ((L >> 1) - 1)];
+    if (e >= (L >> 1)) { w.x = -w.x; w.y = -w.y; }
+    return w;
+}
+template <typename C>
+__device__ __forceinline__ C cprod(const C a, const C w) {  // a w
+    C r;
+    r.x = r_dot2(a.x, w.x, -a.y, w.y);
+    r.y = r_dot2(a.x, w.y, a.y, w.x);
+    return r;
+}
+template <typename C>
+__device__ __forceinline__ C cprodc(const C a, const C w) {  // a conj(w)
+    C r;
+    r.x = r_dot2(a.x, w.x, a.y, w.y);
+    r.y = r_dot2(a.y, w.x, -a.x, w.y);
+    return r;
+}
+
+// The butterfly of the radix-2 span-1 stages, whose twiddle is W^0 = 1: the product is exact,
+// so it is left out (same values; a zero may change sign).
+template <typename C>
+__device__ __forceinline__ void bf_sum_dif(C &u, C &v) {  // (u, v) -> (u + v, u - v)
+    const auto dx = r_sub(u.x, v.x), dy = r_sub(u.y, v.y);
+    u.x = r_add(u.x, v.x);
+    u.y = r_add(u.y, v.y);
+    v.x = dx;
+    v.y = dy;
+}
+
 // In-place DIF over `nl` lines of length L stored contiguously (line stride L), natural order in,
 // bit-reversed out.  RADIX 4 runs two radix-2 stages (spans h, h/2) per pass over shared memory:
 // each thread keeps 4 values in registers, halving the passes and barriers.  The stages run from
@@ -125,17 +159,31 @@ __device__ __forceinline__ void fft_dif(typename Cx<T>::t *x, int nl, int L, con
                 const int line = b >> lq, k = b & ((L >> 2) - 1);
                 const int j = k & (q - 1), blk = k >> lqq;
                 C *xl = x + line * L + blk * 2 * h;
-                C a0 = xl[j], a1 = xl[j + q], a2 = xl[j + h], a3 = xl[j + h + q];
-                bf_dif(a0, a2, tw[j * tA]);
-                bf_dif(a1, a3, tw[(j + q) * tA]);
-                const C wb = tw[j * tB];
-                bf_dif(a0, a1, wb);
-                bf_dif(a2, a3, wb);
-                xl[j] = a0;
-                xl[j + q] = a1;
-                xl[j + h] = a2;
-                xl[j + h + q] = a3;
+                const C a0 = xl[j], a1 = xl[j + q], a2 = xl[j + h], a3 = xl[j + h + q];
+                // spans h and h/2 at once: with w = W^(j tA), W^((j+q) tA) = -i w and W^(j tB) = w^2,
+                //   out0 = s + t, out1 = (s - t) w^2, out2 = (d - i e) w, out3 = (d + i e) w^3
+                // for s = a0 + a2, t = a1 + a3, d = a0 - a2, e = a1 - a3
+                C sv, tv, d, e;
+                sv.x = r_add(a0.x, a2.x); sv.y = r_add(a0.y, a2.y);
+                tv.x = r_add(a1.x, a3.x); tv.y = r_add(a1.y, a3.y);
+                d.x = r_sub(a0.x, a2.x); d.y = r_sub(a0.y, a2.y);
+                e.x = r_sub(a1.x, a3.x); e.y = r_sub(a1.y, a3.y);
+                C o0, o1, o2, o3;
+                o0.x = r_add(sv.x, tv.x); o0.y = r_add(sv.y, tv.y);
+                o1.x = r_sub(sv.x, tv.x); o1.y = r_sub(sv.y, tv.y);
+                o2.x = r_add(d.x, e.y); o2.y = r_sub(d.y, e.x);
+                o3.x = r_sub(d.x, e.y); o3.y = r_add(d.y, e.x);
+                if (j > 0) {
+                    o1 = cprod(o1, tw[j * tB]);
+                    o2 = cprod(o2, tw[j * tA]);
+                    o3 = cprod(o3, tw_at(tw, 3 * j * tA, L));
+                }
+                xl[j] = o0;
+                xl[j + q] = o1;
+                xl[j + h] = o2;
+                xl[j + h + q] = o3;
             }
+
             __syncthreads();
         }
     }
@@ -149,7 +197,10 @@ __device__ __forceinline__ void fft_dif(typename Cx<T>::t *x, int nl, int L, con
             const int j = k & (h - 1), blk = k >> lh;
             C *xl = x + line * L + blk * 2 * h;
             C u = xl[j], v = xl[j + h];
-            bf_dif(u, v, tw[j * tstep]);
+            if (h == 1)
+                bf_sum_dif(u, v);
+            else
+                bf_dif(u, v, tw[j * tstep]);
             xl[j] = u;
             xl[j + h] = v;
         }
@@ -187,11 +238,24 @@ __device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L,
                     a2.x = r_mul(a2.x, l2); a2.y = r_mul(a2.y, l2);
                     a3.x = r_mul(a3.x, l3); a3.y = r_mul(a3.y, l3);
                 }
-                const C wa = tw[j * tA];
-                bf_dit(a0, a1, wa);
-                bf_dit(a2, a3, wa);
-                bf_dit(a0, a2, tw[j * tB]);
-                bf_dit(a1, a3, tw[(j + h) * tB]);
+                // spans h and 2h at once: with v = W^(j tB), W^(j tA) = v^2 and W^((j+h) tB) = -i v,
+                //   b1 = a1 conj(v^2), b2 = a2 conj(v), b3 = a3 conj(v^3);
+                //   out0 = s + t, out2 = s - t, out1 = d + i e, out3 = d - i e
+                // for s = a0 + b1, t = b2 + b3, d = a0 - b1, e = b2 - b3
+                if (j > 0) {
+                    a1 = cprodc(a1, tw[j * tA]);
+                    a2 = cprodc(a2, tw[j * tB]);
+                    a3 = cprodc(a3, tw_at(tw, 3 * j * tB, L));
+                }
+                C sv, tv, d, e;
+                sv.x = r_add(a0.x, a1.x); sv.y = r_add(a0.y, a1.y);
+                d.x = r_sub(a0.x, a1.x); d.y = r_sub(a0.y, a1.y);
+                tv.x = r_add(a2.x, a3.x); tv.y = r_add(a2.y, a3.y);
+                e.x = r_sub(a2.x, a3.x); e.y = r_sub(a2.y, a3.y);
+                a0.x = r_add(sv.x, tv.x); a0.y = r_add(sv.y, tv.y);
+                a2.x = r_sub(sv.x, tv.x); a2.y = r_sub(sv.y, tv.y);
+                a1.x = r_sub(d.x, e.y); a1.y = r_add(d.y, e.x);
+                a3.x = r_add(d.x, e.y); a3.y = r_sub(d.y, e.x);
                 xl[j] = a0;
                 xl[j + h] = a1;
                 xl[j + 2 * h] = a2;
@@ -215,7 +279,10 @@ __device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L,
                 u.x = r_mul(u.x, lu); u.y = r_mul(u.y, lu);
                 v.x = r_mul(v.x, lv); v.y = r_mul(v.y, lv);
             }
-            bf_dit(u, v, tw[j * tstep]);
+            if (h == 1)
+                bf_sum_dif(u, v);
+            else
+                bf_dit(u, v, tw[j * tstep]);
             xl[j] = u;
             xl[j + h] = v;
         }
@@ -961,8 +1028,9 @@ int kgop_set(KgOp *op, const fkski_kernel *kern, int param, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ pass configuration and tuner
-// A Kronecker pass is launched with (RADIX, complex lines per CTA, threads per CTA).  The choice
-// changes speed only (the stage groupings are bit-identical, and lines are independent).  The
+// A Kronecker pass is launched with (kernel, complex lines per CTA, threads per CTA).  The choice
+// changes speed only: lines are independent, and which kernel runs (register or shared-memory
+// transform) depends on the precision and L alone.  The
 // tuner times every candidate on the real pass shape (once per shape and process, outside any
 // graph capture: the solver calls kgop_tune before capturing) and keeps the fastest; untuned shapes get a default that
 // puts at least ~4 CTAs on every SM.
@@ -1069,11 +1137,7 @@ static int launch_kron(const T *src, T *dst, RealPass p, const PassCfg &cfg, con
         FK_TRY(raise_smem_limit((const void *)k_kron_pass<T, EPIV, RADV>, sm)); \
         k_kron_pass<T, EPIV, RADV><<<nb, cfg.threads, sm, s>>>(src, dst, p, lam, tw, addv, alpha_dev, alpha, gate); \
     } while (0)
-    if (addv) {
-        if (cfg.radix == 4) FK_KRON(true, 4); else FK_KRON(true, 2);
-    } else {
-        if (cfg.radix == 4) FK_KRON(false, 4); else FK_KRON(false, 2);
-    }
+    if (addv) FK_KRON(true, 4); else FK_KRON(false, 4);
 #undef FK_KRON
     FK_LAUNCH();
     return FKSKI_OK;
@@ -1142,7 +1206,7 @@ static int tune_pass(int dtype, RealPass p, const T *lam, const typename Cx<T>::
         }
     } else {
         const int clmax = std::max(1, FFT_SMEM_CPLX / p.L);
-        for (int radix : {4, 2}) {
+        for (int radix : {4}) {
             for (int threads : {128, 256, 512}) {
                 for (int cl = 1; cl <= clmax && rc == FKSKI_OK; cl <<= 1) {
                     if (cl > 1 && cl / 2 >= ncl) break;  // more lines per CTA than there are lines
