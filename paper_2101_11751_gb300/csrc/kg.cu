@@ -1043,7 +1043,9 @@ struct PassCfg {
 // L = 64 (its 16-value columns need twice the registers, and for L = 128, 256 the
 // shared-memory kernel is as fast or faster); double-float up to DF_REG_LMAX.  The rule depends
 // on the shape only.
-constexpr int DF_REG_LMAX = 64;  // L = 128, 256: the shared-memory radix-4 pass is faster (20.9 vs 28.1 us at L = 256)
+// L = 128, 256: the shared-memory radix-4 pass is faster (L = 256: 20.9 against 28.1 us per pass;
+// L = 128, 17 rhs on a 64^3 grid: 1.71 against 1.85 ms per gradient iteration)
+constexpr int DF_REG_LMAX = 64;
 static bool reg_fft_ok(int dtype, int L) {
     return L >= 8 && L <= (dtype == FKSKI_F32 ? 256 : (dtype == FK_DF ? DF_REG_LMAX : 64));
 }
