@@ -47,6 +47,7 @@ def measured_peaks():
     return HBM_FALLBACK, "fallback"
 
 
+FP32_LANE_OPS_TS = 152 * 128 * 2.07e9 / 1e12  # FP32 lane operations per second (T), GB300 at 2.07 GHz
 SPMV_KERNEL = "k_band_spmv4hd<49, 0>"  # the MIXED iteration's band product: FP32 half band, double-float x, u
 SPMV32_KERNEL = "k_band_spmv4h<49, 0>"  # the same product on FP32 vectors (the FP32 mode)
 
@@ -641,6 +642,14 @@ def main():
                      "bound": "hbm", "achieved": spmv_gbs,
                      "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": spmv_gbs / hbm_peak,
                      "traffic": profiled_traffic(SPMV_KERNEL), "algorithmic_bytes": spmv_bytes, "launch_ms": spmv_ms},
+        # the same double-float band product against the FP32 pipes: 11 FP32 operations per band
+        # term (TwoProd of the high parts, the low part's product, TwoSum, two additions), 343
+        # terms per node; peak = 152 SMs x 128 FP32 lanes x 2.07 GHz
+        "roofline_alu": {"kernel": SPMV_KERNEL, "bound": "alu",
+                         "achieved": 11 * 343 * m / (spmv_ms / 1e3) / 1e12,
+                         "peak": FP32_LANE_OPS_TS, "unit": "T FP32 ops/s",
+                         "frac": 11 * 343 * m / (spmv_ms / 1e3) / 1e12 / FP32_LANE_OPS_TS,
+                         "algorithmic_ops": 11 * 343 * m, "launch_ms": spmv_ms},
         "roofline_fp32_spmv": {"kernel": SPMV32_KERNEL + " (the FP32 mode's band product)", "bound": "hbm",
                                "achieved": spmv32_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": spmv32_gbs / hbm_peak,
                                "traffic": profiled_traffic(SPMV32_KERNEL), "algorithmic_bytes": spmv32_bytes,
