@@ -140,14 +140,24 @@ __device__ __forceinline__ void bf_sum_dif(C &u, C &v) {  // (u, v) -> (u + v, u
     v.y = dy;
 }
 
+// Shared-memory line layout.  PAD inserts one complex slot after every 8, so that the small-span
+// stages, whose four accesses of a group lie at a stride of 2 to 8 slots, spread over all banks
+// instead of a quarter of them; lines are then L + L/8 slots apart.
+template <bool PAD>
+__device__ __forceinline__ int pad_index(int e) { return PAD ? e + (e >> 3) : e; }
+template <bool PAD>
+__host__ __device__ __forceinline__ int line_stride(int L) { return PAD ? L + (L >> 3) : L; }
+
 // In-place DIF over `nl` lines of length L stored contiguously (line stride L), natural order in,
 // bit-reversed out.  RADIX 4 runs two radix-2 stages (spans h, h/2) per pass over shared memory:
 // each thread keeps 4 values in registers, halving the passes and barriers.  The stages run from
 // span h0 down to 1 (h0 = L/2 for a whole transform; a caller that has already done the larger
 // spans passes the next one).
-template <typename T, int RADIX>
+template <typename T, int RADIX, bool PAD = false>
 __device__ __forceinline__ void fft_dif(typename Cx<T>::t *x, int nl, int L, const typename Cx<T>::t *tw, int h0 = 0) {
     using C = typename Cx<T>::t;
+    const int LS = line_stride<PAD>(L);
+    auto at = [&](int line, int e) -> C & { return x[line * LS + pad_index<PAD>(e)]; };
     int h = h0 > 0 ? h0 : (L >> 1);
     if (RADIX == 4) {
         const int ng = nl * (L >> 2);
@@ -158,8 +168,8 @@ __device__ __forceinline__ void fft_dif(typename Cx<T>::t *x, int nl, int L, con
             for (int b = threadIdx.x; b < ng; b += blockDim.x) {
                 const int line = b >> lq, k = b & ((L >> 2) - 1);
                 const int j = k & (q - 1), blk = k >> lqq;
-                C *xl = x + line * L + blk * 2 * h;
-                const C a0 = xl[j], a1 = xl[j + q], a2 = xl[j + h], a3 = xl[j + h + q];
+                const int e0 = blk * 2 * h + j;
+                const C a0 = at(line, e0), a1 = at(line, e0 + q), a2 = at(line, e0 + h), a3 = at(line, e0 + h + q);
                 // spans h and h/2 at once: with w = W^(j tA), W^((j+q) tA) = -i w and W^(j tB) = w^2,
                 //   out0 = s + t, out1 = (s - t) w^2, out2 = (d - i e) w, out3 = (d + i e) w^3
                 // for s = a0 + a2, t = a1 + a3, d = a0 - a2, e = a1 - a3
@@ -178,10 +188,10 @@ __device__ __forceinline__ void fft_dif(typename Cx<T>::t *x, int nl, int L, con
                     o2 = cprod(o2, tw[j * tA]);
                     o3 = cprod(o3, tw_at(tw, 3 * j * tA, L));
                 }
-                xl[j] = o0;
-                xl[j + q] = o1;
-                xl[j + h] = o2;
-                xl[j + h + q] = o3;
+                at(line, e0) = o0;
+                at(line, e0 + q) = o1;
+                at(line, e0 + h) = o2;
+                at(line, e0 + h + q) = o3;
             }
 
             __syncthreads();
@@ -195,14 +205,14 @@ __device__ __forceinline__ void fft_dif(typename Cx<T>::t *x, int nl, int L, con
         for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
             const int line = b >> lhalf, k = b & ((L >> 1) - 1);
             const int j = k & (h - 1), blk = k >> lh;
-            C *xl = x + line * L + blk * 2 * h;
-            C u = xl[j], v = xl[j + h];
+            const int e0 = blk * 2 * h + j;
+            C u = at(line, e0), v = at(line, e0 + h);
             if (h == 1)
                 bf_sum_dif(u, v);
             else
                 bf_dif(u, v, tw[j * tstep]);
-            xl[j] = u;
-            xl[j + h] = v;
+            at(line, e0) = u;
+            at(line, e0 + h) = v;
         }
         __syncthreads();
     }
@@ -213,10 +223,12 @@ __device__ __forceinline__ void fft_dif(typename Cx<T>::t *x, int nl, int L, con
 // run (htop = L for a whole transform; a caller that finishes the largest span itself passes L/2).
 // With `lam`, the inputs of the first stage are first multiplied by lam[position in the line]
 // (the pointwise spectrum product, rounded exactly as a separate pass would round it).
-template <typename T, int RADIX>
+template <typename T, int RADIX, bool PAD = false>
 __device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L, const typename Cx<T>::t *tw,
                                             int htop = 0, const T *__restrict__ lam = nullptr) {
     using C = typename Cx<T>::t;
+    const int LS = line_stride<PAD>(L);
+    auto at = [&](int line, int e) -> C & { return x[line * LS + pad_index<PAD>(e)]; };
     if (htop <= 0) htop = L;
     int h = 1;
     if (RADIX == 4) {
@@ -228,8 +240,8 @@ __device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L,
             for (int b = threadIdx.x; b < ng; b += blockDim.x) {
                 const int line = b >> lq, k = b & ((L >> 2) - 1);
                 const int j = k & (h - 1), blk = k >> lh;
-                C *xl = x + line * L + blk * 4 * h;
-                C a0 = xl[j], a1 = xl[j + h], a2 = xl[j + 2 * h], a3 = xl[j + 3 * h];
+                const int e0 = blk * 4 * h + j;
+                C a0 = at(line, e0), a1 = at(line, e0 + h), a2 = at(line, e0 + 2 * h), a3 = at(line, e0 + 3 * h);
                 if (lam && h == 1) {
                     const T *lb = lam + blk * 4;
                     const T l0 = lb[0], l1 = lb[1], l2 = lb[2], l3 = lb[3];
@@ -256,10 +268,10 @@ __device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L,
                 a2.x = r_sub(sv.x, tv.x); a2.y = r_sub(sv.y, tv.y);
                 a1.x = r_sub(d.x, e.y); a1.y = r_add(d.y, e.x);
                 a3.x = r_add(d.x, e.y); a3.y = r_sub(d.y, e.x);
-                xl[j] = a0;
-                xl[j + h] = a1;
-                xl[j + 2 * h] = a2;
-                xl[j + 3 * h] = a3;
+                at(line, e0) = a0;
+                at(line, e0 + h) = a1;
+                at(line, e0 + 2 * h) = a2;
+                at(line, e0 + 3 * h) = a3;
             }
             __syncthreads();
         }
@@ -272,8 +284,8 @@ __device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L,
         for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
             const int line = b >> lhalf, k = b & ((L >> 1) - 1);
             const int j = k & (h - 1), blk = k >> lh;
-            C *xl = x + line * L + blk * 2 * h;
-            C u = xl[j], v = xl[j + h];
+            const int e0 = blk * 2 * h + j;
+            C u = at(line, e0), v = at(line, e0 + h);
             if (lam && h == 1) {
                 const T lu = lam[blk * 2], lv = lam[blk * 2 + 1];
                 u.x = r_mul(u.x, lu); u.y = r_mul(u.y, lu);
@@ -283,8 +295,8 @@ __device__ __forceinline__ void fft_dit_inv(typename Cx<T>::t *x, int nl, int L,
                 bf_sum_dif(u, v);
             else
                 bf_dit(u, v, tw[j * tstep]);
-            xl[j] = u;
-            xl[j + h] = v;
+            at(line, e0) = u;
+            at(line, e0 + h) = v;
         }
         __syncthreads();
     }
@@ -310,7 +322,8 @@ constexpr int FFT_TMAX = 512;
 
 // One CTA transforms Q real lines (Q/2 complex lines).  Shared memory: the twiddles (copied from
 // a table computed once per operator), the Q line base addresses (the only 64-bit index
-// arithmetic, once per line), then the lines.  Two stages are folded into the global-memory
+// arithmetic, once per line), then the lines in the padded layout (pad_index).  Two stages are
+// folded into the global-memory
 // phases: the upper half of every embedded line is zero (M <= L/2), so the first DIF stage (span
 // L/2) is one complex multiply at load time, and only the first M outputs are kept, so the last
 // DIT stage (span L/2) is one complex multiply-add at store time.  The spectrum product is folded
@@ -326,6 +339,7 @@ __global__ void __launch_bounds__(FFT_TMAX) k_kron_pass(const T *__restrict__ in
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int L = p.L, M = p.M, Q = p.Q, H = L >> 1;
+    const int LS = line_stride<true>(L);
     const int nc = Q >> 1;
     C *tw = reinterpret_cast<C *>(smraw);
     long long *la = reinterpret_cast<long long *>(tw + H);
@@ -363,8 +377,8 @@ __global__ void __launch_bounds__(FFT_TMAX) k_kron_pass(const T *__restrict__ in
         C v;
         v.x = r_dot2(u.x, w.x, -u.y, w.y);
         v.y = r_dot2(u.x, w.y, u.y, w.x);
-        x[c * L + i] = u;
-        x[c * L + i + H] = v;
+        x[c * LS + pad_index<true>(i)] = u;
+        x[c * LS + pad_index<true>(i + H)] = v;
     };
     if (S == 1) {  // lines are contiguous: consecutive threads along the line (H is a power of two)
         const int lh = __ffs(H) - 1;
@@ -373,12 +387,12 @@ __global__ void __launch_bounds__(FFT_TMAX) k_kron_pass(const T *__restrict__ in
         for (int e = threadIdx.x; e < nc * H; e += blockDim.x) load_one(e & (nc - 1), e >> lc);
     }
     __syncthreads();
-    fft_dif<T, RADIX>(x, nc, L, tw, H >> 1);
-    fft_dit_inv<T, RADIX>(x, nc, L, tw, H, lam_br);
+    fft_dif<T, RADIX, true>(x, nc, L, tw, H >> 1);
+    fft_dit_inv<T, RADIX, true>(x, nc, L, tw, H, lam_br);
     const T alpha = EPI ? (alpha_dev ? (T)(*alpha_dev) : (T)alpha_host) : T(0);
     // last DIT stage (span L/2) for the kept outputs i < M: u + v conj(w_i)
     auto store_one = [&](int c, int i) {
-        const C u = x[c * L + i], v = x[c * L + i + H], w = tw[i];
+        const C u = x[c * LS + pad_index<true>(i)], v = x[c * LS + pad_index<true>(i + H)], w = tw[i];
         const T tx = r_dot2(v.x, w.x, v.y, w.y);
         const T ty = r_dot2(v.y, w.x, -v.x, w.y);
         const long long a0 = la[2 * c], a1 = la[2 * c + 1];
@@ -1133,7 +1147,8 @@ static int launch_kron(const T *src, T *dst, RealPass p, const PassCfg &cfg, con
         FK_LAUNCH();
         return FKSKI_OK;
     }
-    const size_t sm = sizeof(typename Cx<T>::t) * ((size_t)p.L / 2 + (size_t)cfg.cl * p.L) + sizeof(long long) * p.Q;
+    const size_t sm = sizeof(typename Cx<T>::t) * ((size_t)p.L / 2 + (size_t)cfg.cl * line_stride<true>(p.L)) +
+                      sizeof(long long) * p.Q;
 #define FK_KRON(EPIV, RADV)                                                                                      \
     do {                                                                                                         \
         FK_TRY(raise_smem_limit((const void *)k_kron_pass<T, EPIV, RADV>, sm)); \
